@@ -1,0 +1,188 @@
+"""Seeded synthetic workloads shaped like the paper's cases.
+
+This module holds the initial states and the parameter sets only: none of the
+method's arithmetic lives here.  It is the single input source shared by the
+CUDA path and the CPU oracle, and it imports neither.
+
+A parameter set is a plain ``dict`` with the physical names of the method
+(Sec. 2 and the parameter paragraph of Sec. 4):
+
+``dim, nx, ny, nz, dx, dt, cs, rhoL, rhoG, etaL, etaG, rho_ref, sigma, M, W,
+g (3-tuple), bc (3-tuple of "periodic" | "noslip" | "freeslip"),
+ch_scheme (2 | 4), iso (9 | 15 | 19 | 27), bulk_visc, p_average, ch_advection``
+
+and a field set is a ``dict`` of float64 numpy arrays ``phi, p, u, v[, w]``
+of shape ``(ny, nx)`` or ``(nz, ny, nx)``.  The velocity component along an
+axis lives on the low face of each cell along that axis.
+
+Uniform noise is drawn from SplitMix64 (Steele, Lea & Flood 2014) of
+``seed * 2**32 + cell index``, mapped to ``[-amp, amp]`` with 53-bit mantissas,
+so the same cell gets the same number at any grid decomposition.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """SplitMix64 finaliser of the uint64 counters ``x`` (published constants)."""
+    with np.errstate(over="ignore"):
+        z = (x + np.uint64(0x9E3779B97F4A7C15)) & np.uint64(_M64)
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & np.uint64(_M64)
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & np.uint64(_M64)
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform_noise(seed: int, shape, amp: float) -> np.ndarray:
+    """Uniform numbers in [-amp, amp], one per cell, from SplitMix64(seed, index)."""
+    n = int(np.prod(shape))
+    ctr = np.arange(n, dtype=np.uint64) + np.uint64((int(seed) & 0xFFFFFFFF) << 32)
+    r = splitmix64(ctr)
+    u01 = (r >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    return (amp * (2.0 * u01 - 1.0)).reshape(shape)
+
+
+def base_params(dim: int, nx: int, ny: int, nz: int = 1, **kw) -> dict:
+    prm = dict(dim=dim, nx=nx, ny=ny, nz=nz if dim == 3 else 1, dx=1.0, dt=0.1, cs=1.0,
+               rhoL=1.0, rhoG=0.1, etaL=0.1, etaG=0.01, rho_ref=0.0, sigma=0.01, M=0.02, W=4.0,
+               g=(0.0, 0.0, 0.0), bc=("periodic",) * 3, ch_scheme=2 if dim == 2 else 4,
+               iso=9 if dim == 2 else 15, bulk_visc=1, p_average=1, ch_advection=0)
+    prm.update(kw)
+    return prm
+
+
+def shape_of(prm: dict):
+    if prm["dim"] == 3:
+        return (prm["nz"], prm["ny"], prm["nx"])
+    return (prm["ny"], prm["nx"])
+
+
+def zero_fields(prm: dict) -> dict:
+    shp = shape_of(prm)
+    f = {k: np.zeros(shp) for k in ("phi", "p", "u", "v")}
+    if prm["dim"] == 3:
+        f["w"] = np.zeros(shp)
+    return f
+
+
+def cell_centres(prm: dict):
+    """Coordinates of the cell centres, one array per axis (x, y[, z])."""
+    dx = prm["dx"]
+    if prm["dim"] == 3:
+        z, y, x = np.meshgrid((np.arange(prm["nz"]) + 0.5) * dx, (np.arange(prm["ny"]) + 0.5) * dx,
+                              (np.arange(prm["nx"]) + 0.5) * dx, indexing="ij")
+        return x, y, z
+    y, x = np.meshgrid((np.arange(prm["ny"]) + 0.5) * dx, (np.arange(prm["nx"]) + 0.5) * dx,
+                       indexing="ij")
+    return x, y
+
+
+# ---------------------------------------------------------------------------
+# the five workloads
+# ---------------------------------------------------------------------------
+
+def static_drop(n: int = 64, R: float = 16.0, W_cfg: float = 2.0, noise: float = 1e-3, seed: int = 1,
+                steps: int = 2000):
+    """2D static drop, periodic n x n, dx = 1, drop of radius R centred in the box.
+
+    phi = tanh((R - r) / (sqrt(2) W_cfg)) + U[-noise, noise]; u = v = p = 0.
+    Density ratio 10, viscosity ratio 10 (heavy inside), sigma = 0.01,
+    M = 0.02, Mach 0.1, acoustic CFL 0.3.  With U_c = sigma / eta_L (Sec. 4)
+    and eta_L = 0.1 this gives c_s = 1, dt = 0.3.  The model width W is the
+    one whose equilibrium profile tanh(2d/W) equals the prescribed initial
+    profile: W = 2 sqrt(2) W_cfg.
+    """
+    etaL, sigma, Ma, cfl = 0.1, 0.01, 0.1, 0.3
+    Uc = sigma / etaL
+    cs = Uc / Ma
+    prm = base_params(2, n, n, dx=1.0, cs=cs, dt=cfl * 1.0 / cs, rhoL=1.0, rhoG=0.1, etaL=etaL,
+                      etaG=etaL / 10.0, sigma=sigma, M=0.02, W=2.0 * math.sqrt(2.0) * W_cfg,
+                      bc=("periodic", "periodic", "periodic"))
+    prm["steps"] = steps
+    f = zero_fields(prm)
+    x, y = cell_centres(prm)
+    r = np.sqrt((x - n / 2.0) ** 2 + (y - n / 2.0) ** 2)
+    f["phi"] = np.tanh((R - r) / (math.sqrt(2.0) * W_cfg)) + uniform_noise(seed, f["phi"].shape, noise)
+    return prm, f
+
+
+def rayleigh_taylor(nx: int = 256, ny: int = 1024, variant: str = "pe1000"):
+    """2D Rayleigh-Taylor, width 1, height 4, periodic in x, free-slip walls in y.
+
+    Heavy fluid (phi = +1, rho_L = 1) over light (rho_G = 1/3, Atwood 0.5),
+    equal viscosity, Re = sqrt(g lambda^3)/nu_L = 3000 with g = lambda = 1,
+    sigma = 0, rho_ref = rho_G, W = 4 cells, interface y = 2 + 0.1 cos(2 pi x).
+    The sound speed follows the paper's RT runs, c = dx/dt_paper = 200 U_c
+    (c_s = c / sqrt 3).  ``variant="pe1000"``: Pe = 1000 (M = 1e-3) and
+    dt = 1.2e-6, about half the explicit CH limit; ``variant="paper"``:
+    Pe = 8e4 and N_t = 51200 steps per unit time.
+    """
+    dx = 1.0 / nx
+    cs = 200.0 / math.sqrt(3.0)
+    if variant == "paper":
+        M, dt = 1.0 / 8e4, 1.0 / 51200.0
+    else:
+        M, dt = 1.0e-3, 1.2e-6
+    eta = 1.0 / 3000.0
+    prm = base_params(2, nx, ny, dx=dx, dt=dt, cs=cs, rhoL=1.0, rhoG=1.0 / 3.0, etaL=eta, etaG=eta,
+                      rho_ref=1.0 / 3.0, sigma=0.0, M=M, W=4.0 * dx, g=(0.0, -1.0, 0.0),
+                      bc=("periodic", "freeslip", "periodic"))
+    f = zero_fields(prm)
+    x, y = cell_centres(prm)
+    h = 2.0 + 0.1 * np.cos(2.0 * math.pi * x)
+    f["phi"] = np.tanh(2.0 * (y - h) / prm["W"])
+    return prm, f
+
+
+def bubble3d(nx: int = 256, ny: int = 256, nz: int = 512, R: float = 32.0, gap: float = 64.0,
+             W: float = 3.0):
+    """3D buoyant bubble in a closed box (no-slip walls on all sides), dx = dt = 1.
+
+    Liquid outside (phi = +1, rho_L = 1), gas bubble inside (rho_G = 0.1),
+    viscosity ratio 10, Eotvos g drho D^2/sigma = 10 and Morton
+    g eta_L^4 drho/(rho_L^2 sigma^3) = 1e-4 with D = 2R and g = 1e-5 along -z;
+    c_s = 1/sqrt 3 (the paper's tie to dx/dt), M = 0.01, rho_ref = rho_L,
+    D3Q15 isotropic stencils and RK4 for the CH equation.  The bubble centre
+    sits ``gap + R`` cells above the bottom wall, centred in x and y.
+    """
+    rhoL, rhoG, g = 1.0, 0.1, 1e-5
+    D = 2.0 * R
+    sigma = g * (rhoL - rhoG) * D * D / 10.0
+    etaL = (1e-4 * rhoL * rhoL * sigma ** 3 / (g * (rhoL - rhoG))) ** 0.25
+    prm = base_params(3, nx, ny, nz, dx=1.0, dt=1.0, cs=1.0 / math.sqrt(3.0), rhoL=rhoL, rhoG=rhoG,
+                      etaL=etaL, etaG=etaL / 10.0, rho_ref=rhoL, sigma=sigma, M=0.01, W=W,
+                      g=(0.0, 0.0, -g), bc=("noslip", "noslip", "noslip"), ch_scheme=4, iso=15)
+    f = zero_fields(prm)
+    x, y, z = cell_centres(prm)
+    r = np.sqrt((x - nx / 2.0) ** 2 + (y - ny / 2.0) ** 2 + (z - (gap + R)) ** 2)
+    f["phi"] = -np.tanh(2.0 * (R - r) / W)
+    return prm, f
+
+
+def random_fields(prm: dict, seed: int, amp_u: float = 0.05, amp_p: float = 0.01) -> dict:
+    """A rough synthetic state for operator-level parity: phi in (-1, 1) with
+    interfaces of a few cells, velocities and pressure of the given amplitudes.
+    Wall faces of the normal velocity are zeroed."""
+    shp = shape_of(prm)
+    f = {}
+    base = uniform_noise(seed, shp, 1.0)
+    # a smooth-ish phi: tanh of a low-pass of the noise
+    sm = base.copy()
+    for ax in range(len(shp)):
+        sm = (np.roll(sm, 1, ax) + 2.0 * sm + np.roll(sm, -1, ax)) / 4.0
+    f["phi"] = np.tanh(4.0 * sm)
+    f["p"] = uniform_noise(seed + 101, shp, amp_p)
+    names = ["u", "v", "w"][: prm["dim"]]
+    for a, nm in enumerate(names):
+        vel = uniform_noise(seed + 202 + a, shp, amp_u)
+        if prm["bc"][a] != "periodic":
+            ax = len(shp) - 1 - a
+            sl = [slice(None)] * len(shp)
+            sl[ax] = 0
+            vel[tuple(sl)] = 0.0
+        f[nm] = vel
+    return f

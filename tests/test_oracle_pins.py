@@ -1,0 +1,566 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these tests re-types the oracle's stencils: each compares it with a
+closed form derived by hand from the paper's equations (Fourier symbols of
+the linearised operators, polynomial exactness, moment conditions of the
+lattice weights), with an exact solution of a reduced problem (uniform
+acceleration, 1D variable-viscosity shear, discrete flat-interface
+equilibrium, Taylor-Green decay) or with an invariant (conservation,
+translation, mirror and axis-exchange symmetry, the Laplace law).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2011_00814_gb300 import inputs
+from tests.fields import positions
+
+# ----------------------------------------------------------------------------
+# lattice weights: moment conditions (isotropy up to 4th order)
+# ----------------------------------------------------------------------------
+
+LATTICES = [(2, 9), (3, 15), (3, 19), (3, 27)]
+
+
+@pytest.mark.parametrize("dim,iso", LATTICES)
+def test_lattice_moments(dim, iso):
+    prm = inputs.base_params(dim, 4, 4, 4, iso=iso)
+    e, w = oracle.lattice_table(prm)
+    assert len(w) == iso
+    e = e[:, :dim].astype(np.float64)
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.all(np.abs(w @ e) < 1e-15)
+    second = np.einsum("q,qa,qb->ab", w, e, e)
+    assert np.allclose(second, np.eye(dim) / 3.0, atol=1e-15)
+    third = np.einsum("q,qa,qb,qc->abc", w, e, e, e)
+    assert np.all(np.abs(third) < 1e-15)
+    fourth = np.einsum("q,qa,qb,qc,qd->abcd", w, e, e, e, e)
+    d = np.eye(dim)
+    iso4 = (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+            + np.einsum("ad,bc->abcd", d, d)) / 9.0
+    assert np.allclose(fourth, iso4, atol=1e-15)
+
+
+@pytest.mark.parametrize("dim,iso", LATTICES)
+def test_iso_stencils_exact_on_polynomials(dim, iso):
+    n = 8
+    prm = inputs.base_params(dim, n, n, n, dx=0.5, iso=iso)
+    X = positions(prm, "c")
+    dx = prm["dx"]
+    xs = [c * dx for c in X]
+    coef_lin = [0.7, -1.3, 0.4][:dim]
+    lin = sum(c * x for c, x in zip(coef_lin, xs))
+    quad = sum((a + 1.0) * x * x for a, x in enumerate(xs)) + 0.5 * xs[0] * xs[1]
+    inner = tuple([slice(1, -1)] * dim)
+    g = oracle.grad_iso(prm, lin)
+    for a in range(dim):
+        assert np.allclose(g[a][inner], coef_lin[a], rtol=0, atol=1e-12)
+    gq = oracle.grad_iso(prm, quad)
+    exact = [2.0 * (a + 1.0) * xs[a] + (0.5 * xs[1] if a == 0 else 0.5 * xs[0] if a == 1 else 0.0)
+             for a in range(dim)]
+    for a in range(dim):
+        assert np.allclose(gq[a][inner], exact[a][inner], rtol=0, atol=1e-11)
+    lq = oracle.lap_iso(prm, quad)
+    lap_exact = sum(2.0 * (a + 1.0) for a in range(dim))
+    assert np.allclose(lq[inner], lap_exact, rtol=0, atol=1e-10)
+
+
+# ----------------------------------------------------------------------------
+# Fourier symbols of the linearised flow operator (uniform phi = phi0)
+# ----------------------------------------------------------------------------
+
+def _material(prm, phi0):
+    rho = 0.5 * (prm["rhoL"] * (1 + phi0) + prm["rhoG"] * (1 - phi0))
+    eta = 0.5 * (prm["etaL"] * (1 + phi0) + prm["etaG"] * (1 - phi0))
+    return rho, eta, eta / rho
+
+
+def flow_symbol(prm, theta, phi0):
+    """(d+1)x(d+1) symbol of (p, u_1..u_d) for fields q_hat exp(i theta . position).
+
+    Derived by hand from Eqs. div-v, diff-p, u-stress (a)-(d), gradp-u and
+    gradp-u-p-ave-3d with s_a = 2 i sin(theta_a / 2):
+      L_p   = -rho c^2 sum_a s_a U_a / dx + nu sum_a s_a^2 P / dx^2
+      rho L_c = -A_c s_c P / dx + eta [2 s_c^2 U_c + sum_{t!=c}(s_t^2 U_c + s_t s_c U_t)] / dx^2
+              + eta_b s_c sum_a s_a U_a / dx^2
+    with the averaging factor A_c = prod_{t != c} (4 + 2 cos theta_t) / 6.
+    """
+    d = prm["dim"]
+    dx, cs = prm["dx"], prm["cs"]
+    rho, eta, nu = _material(prm, phi0)
+    s = [2j * math.sin(t / 2.0) for t in theta]
+    A = np.zeros((d + 1, d + 1), dtype=complex)
+    A[0, 0] = nu * sum(sa * sa for sa in s) / dx ** 2
+    for a in range(d):
+        A[0, 1 + a] = -rho * cs * cs * s[a] / dx
+    etab = eta if prm["bulk_visc"] else 0.0
+    for c in range(d):
+        avg = 1.0
+        if prm["p_average"]:
+            for t in range(d):
+                if t != c:
+                    avg *= (4.0 + 2.0 * math.cos(theta[t])) / 6.0
+        A[1 + c, 0] = -avg * s[c] / dx / rho
+        A[1 + c, 1 + c] += eta * 2.0 * s[c] * s[c] / dx ** 2 / rho
+        for t in range(d):
+            if t == c:
+                continue
+            A[1 + c, 1 + c] += eta * s[t] * s[t] / dx ** 2 / rho
+            A[1 + c, 1 + t] += eta * s[t] * s[c] / dx ** 2 / rho
+        for a in range(d):
+            A[1 + c, 1 + a] += etab * s[c] * s[a] / dx ** 2 / rho
+    return A
+
+
+def rk3_amplification(hA):
+    I = np.eye(hA.shape[0])
+    return I + hA + hA @ hA / 2.0 + hA @ hA @ hA / 6.0
+
+
+def _mode_field(prm, what, amp, theta):
+    X = positions(prm, what)
+    ph = sum(t * x for t, x in zip(theta, X))
+    return np.real(amp * np.exp(1j * ph))
+
+
+FLOW_CASES = [
+    # dim, shape, phi0, bulk, pavg, theta-index triples
+    (2, (8, 8, 1), 1.0, 1, 1, [(1, 0), (1, 2), (4, 4), (3, 1)]),
+    (2, (8, 6, 1), -1.0, 1, 0, [(2, 1), (4, 3)]),
+    (2, (8, 8, 1), 0.3, 0, 1, [(1, 3), (4, 1)]),
+    (3, (8, 6, 4, ), 1.0, 1, 1, [(1, 1, 1), (4, 3, 2), (2, 0, 1)]),
+    (3, (6, 4, 8), 0.3, 0, 0, [(1, 2, 3), (3, 2, 4)]),
+]
+
+
+@pytest.mark.parametrize("dim,shape,phi0,bulk,pavg,modes", FLOW_CASES)
+def test_flow_operator_fourier_closed_form(dim, shape, phi0, bulk, pavg, modes):
+    nx, ny, nz = shape
+    prm = inputs.base_params(dim, nx, ny, nz, dx=0.5, dt=0.05, cs=1.3, rhoL=1.7, rhoG=0.4, etaL=0.05,
+                             etaG=0.02, sigma=0.02, M=0.01, W=3.0, bulk_visc=bulk, p_average=pavg)
+    n = [nx, ny, nz][:dim]
+    rng = np.random.default_rng(7)
+    eps = 1e-30
+    nsteps = 60
+    for m in modes:
+        theta = [2.0 * math.pi * m[a] / n[a] for a in range(dim)]
+        q0 = rng.normal(size=dim + 1) + 1j * rng.normal(size=dim + 1)
+        f = inputs.zero_fields(prm)
+        f["phi"][...] = phi0
+        f["p"] = _mode_field(prm, "c", eps * q0[0], theta)
+        names = "uvw"[:dim]
+        for a, nm in enumerate(names):
+            f[nm] = _mode_field(prm, nm, eps * q0[1 + a], theta)
+        st = oracle.init_state(prm, f["phi"], f["p"], f["u"], f["v"], f.get("w"))
+        out = oracle.step(prm, st, nsteps)
+        G = rk3_amplification(prm["dt"] * flow_symbol(prm, theta, phi0))
+        qN = np.linalg.matrix_power(G, nsteps) @ q0
+        scale = eps * np.max(np.abs(qN))
+        err = np.max(np.abs(out["p"] - _mode_field(prm, "c", eps * qN[0], theta))) / scale
+        for a, nm in enumerate(names):
+            err = max(err, np.max(np.abs(out[nm] - _mode_field(prm, nm, eps * qN[1 + a], theta))) / scale)
+        assert err < 1e-11, (m, err)
+        # phi stays uniform: the linearised flow does not feed back at O(eps)
+        assert np.max(np.abs(out["phi"] - phi0)) < 1e-14
+
+
+# ----------------------------------------------------------------------------
+# Fourier symbol of the linearised Cahn-Hilliard step (u = 0, sigma = 0)
+# ----------------------------------------------------------------------------
+
+def iso_laplacian_symbol(dim, iso, theta, dx):
+    """Symbol of Eq. laplacian-iso with the standard weights, summed by hand."""
+    c = [math.cos(t) for t in theta]
+    if iso == 9:
+        return 2.0 / (3.0 * dx * dx) * (2 * c[0] + 2 * c[1] + c[0] * c[1] - 5.0)
+    sc = sum(c)
+    scc = c[0] * c[1] + c[1] * c[2] + c[0] * c[2]
+    ccc = c[0] * c[1] * c[2]
+    if iso == 15:
+        return 2.0 / (3.0 * dx * dx) * (2 * sc + ccc - 7.0)
+    if iso == 19:
+        return 2.0 / (3.0 * dx * dx) * (sc + scc - 6.0)
+    return 2.0 / (9.0 * dx * dx) * (4 * sc + 2 * scc + ccc - 19.0)
+
+
+def iso_gradient_symbol_x(dim, iso, theta, dx):
+    """Symbol of the x-component of Eq. 1st-der-iso (i times a real number)."""
+    sx = math.sin(theta[0])
+    c = [math.cos(t) for t in theta]
+    if iso == 9:
+        return 1j * sx * (2.0 + c[1]) / (3.0 * dx)
+    if iso == 15:
+        return 1j * sx * (2.0 + c[1] * c[2]) / (3.0 * dx)
+    if iso == 19:
+        return 1j * sx * (1.0 + c[1] + c[2]) / (3.0 * dx)
+    return 1j * sx * (4.0 + 2.0 * c[1] + 2.0 * c[2] + c[1] * c[2]) / (9.0 * dx)
+
+
+def ch_polynomial(z, scheme):
+    if scheme == 2:
+        return 1 + z + z * z / 2
+    return 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+
+
+CH_CASES = [
+    (2, 9, 2, (8, 8, 1), [(1, 0), (2, 3), (4, 4)]),
+    (3, 15, 4, (8, 4, 6), [(1, 1, 1), (4, 2, 3), (2, 0, 1)]),
+    (3, 19, 2, (6, 6, 4), [(1, 2, 1), (3, 3, 2)]),
+    (3, 27, 4, (4, 6, 6), [(1, 1, 2), (2, 3, 3)]),
+]
+
+
+@pytest.mark.parametrize("dim,iso,scheme,shape,modes", CH_CASES)
+@pytest.mark.parametrize("phi0", [0.0, 0.6])
+def test_ch_step_fourier_closed_form(dim, iso, scheme, shape, modes, phi0):
+    nx, ny, nz = shape
+    prm = inputs.base_params(dim, nx, ny, nz, dx=1.0, dt=0.4, sigma=0.0, M=0.05, W=4.0, iso=iso,
+                             ch_scheme=scheme)
+    n = [nx, ny, nz][:dim]
+    a_ = 3.0 / (4.0 * prm["W"])
+    kappa = 3.0 * prm["W"] / 8.0
+    fpp = 4.0 * a_ * (3.0 * phi0 * phi0 - 1.0)
+    nsteps = 40
+    for m in modes:
+        theta = [2.0 * math.pi * m[a] / n[a] for a in range(dim)]
+        lam = iso_laplacian_symbol(dim, iso, theta, prm["dx"])
+        z = prm["dt"] * prm["M"] * lam * (fpp - kappa * lam)
+        gN = ch_polynomial(z, scheme) ** nsteps
+        # odd part in eps: (run(+eps) - run(-eps)) / 2 removes the even nonlinear terms
+        eps = 1e-12 if phi0 == 0.0 else 1e-6
+        res = []
+        for sgn in (1.0, -1.0):
+            f = inputs.zero_fields(prm)
+            f["phi"] = phi0 + _mode_field(prm, "c", sgn * eps * (0.8 + 0.3j), theta)
+            st = oracle.init_state(prm, f["phi"])
+            out = oracle.step(prm, st, nsteps)
+            assert np.max(np.abs(out["u"])) == 0.0  # no force acts on the flow
+            res.append(out["phi"] - phi0)
+        lin = (res[0] - res[1]) / 2.0
+        expect = _mode_field(prm, "c", eps * (0.8 + 0.3j) * gN, theta)
+        # round-off is set by the initial amplitude, so measure against it
+        scale = eps * max(abs(gN), 1.0)
+        tol = 1e-11 if phi0 == 0.0 else 1e-8
+        assert np.max(np.abs(lin - expect)) / scale < tol, (m, z)
+
+
+# ----------------------------------------------------------------------------
+# time-centred advection velocity: uniformly accelerated, density-matched flow
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,iso,scheme", [(2, 9, 2), (3, 15, 4), (3, 27, 2)])
+def test_ch_advection_uses_time_centred_velocity(dim, iso, scheme):
+    """rho_L = rho_G, eta_L = eta_G, sigma = 0: the velocity stays uniform and
+    grows linearly, u(t) = U0 + a t with a = (rho - rho_ref) g_x / rho; the
+    CH step of step n advects phi with u(t_{n+1/2}) (Eq. u-center-2d), so a
+    small phi mode is multiplied by P(z_n) with
+    z_n = -dt u(t_{n+1/2}) G_x(theta) + dt M lam (f''(0) - kappa lam)."""
+    nx, ny, nz = 8, 6, 4
+    prm = inputs.base_params(dim, nx, ny, nz, dx=1.0, dt=0.3, rhoL=1.2, rhoG=1.2, etaL=0.05, etaG=0.05,
+                             sigma=0.0, M=0.02, W=4.0, rho_ref=0.5, g=(0.02, 0.0, 0.0), iso=iso,
+                             ch_scheme=scheme)
+    n = [nx, ny, nz][:dim]
+    theta = [2.0 * math.pi * m / nn for m, nn in zip([1, 1, 1][:dim], n)]
+    U0 = 0.15
+    acc = (prm["rhoL"] - prm["rho_ref"]) * prm["g"][0] / prm["rhoL"]
+    eps = 1e-12
+    f = inputs.zero_fields(prm)
+    f["u"][...] = U0
+    f["phi"] = _mode_field(prm, "c", eps * (1.0 - 0.5j), theta)
+    st = oracle.init_state(prm, f["phi"], u=f["u"])
+    nsteps = 25
+    out = oracle.step(prm, st, nsteps)
+    dt = prm["dt"]
+    assert np.allclose(out["u"], U0 + acc * nsteps * dt, rtol=0, atol=1e-14)
+    lam = iso_laplacian_symbol(dim, iso, theta, prm["dx"])
+    Gx = iso_gradient_symbol_x(dim, iso, theta, prm["dx"])
+    a_, kappa = 3.0 / (4.0 * prm["W"]), 3.0 * prm["W"] / 8.0
+    amp = 1.0 - 0.5j
+    for k in range(nsteps):
+        uh = U0 + acc * (k + 0.5) * dt
+        z = -dt * uh * Gx + dt * prm["M"] * lam * (-4.0 * a_ - kappa * lam)
+        amp *= ch_polynomial(z, scheme)
+    expect = _mode_field(prm, "c", eps * amp, theta)
+    assert np.max(np.abs(out["phi"] - expect)) / (eps * abs(amp)) < 1e-10
+
+
+# ----------------------------------------------------------------------------
+# body force: uniform phi, the velocity grows at (rho - rho_ref) g / rho
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_gravity_uniform_acceleration(dim):
+    prm = inputs.base_params(dim, 6, 5, 4, dx=1.0, dt=0.2, rhoL=2.0, rhoG=0.5, rho_ref=0.8,
+                             g=(0.01, -0.03, 0.02), sigma=0.0)
+    phi0 = 0.25
+    f = inputs.zero_fields(prm)
+    f["phi"][...] = phi0
+    st = oracle.init_state(prm, f["phi"])
+    out = oracle.step(prm, st, 10)
+    rho, _, _ = _material(prm, phi0)
+    for a, nm in enumerate("uvw"[:dim]):
+        assert np.allclose(out[nm], (rho - prm["rho_ref"]) * prm["g"][a] / rho * 10 * prm["dt"],
+                           rtol=1e-13, atol=0)
+    assert np.max(np.abs(out["p"])) < 1e-14
+
+
+# ----------------------------------------------------------------------------
+# variable viscosity: 1D shear across a flat interface
+# ----------------------------------------------------------------------------
+
+def _flat_equilibrium(n, W, dx=1.0):
+    """Discrete equilibrium of mu = 4 a phi (phi^2 - 1) - kappa phi'' = 0 on a
+    periodic line of n cells with two interfaces at cell faces n/4 and 3n/4,
+    phi = +1 between them.  The unknowns are the cells n/4 .. n/2-1; the rest
+    follows from the symmetries (even about n/2, odd about n/4), which removes
+    the translation mode.  Plain Newton with the textbook 3-point Laplacian."""
+    a_, kappa = 3.0 / (4.0 * W), 3.0 * W / 8.0
+    q = n // 4
+    m = n // 2 - q
+
+    def expand(y):
+        full = np.empty(n)
+        full[q:q + m] = y                      # cells q .. n/2-1
+        full[q + m:q + 2 * m] = y[::-1]        # even about n/2
+        full[q - m:q] = -y[::-1]               # odd about the face q   (cells 0 .. q-1)
+        full[q + 2 * m:] = -y[: n - (q + 2 * m)]  # odd about the face 3n/4
+        return full
+
+    xs = (np.arange(q, q + m) + 0.5 - q) * dx
+    y = np.tanh(2.0 * xs / W)
+    for _ in range(60):
+        f = expand(y)
+        lap = (np.roll(f, -1) - 2 * f + np.roll(f, 1)) / dx ** 2
+        mu = 4 * a_ * f * (f * f - 1.0) - kappa * lap
+        r = mu[q:q + m]
+        J = np.zeros((m, m))
+        h = 1e-7
+        for k in range(m):
+            yp = y.copy()
+            yp[k] += h
+            fp = expand(yp)
+            lp = (np.roll(fp, -1) - 2 * fp + np.roll(fp, 1)) / dx ** 2
+            J[:, k] = ((4 * a_ * fp * (fp * fp - 1.0) - kappa * lp)[q:q + m] - r) / h
+        y = y - np.linalg.solve(J, r)
+        if np.max(np.abs(r)) < 1e-15:
+            break
+    return expand(y)
+
+
+def test_flat_interface_equilibrium_is_stationary():
+    n, W = 64, 4.0
+    prof = _flat_equilibrium(n, W)
+    # the discrete profile approaches tanh(2d/W) (Eq. chem-pot with a, kappa)
+    d = np.arange(n // 4, n // 2) + 0.5 - n // 4
+    assert np.max(np.abs(prof[n // 4:n // 2] - np.tanh(2.0 * d / W))) < 0.02
+    prm = inputs.base_params(2, n, 6, dx=1.0, dt=0.3, cs=1.0, W=W, sigma=0.05, M=0.05)
+    phi = np.tile(prof, (6, 1))
+    st = oracle.init_state(prm, phi)
+    assert np.max(np.abs(st["mu"])) < 1e-12
+    out = oracle.step(prm, st, 300)
+    assert np.max(np.abs(out["phi"] - phi)) < 1e-12
+    assert np.max(np.abs(out["u"])) < 1e-12 and np.max(np.abs(out["v"])) < 1e-12
+    assert np.max(np.abs(out["p"])) < 1e-12
+
+
+def test_variable_viscosity_shear_closed_form():
+    """phi = the flat equilibrium varying in y, u = u(y), v = p = 0: every term
+    but d/dy(eta du/dy) vanishes, so rho_j du_j/dt =
+    [eta_{j+1/2}(u_{j+1}-u_j) - eta_{j-1/2}(u_j-u_{j-1})]/dx^2 with
+    eta_{j+1/2} the mean of the two cell viscosities (the corner mean of
+    Eq. u-stress (b) reduces to it), integrated by TVD-RK3."""
+    n, W = 32, 4.0
+    prof = _flat_equilibrium(n, W)
+    prm = inputs.base_params(2, 4, n, dx=1.0, dt=0.4, cs=1.0, rhoL=1.0, rhoG=0.1, etaL=0.2, etaG=0.01,
+                             W=W, sigma=0.01, M=0.02)
+    rng = np.random.default_rng(3)
+    uy = rng.normal(size=n) * 1e-3
+    phi = np.tile(prof[:, None], (1, 4))
+    u = np.tile(uy[:, None], (1, 4))
+    st = oracle.init_state(prm, phi, u=u)
+    nsteps = 50
+    out = oracle.step(prm, st, nsteps)
+    rho = 0.5 * (prm["rhoL"] * (1 + prof) + prm["rhoG"] * (1 - prof))
+    eta = 0.5 * (prm["etaL"] * (1 + prof) + prm["etaG"] * (1 - prof))
+    A = np.zeros((n, n))
+    for j in range(n):
+        ep = 0.5 * (eta[j] + eta[(j + 1) % n])
+        em = 0.5 * (eta[j] + eta[(j - 1) % n])
+        A[j, (j + 1) % n] += ep / rho[j]
+        A[j, (j - 1) % n] += em / rho[j]
+        A[j, j] -= (ep + em) / rho[j]
+    hA = prm["dt"] * A
+    G = np.eye(n) + hA + hA @ hA / 2 + hA @ hA @ hA / 6
+    uN = np.linalg.matrix_power(G, nsteps) @ uy
+    assert np.max(np.abs(out["u"] - uN[:, None])) < 1e-12 * np.max(np.abs(uy)) + 1e-16
+    assert np.max(np.abs(out["v"])) < 1e-14
+    assert np.max(np.abs(out["phi"] - phi)) < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# invariants
+# ----------------------------------------------------------------------------
+
+def _random_state(prm, seed):
+    f = inputs.random_fields(prm, seed)
+    return oracle.init_state(prm, f["phi"], f["p"], f["u"], f["v"], f.get("w"))
+
+
+@pytest.mark.parametrize("dim,bc", [(2, ("periodic",) * 3), (2, ("noslip", "freeslip", "periodic")),
+                                    (3, ("periodic",) * 3), (3, ("freeslip", "periodic", "noslip"))])
+def test_phi_conserved_without_flow(dim, bc):
+    prm = inputs.base_params(dim, 10, 8, 6, dx=1.0, dt=0.2, sigma=0.0, M=0.05, bc=bc)
+    f = inputs.random_fields(prm, 11)
+    st = oracle.init_state(prm, f["phi"])
+    out = oracle.step(prm, st, 50)
+    s0, s1 = np.sum(st["phi"]), np.sum(out["phi"])
+    assert abs(s1 - s0) <= 1e-13 * np.sum(np.abs(st["phi"]))
+    assert np.max(np.abs(out["u"])) == 0.0
+    assert np.max(np.abs(out["phi"] - st["phi"])) > 1e-4  # it did evolve
+
+
+@pytest.mark.parametrize("dim,bc", [(2, ("periodic",) * 3), (3, ("noslip", "periodic", "freeslip"))])
+def test_phi_conserved_conservative_advection(dim, bc):
+    prm = inputs.base_params(dim, 10, 8, 6, dx=1.0, dt=0.2, cs=1.0, sigma=0.02, M=0.05, bc=bc,
+                             ch_advection=1)
+    st = _random_state(prm, 5)
+    out = oracle.step(prm, st, 30)
+    assert abs(np.sum(out["phi"]) - np.sum(st["phi"])) <= 1e-13 * np.sum(np.abs(st["phi"]))
+    assert np.max(np.abs(out["u"])) > 1e-4
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_translation_invariance_exact(dim):
+    prm = inputs.base_params(dim, 8, 6, 4, dx=1.0, dt=0.2, cs=1.0, g=(0.001, -0.002, 0.003), rho_ref=0.5)
+    st = _random_state(prm, 21)
+    shift = (1, 2, 3)[:dim][::-1]
+    axes = tuple(range(dim))
+    sh = {k: np.roll(v, shift, axes) for k, v in st.items()}
+    a = oracle.step(prm, st, 3)
+    b = oracle.step(prm, sh, 3)
+    for k in a:
+        assert np.array_equal(np.roll(a[k], shift, axes), b[k]), k
+
+
+def _mirror(prm, st, axis):
+    """Reflect the state across the plane normal to ``axis`` through the box centre."""
+    dim = prm["dim"]
+    ax = dim - 1 - axis                       # numpy axis of grid axis
+    out = {}
+    for k, v in st.items():
+        r = np.flip(v, ax)
+        if k == "uvw"[axis]:
+            # faces: new face i sits at old face n - i  (old face n == old face 0 when periodic)
+            r = -np.roll(r, 1, ax)
+            if prm["bc"][axis] != "periodic":
+                sl = [slice(None)] * dim
+                sl[ax] = 0
+                r[tuple(sl)] = 0.0
+        out[k] = r
+    return out
+
+
+def _swap(prm, st, a, b):
+    """Exchange grid axes a and b (square in those axes): fields transposed, u_a <-> u_b."""
+    dim = prm["dim"]
+    na, nb = dim - 1 - a, dim - 1 - b
+    out = {k: np.swapaxes(v, na, nb).copy() for k, v in st.items()}
+    ka, kb = "uvw"[a], "uvw"[b]
+    out[ka], out[kb] = out[kb], out[ka]
+    return out
+
+
+@pytest.mark.parametrize("dim,bc,axis", [
+    (2, ("periodic",) * 3, 0), (2, ("periodic",) * 3, 1), (2, ("noslip", "freeslip", "periodic"), 0),
+    (2, ("noslip", "freeslip", "periodic"), 1), (3, ("periodic",) * 3, 2),
+    (3, ("freeslip", "noslip", "noslip"), 0), (3, ("noslip", "noslip", "noslip"), 1)])
+def test_mirror_symmetry(dim, bc, axis):
+    prm = inputs.base_params(dim, 8, 6, 6, dx=1.0, dt=0.2, cs=1.0, bc=bc, g=(0.0, 0.0, 0.0))
+    st = _random_state(prm, 33)
+    a = _mirror(prm, oracle.step(prm, st, 3), axis)
+    b = oracle.step(prm, _mirror(prm, st, axis), 3)
+    for k in a:
+        scale = max(np.max(np.abs(b[k])), 1e-3)
+        assert np.max(np.abs(a[k] - b[k])) / scale < 1e-13, k
+
+
+@pytest.mark.parametrize("dim,bc,ab", [(2, ("periodic",) * 3, (0, 1)), (2, ("noslip", "noslip", "periodic"), (0, 1)),
+                                       (3, ("periodic",) * 3, (0, 2)), (3, ("noslip", "freeslip", "freeslip"), (1, 2))])
+def test_axis_exchange_symmetry(dim, bc, ab):
+    n = 6
+    prm = inputs.base_params(dim, n, n, n, dx=1.0, dt=0.2, cs=1.0, bc=bc)
+    st = _random_state(prm, 44)
+    a = _swap(prm, oracle.step(prm, st, 3), *ab)
+    b = oracle.step(prm, _swap(prm, st, *ab), 3)
+    for k in a:
+        scale = max(np.max(np.abs(b[k])), 1e-3)
+        assert np.max(np.abs(a[k] - b[k])) / scale < 1e-13, k
+
+
+# ----------------------------------------------------------------------------
+# Taylor-Green vortex in the single-phase limit: second-order convergence
+# ----------------------------------------------------------------------------
+
+def _taylor_green_error(N, Ma=0.02, nu=0.05, t_end=1.0):
+    L = 2.0 * math.pi
+    dx = L / N
+    U = 1.0
+    cs = U / Ma
+    dt0 = 0.4 * dx / cs
+    nsteps = int(math.ceil(t_end / dt0))
+    dt = t_end / nsteps
+    prm = inputs.base_params(2, N, N, dx=dx, dt=dt, cs=cs, rhoL=1.0, rhoG=1.0, etaL=nu, etaG=nu,
+                             sigma=0.0, M=0.0, W=4.0 * dx)
+    f = inputs.zero_fields(prm)
+    xc, yc = [c * dx for c in positions(prm, "c")]
+    xu, yu = [c * dx for c in positions(prm, "u")]
+    xv, yv = [c * dx for c in positions(prm, "v")]
+    f["phi"][...] = 1.0
+    f["u"] = U * np.sin(xu) * np.cos(yu)
+    f["v"] = -U * np.cos(xv) * np.sin(yv)
+    f["p"] = 0.25 * U * U * (np.cos(2 * xc) + np.cos(2 * yc))
+    st = oracle.init_state(prm, f["phi"], f["p"], f["u"], f["v"])
+    out = oracle.step(prm, st, nsteps)
+    dec = math.exp(-2.0 * nu * t_end)
+    eu = np.max(np.abs(out["u"] - f["u"] * dec))
+    ev = np.max(np.abs(out["v"] - f["v"] * dec))
+    return max(eu, ev) / (U * dec)
+
+
+@pytest.mark.slow
+def test_taylor_green_second_order():
+    e1 = _taylor_green_error(16)
+    e2 = _taylor_green_error(32)
+    assert e1 < 0.05
+    rate = math.log2(e1 / e2)
+    assert rate > 1.7, (e1, e2, rate)
+
+
+# ----------------------------------------------------------------------------
+# static drop (the 64 x 64 case): Laplace law
+# ----------------------------------------------------------------------------
+
+@pytest.mark.slow
+def test_static_drop_laplace_law():
+    """Laplace law for the 64 x 64 drop once its transient has settled.
+
+    With F_ST = -sigma phi grad mu the jump sits in P = p + sigma phi mu (the
+    pressure of the equivalent mu grad phi form); it must equal sigma/R_eff,
+    R_eff the radius of the phi > 0 area.  After 2000 steps the jump is still
+    in a slow transient (about 0.92 sigma/R), so the pin is taken at 8000."""
+    prm, f = inputs.static_drop()
+    st = oracle.init_state(prm, f["phi"])
+    out = oracle.step(prm, st, 8000)
+    n = prm["nx"]
+    x, y = positions(prm, "c")
+    r = np.hypot(x - n / 2, y - n / 2)
+    R_eff = math.sqrt(np.sum(out["phi"] > 0) / math.pi)
+    P = out["p"] + prm["sigma"] * out["phi"] * out["mu"]
+    dP = np.mean(P[r < 8.0]) - np.mean(P[r > 24.0])
+    assert abs(dP / (prm["sigma"] / R_eff) - 1.0) < 0.03, (dP, R_eff)
+    # spurious currents stay far below the capillary velocity sigma/eta_L
+    assert np.max(np.abs(out["u"])) < 0.01 * prm["sigma"] / prm["etaL"]
