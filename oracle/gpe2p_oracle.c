@@ -87,9 +87,11 @@ static double fac(const orc_par *P, const double *f, int c, int i, int j, int k)
       x[a] %= n;
       if (x[a] < 0) x[a] += n;
     } else if (a == c) {
-      if (x[a] == 0 || x[a] == n) return 0.0;
+      /* odd about a wall face; a mirrored index can land on the opposite
+       * wall face (n = 1), which is zero as well */
       if (x[a] < 0) { x[a] = -x[a]; s = -s; }
       else if (x[a] > n) { x[a] = 2 * n - x[a]; s = -s; }
+      if (x[a] == 0 || x[a] == n) return 0.0;
     } else {
       if (x[a] < 0) { x[a] = -1 - x[a]; if (P->bc[a] == ORC_NOSLIP) s = -s; }
       else if (x[a] >= n) { x[a] = 2 * n - 1 - x[a]; if (P->bc[a] == ORC_NOSLIP) s = -s; }
