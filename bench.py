@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of the two-phase GPE step (flow TVD-RK3 + Cahn-Hilliard RK4) on GB300.
+
+Workload: the 3D buoyant bubble, 256 x 256 x 512 cells (33.5M), FP32, no-slip
+walls, D3Q15 isotropic stencils, RK4 for the CH equation; synthetic, seeded.
+A step is one full time step of the method over the whole grid; the metric is
+cell-updates/s = cells x steps / time.  The state (about 2.7 GB) is far
+larger than L2, so no flush is needed between steps.
+
+Arms:
+  default            the CUDA library through its C ABI, inputs resident in HBM
+                     (value), plus the end-to-end number through the same
+                     API with host buffers copied in and out every step (e2e),
+                     the live roofline of the dominant kernel and the CPU
+                     oracle timed on a bounded sample (cpu_baseline).
+  --impl reference   the CPU FP64 oracle on the host cores, a bounded sample
+                     per step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+N > 1 runs N independent replicas (one per GPU, launched by torchrun); the
+value is the total over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2011_00814_gb300 import inputs  # noqa: E402
+
+METRIC = "cell-updates/s (RK3 step)"
+UNIT = "cell-updates/s"
+WORKLOAD = "3D buoyant bubble 256x256x512 FP32 (no-slip walls, D3Q15, RK4 CH)"
+
+# algorithmic words per cell of each launch kind in the 3D FP32 step
+# (reads + writes of one pass; see the measurement section of the design doc)
+WORDS = {"flow_stage1": 10, "flow_stage2": 14, "flow_stage3": 14, "ch_stage": None, "mu": 2}
+CH_WORDS_RK4 = [13, 9, 9, 8]  # CH stage 1 (builds uhat from u^n, u^{n+1}), 2, 3, 4
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("flow.cu", "gpe2p_dev.cuh", "gpe2p_launch.h"):
+        with open(os.path.join(ROOT, "paper_2011_00814_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "flow_stage_bubble3d_traffic.json")
+    try:
+        with open(p) as fh:
+            t = json.load(fh)
+        if t.get("source_sha") == source_hash():
+            return float(t["bytes_per_launch_full_grid"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(seconds=15.0, n=64):
+    """The CPU oracle, as it stands, on a bounded sample of the workload: the
+    same bubble physics in an n^3 closed box (bubble radius n/4), FP64."""
+    import oracle
+    threads = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(threads))
+    prm, f = inputs.bubble3d(n, n, n, R=n / 8.0, gap=n / 8.0)
+    st = oracle.init_state(prm, f["phi"], w=f["w"])
+    t0 = time.perf_counter()
+    st = oracle.step(prm, st, 1)
+    t1 = time.perf_counter()
+    steps = 1
+    more = int(max(0, (seconds - (t1 - t0)) / max(t1 - t0, 1e-3)))
+    if more:
+        st = oracle.step(prm, st, more)
+        steps += more
+    el = time.perf_counter() - t0
+    return {"value": n ** 3 * steps / el, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+            "kind": "oracle",
+            "sample": f"{n}^3 closed box, same bubble physics, FP64 oracle, {steps} step(s) in {el:.1f} s"}
+
+
+def dist_setup(n_gpus):
+    if n_gpus <= 1 and "WORLD_SIZE" not in os.environ:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, dist
+
+
+def run_reference(args):
+    rank, world, dist = 0, 1, None
+    if "WORLD_SIZE" in os.environ and int(os.environ["WORLD_SIZE"]) > 1:
+        if int(os.environ.get("RANK", 0)) != 0:
+            return 0
+    import oracle
+    threads = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(threads))
+    # size one step's sample so that warmup + steps end within about 2 minutes
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    n = 8
+    for cand in (64, 48, 32, 24, 16, 12, 8):
+        if cand ** 3 / 6.0e5 <= budget:
+            n = cand
+            break
+    prm, f = inputs.bubble3d(n, n, n, R=n / 8.0, gap=n / 8.0)
+    st = oracle.init_state(prm, f["phi"], w=f["w"])
+    for _ in range(args.warmup):
+        st = oracle.step(prm, st, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st = oracle.step(prm, st, 1)
+    el = time.perf_counter() - t0
+    val = n ** 3 * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{n}^3 closed box per step"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+                             "kind": "oracle", "sample": f"{n}^3 closed box, same bubble physics, FP64"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--profile-steps", type=int, default=3)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2011_00814_gb300 import build, gpe2p
+
+    rank, world, dist = dist_setup(args.gpus)
+    dev = torch.cuda.current_device()
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    gpe2p.lib()
+
+    prm, f = inputs.bubble3d()
+    prm = dict(prm, precision=32)
+    ncell = prm["nx"] * prm["ny"] * prm["nz"]
+    stream = torch.cuda.Stream()
+    solver = gpe2p.Solver(prm, stream=stream.cuda_stream)
+    solver.init_fields(f)
+
+    # live per-launch timing of eager steps (CUDA events on the handle's stream)
+    prof = solver.profile_steps(args.profile_steps)
+    names = [n for n, _ in prof]
+    launches_per_step = len(prof)
+
+    for _ in range(args.warmup):
+        solver.step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        gpu_id = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        gpu_id = None
+    with ClockSampler(gpu_id) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            solver.step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    d = solver.diagnostics()
+    value = world * ncell * args.steps / (ms / 1e3)
+
+    # end to end through the public API: pinned host inputs in, state out, every step
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy() for k, v in f.items()}
+    outb = {k: torch.empty(v.shape, dtype=torch.float64).pin_memory().numpy() for k, v in f.items()}
+    lib = gpe2p.lib()
+    dptr = gpe2p._dptr
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        solver._check(lib.gpe2p_init_fields(solver.h, dptr(pin["phi"]), dptr(pin["u"]), dptr(pin["v"]),
+                                            dptr(pin["w"]), dptr(pin["p"])))
+        solver.step()
+        solver._check(lib.gpe2p_read_fields(solver.h, dptr(outb["phi"]), dptr(outb["u"]), dptr(outb["v"]),
+                                            dptr(outb["w"]), dptr(outb["p"]), None))
+    e2e_s = time.perf_counter() - t0
+    e2e_val = world * ncell * args.e2e_steps / e2e_s
+    solver.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel (the flow stage with the q^n combine)
+    peak, peak_kind = load_peaks()
+    by_name = {}
+    for n, t in prof:
+        by_name.setdefault(n, []).append(t)
+    step_ms = sum(t for _, t in prof)
+    share = {n: sum(v) / step_ms for n, v in by_name.items()}
+    dom = "flow_stage2"
+    dom_ms = statistics.mean(by_name["flow_stage2"] + by_name["flow_stage3"])
+    dom_bytes = WORDS["flow_stage2"] * 4 * ncell
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    words_step = (WORDS["flow_stage1"] + WORDS["flow_stage2"] + WORDS["flow_stage3"] + sum(CH_WORDS_RK4)
+                  + 4 * WORDS["mu"])
+    step_gbs = words_step * 4 * ncell / (ms / args.steps / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": ncell, "precision": "fp32", "ch_scheme": "RK4",
+                   "iso": "D3Q15", "l2": "state ~2.7 GB > L2 (no flush needed)",
+                   "parallelism": f"{world} independent replica(s)"},
+        "roofline": {"bound": "hbm", "kernel": "flow_stage_kernel<float,3,combine> (RK3 stages 2 and 3)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "traffic": stored_traffic(),
+                     "algorithmic_bytes_per_launch": dom_bytes,
+                     "step_algorithmic_gbs": step_gbs, "step_frac": step_gbs / peak,
+                     "shares": {k: round(v, 4) for k, v in share.items()}},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 5 * 8 * ncell,
+                "d2h_bytes_per_step": 5 * 8 * ncell, "steps": args.e2e_steps},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+        "diag": {"int_phi": d["int_phi"], "umax": d["umax"], "nan": d["nan_flag"]},
+    }
+    if not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

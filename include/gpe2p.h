@@ -1,0 +1,169 @@
+/*
+ * gpe2p.h -- C ABI of the GB300 two-phase general-pressure-equation solver.
+ *
+ * Method: Huang, "A fully explicit method for two-phase incompressible flows
+ * based on the general pressure equation" (arXiv 2011.00814).  One time step
+ * is the TVD-RK3 update (Eq. tvd-rk3) of pressure and velocity on the
+ * staggered grid of Sec. 3, with the pressure equation of
+ * Eq. gpe-pressure-two-phase, the momentum equation of
+ * Eq. gpe-momentum-two-phase-const-bf (stress with bulk viscosity,
+ * Eq. vis-stress-two-phase; surface tension -sigma phi grad mu; gravity
+ * (rho - rho_ref) g), phi and mu frozen at t^{n+1/2}; followed by one
+ * Cahn-Hilliard step (Eqs. che, chem-pot) with the isotropic stencils of
+ * Eqs. 1st-der-iso and laplacian-iso, TVD-RK2 (Eq. tvd-rk2) or RK4
+ * (Eq. rk4), advected by the time-centred cell velocity of Eq. u-center-2d.
+ *
+ * Layout (all host and device arrays): one array of nx*ny*nz values per field,
+ * x fastest, then y, then z (nz = 1 in 2D).  p, phi and mu are cell averages
+ * at cell centres; the velocity component along axis c is stored on the face
+ * of each cell on its LOW side along c (u[i,j] at x = i dx, v[i,j] at
+ * y = j dx).  On a wall axis the face with index 0 is the wall itself: its
+ * normal velocity is zero and is never updated; the opposite wall face
+ * (index n) is implicit.  Boundary ghosts: p, phi, mu even; tangential
+ * velocity odd (no-slip) or even (free-slip).
+ *
+ * p is the pressure deviation from the uniform reference pressure (only its
+ * differences enter the method, Sec. 4), so the solver stores and returns it
+ * as given; a run started from p = 0 holds p - p_ref.
+ *
+ * Errors: every call returns a gpe2p_status; nothing aborts.  The text of the
+ * last error of a handle is returned by gpe2p_last_error.  A handle is not
+ * thread-safe: calls on one handle must not run concurrently.
+ * Ownership: the handle owns all device memory it allocates (released by
+ * gpe2p_destroy); host arrays passed in stay owned by the caller and are only
+ * accessed during the call.
+ */
+#ifndef GPE2P_H
+#define GPE2P_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GPE2P_OK = 0,
+  GPE2P_EINVAL = 1,     /* bad argument (size, parameter, pointer, dimension) */
+  GPE2P_EUNSTABLE = 2,  /* dt beyond an explicit stability limit (check_stability = 1) */
+  GPE2P_ENOMEM = 3,     /* device or pinned host allocation failed */
+  GPE2P_ECUDA = 4,      /* a CUDA runtime call or kernel launch failed */
+  GPE2P_EDIVERGED = 5,  /* NaN/Inf found in the state by the diagnostics */
+  GPE2P_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+  GPE2P_ESTATE = 7      /* call out of order (e.g. step before init_fields) */
+} gpe2p_status;
+
+enum { GPE2P_PERIODIC = 0, GPE2P_NOSLIP = 1, GPE2P_FREESLIP = 2 };
+
+/* Parameters of one problem (Sec. 2, Sec. 4).  Physical units are the
+ * caller's; the method is dimensional. */
+typedef struct {
+  int dim;                 /* 2 or 3 */
+  int nx, ny, nz;          /* cells per axis, each in [1, 65536]; nz = 1 in 2D */
+  double dx, dt, cs;       /* mesh size, time step, sound speed c_s (Eq. gpe-pressure) */
+  double rhoL, rhoG;       /* densities at phi = +1 / -1 (Eq. density-viscosity-op-two-phase) */
+  double etaL, etaG;       /* dynamic viscosities at phi = +1 / -1 */
+  double rho_ref;          /* reference density of the hydrostatic split (Sec. 2) */
+  double sigma;            /* physical surface tension; F_ST = -sigma phi grad mu */
+  double M;                /* mobility of Eq. che */
+  double W;                /* interface width: a = 3/(4W), kappa = 3W/8 (Eq. chem-pot) */
+  double g[3];             /* constant body force per unit mass */
+  int bc[3];               /* per axis (both sides): GPE2P_PERIODIC / NOSLIP / FREESLIP */
+  int precision;           /* 32 (FP32 storage and arithmetic) or 64 */
+  int ch_scheme;           /* 2: TVD-RK2 (Eq. tvd-rk2), 4: classic RK4 (Eq. rk4) */
+  int iso;                 /* isotropic stencil lattice: 9 (2D), 15, 19, 27 (3D) */
+  int bulk_visc;           /* 1: eta_b = eta (Sec. 2, the paper's choice); 0: eta_b = 0 */
+  int p_average;           /* 1: averaged pressure in grad p (Eqs. gradp-u-*), 0: plain */
+  int ch_advection;        /* 0: u.grad(phi) as in Eq. che; 1: div(u phi) (conservative) */
+  int check_stability;     /* 1: gpe2p_create refuses dt beyond gpe2p_stability_limits */
+  int diag_every;          /* gpe2p_advance: check for NaN/Inf every this many steps (0: at the end) */
+} gpe2p_params;
+
+typedef struct gpe2p_ctx *gpe2p_handle;
+
+/* Scalar diagnostics of the current state (FP64 reductions in any precision). */
+typedef struct {
+  double int_phi;     /* sum over cells of phi dx^dim */
+  double kinetic;     /* 1/2 sum over faces of rho_face u^2 dx^dim */
+  double umax;        /* max over faces of |velocity component| */
+  int nan_flag;       /* 1 if any of p, phi or a velocity component is NaN or Inf */
+  long long step;     /* steps taken since gpe2p_init_fields */
+  double t;           /* step * dt */
+} gpe2p_diag;
+
+/* Explicit stability limits of dt for the parameters: out[0] acoustic
+ * (RK3 imaginary-axis limit sqrt 3 against the staggered acoustic operator,
+ * with the pressure averaging), out[1] viscous (RK3 real-axis limit against
+ * the largest shear + bulk viscous and pressure-diffusion eigenvalue),
+ * out[2] Cahn-Hilliard (RK2/RK4 real-axis limit against M lam (8a + kappa lam),
+ * lam the largest magnitude of the isotropic Laplacian symbol).  Host-only;
+ * needs no GPU.  Returns GPE2P_EINVAL on bad parameters. */
+int gpe2p_stability_limits(const gpe2p_params *p, double out_dt_max[3]);
+
+/* Validates p, allocates the device state on the current CUDA device and
+ * creates the handle.  stream: a cudaStream_t to run on, or NULL for a
+ * stream the handle creates (non-blocking).  The state is undefined until
+ * gpe2p_init_fields. */
+int gpe2p_create(const gpe2p_params *p, void *stream, gpe2p_handle *out);
+
+/* Sets the state from host arrays (nx*ny*nz doubles each, layout above):
+ * phi, u, v and p are required, w is required in 3D and ignored in 2D.
+ * Wall faces of the normal velocity are set to zero.  mu is computed from
+ * phi (Eq. chem-pot); phi is taken as phi^{1/2} of the time-staggered scheme
+ * (Sec. 3).  Resets the step counter.  Synchronises the handle's stream. */
+int gpe2p_init_fields(gpe2p_handle h, const double *phi, const double *u, const double *v,
+                      const double *w, const double *p);
+
+/* Advances one full step (flow TVD-RK3 + CH step), asynchronously on the
+ * handle's stream.  The first call on a handle captures the step into CUDA
+ * graphs and should come before any capture the caller runs on the stream. */
+int gpe2p_step(gpe2p_handle h);
+
+/* Advances nsteps full steps by replaying the captured step graphs; checks
+ * for NaN/Inf every diag_every steps and at the end (GPE2P_EDIVERGED if
+ * found: the state is left as it was at that check and stays readable).
+ * If last != NULL it receives the diagnostics at the end.  Synchronises. */
+int gpe2p_advance(gpe2p_handle h, long long nsteps, gpe2p_diag *last);
+
+/* Copies the state to host arrays (nx*ny*nz doubles each).  Any pointer
+ * may be NULL to skip that field; w is ignored in 2D.  Synchronises. */
+int gpe2p_read_fields(gpe2p_handle h, double *phi, double *u, double *v, double *w, double *p,
+                      double *mu);
+
+/* Diagnostics of the current state (see gpe2p_diag).  Synchronises. */
+int gpe2p_diagnostics(gpe2p_handle h, gpe2p_diag *out);
+
+/* Semi-discrete rates of the current state, for operator-level checks:
+ * Lp, Lu, Lv, Lw the right-hand sides of the flow equations
+ * (Eq. p-u-v-semidiscrete-2d; zero on wall faces) and Lphi the CH rate
+ * -uhat.grad(phi) + M lap(mu) (Eq. che) with uhat the cell average of the
+ * current face velocities.  Host arrays of nx*ny*nz doubles; any may be
+ * NULL; Lw is ignored in 2D.  Synchronises. */
+int gpe2p_eval_rates(gpe2p_handle h, double *Lp, double *Lu, double *Lv, double *Lw, double *Lphi);
+
+/* Measurement aid: advances nsteps full steps launched eagerly (not from
+ * the graphs), timing every kernel launch of a step with CUDA events on the
+ * handle's stream.  ms[i] receives the mean duration in milliseconds of the
+ * i-th launch of a step (i < max_launches), *nlaunches the launches per step,
+ * names (if not NULL) a comma-separated list of their kernel names, truncated
+ * to names_len bytes.  The state advances exactly as with gpe2p_advance.
+ * Synchronises. */
+int gpe2p_profile_steps(gpe2p_handle h, int nsteps, double *ms, int max_launches, int *nlaunches,
+                        char *names, int names_len);
+
+/* Device pointer of a field of the current state, in the handle's precision
+ * (float or double), layout above: which = 0 p, 1 u, 2 v, 3 w, 4 phi, 5 mu.
+ * Valid until the next call that advances, re-initialises or destroys the
+ * handle. */
+int gpe2p_field_ptr(gpe2p_handle h, int which, void **dptr);
+
+/* Text of the handle's last error ("" if none); with h == NULL, the last
+ * error of a failed gpe2p_create on this thread. */
+const char *gpe2p_last_error(gpe2p_handle h);
+
+/* Releases the handle and its device memory.  NULL is ignored. */
+void gpe2p_destroy(gpe2p_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPE2P_H */

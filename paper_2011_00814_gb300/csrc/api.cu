@@ -1,0 +1,709 @@
+// api.cu -- host side of the C ABI declared in include/gpe2p.h: parameter
+// validation, explicit stability limits, device state, the step as a
+// sequence of kernels captured into CUDA graphs, host I/O and diagnostics.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/gpe2p.h"
+#include "gpe2p_launch.h"
+
+using namespace gpe2p;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+enum { FLD_P = 0, FLD_U = 1, FLD_V = 2, FLD_W = 3 };
+
+}  // namespace
+
+struct gpe2p_ctx {
+  gpe2p_params prm;
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  long long ncell = 0;
+  int esize = 8;
+  char* base = nullptr;         // one device allocation holds the whole state
+  void* Q[3][4] = {};           // three sets of (p, u, v, w): q^n, stage, stage
+  void* phi = nullptr;          // phi^{n+1/2}
+  void* mu = nullptr;           // mu(phi^{n+1/2})
+  void* phis[2] = {};           // CH stage states
+  void* mus = nullptr;          // mu of a CH stage state
+  void* acc = nullptr;          // RK4 accumulator
+  void* uh[3] = {};             // time-centred cell velocity
+  double* d_stage = nullptr;    // one FP64 field for host transfers
+  double* d_part = nullptr;     // reduction scratch: 4 doubles per block
+  double* d_out = nullptr;      // 4 reduced values
+  double* h_out = nullptr;      // pinned copy of d_out
+  int nblk = 0;
+  int cur = 0;                  // which Q set holds q^n (0 or 1)
+  long long step = 0;
+  int kchunk = 8;
+  bool initialized = false;
+  bool have_graph = false;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  std::string err;
+};
+
+static int fail(gpe2p_ctx* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+static int cuda_fail(gpe2p_ctx* h, cudaError_t e, const char* what) {
+  return fail(h, GPE2P_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call, what)                            \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// validation and stability limits
+// ---------------------------------------------------------------------------
+
+static bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+static int validate(const gpe2p_params* p, std::string& why) {
+  if (!p) { why = "params is NULL"; return GPE2P_EINVAL; }
+  if (p->dim != 2 && p->dim != 3) { why = "dim must be 2 or 3"; return GPE2P_EINVAL; }
+  const int nz = p->dim == 3 ? p->nz : 1;
+  if (p->nx < 1 || p->ny < 1 || nz < 1 || p->nx > 65536 || p->ny > 65536 || nz > 65536) {
+    why = "nx, ny, nz must lie in [1, 65536]";
+    return GPE2P_EINVAL;
+  }
+  if ((double)p->nx * p->ny * nz > 4.0e9) { why = "more than 4e9 cells"; return GPE2P_EINVAL; }
+  if (!finite_pos(p->dx) || !finite_pos(p->dt) || !finite_pos(p->cs)) {
+    why = "dx, dt and cs must be finite and positive";
+    return GPE2P_EINVAL;
+  }
+  if (!finite_pos(p->rhoL) || !finite_pos(p->rhoG)) { why = "densities must be positive"; return GPE2P_EINVAL; }
+  if (!std::isfinite(p->etaL) || !std::isfinite(p->etaG) || p->etaL < 0 || p->etaG < 0) {
+    why = "viscosities must be finite and non-negative";
+    return GPE2P_EINVAL;
+  }
+  if (!std::isfinite(p->sigma) || p->sigma < 0 || !std::isfinite(p->M) || p->M < 0) {
+    why = "sigma and M must be finite and non-negative";
+    return GPE2P_EINVAL;
+  }
+  if (!finite_pos(p->W)) { why = "W must be finite and positive"; return GPE2P_EINVAL; }
+  if (!std::isfinite(p->rho_ref) || !std::isfinite(p->g[0]) || !std::isfinite(p->g[1]) ||
+      !std::isfinite(p->g[2])) {
+    why = "rho_ref and g must be finite";
+    return GPE2P_EINVAL;
+  }
+  for (int a = 0; a < p->dim; ++a)
+    if (p->bc[a] < 0 || p->bc[a] > 2) { why = "bc must be PERIODIC, NOSLIP or FREESLIP"; return GPE2P_EINVAL; }
+  if (p->precision != 32 && p->precision != 64) { why = "precision must be 32 or 64"; return GPE2P_EINVAL; }
+  if (p->ch_scheme != 2 && p->ch_scheme != 4) { why = "ch_scheme must be 2 or 4"; return GPE2P_EINVAL; }
+  if (p->dim == 2 && p->iso != 9) { why = "2D needs iso = 9 (D2Q9)"; return GPE2P_EINVAL; }
+  if (p->dim == 3 && p->iso != 15 && p->iso != 19 && p->iso != 27) {
+    why = "3D needs iso = 15, 19 or 27";
+    return GPE2P_EINVAL;
+  }
+  if ((p->bulk_visc | p->p_average | p->ch_advection | p->check_stability) & ~1) {
+    why = "bulk_visc, p_average, ch_advection and check_stability are 0 or 1";
+    return GPE2P_EINVAL;
+  }
+  if (p->diag_every < 0) { why = "diag_every must be >= 0"; return GPE2P_EINVAL; }
+  return GPE2P_OK;
+}
+
+// largest magnitude of the isotropic Laplacian symbol (times dx^2), by scan
+static double iso_lambda_max(int dim, int iso) {
+  double w0, w1, w2 = 0.0, w3 = 0.0;
+  if (iso == 9) { w0 = 4.0 / 9; w1 = 1.0 / 9; w2 = 1.0 / 36; }
+  else if (iso == 15) { w0 = 2.0 / 9; w1 = 1.0 / 9; w3 = 1.0 / 72; }
+  else if (iso == 19) { w0 = 1.0 / 3; w1 = 1.0 / 18; w2 = 1.0 / 36; }
+  else { w0 = 8.0 / 27; w1 = 2.0 / 27; w2 = 1.0 / 54; w3 = 1.0 / 216; }
+  const int N = 24;
+  double best = 0.0;
+  for (int a = 0; a <= N; ++a)
+    for (int b = 0; b <= N; ++b)
+      for (int c = 0; c <= (dim == 3 ? N : 0); ++c) {
+        const double t[3] = {M_PI * a / N, M_PI * b / N, M_PI * c / N};
+        double s = 0.0;
+        for (int ez = (dim == 3 ? -1 : 0); ez <= (dim == 3 ? 1 : 0); ++ez)
+          for (int ey = -1; ey <= 1; ++ey)
+            for (int ex = -1; ex <= 1; ++ex) {
+              const int sh = ex * ex + ey * ey + ez * ez;
+              const double w = sh == 0 ? 0.0 : (sh == 1 ? w1 : (sh == 2 ? w2 : w3));
+              s += w * std::cos(t[0] * ex + t[1] * ey + t[2] * ez);
+            }
+        const double lam = 6.0 * (s - (1.0 - w0));
+        if (-lam > best) best = -lam;
+      }
+  return best;
+}
+
+extern "C" int gpe2p_stability_limits(const gpe2p_params* p, double out[3]) {
+  std::string why;
+  int rc = validate(p, why);
+  if (rc != GPE2P_OK) return fail(nullptr, rc, why);
+  if (!out) return fail(nullptr, GPE2P_EINVAL, "out is NULL");
+  const int d = p->dim;
+  const double dx = p->dx;
+  // acoustic: omega^2 = cs^2 (4/dx^2) sum_a sin^2(t_a/2) A_a(t), A_a the
+  // product of the transverse averaging factors (4 + 2 cos t)/6
+  double amax = 0.0;
+  const int N = 32;
+  for (int a = 0; a <= N; ++a)
+    for (int b = 0; b <= N; ++b)
+      for (int c = 0; c <= (d == 3 ? N : 0); ++c) {
+        const double t[3] = {M_PI * a / N, M_PI * b / N, M_PI * c / N};
+        double s = 0.0;
+        for (int x = 0; x < d; ++x) {
+          double A = 1.0;
+          if (p->p_average)
+            for (int y = 0; y < d; ++y)
+              if (y != x) A *= (4.0 + 2.0 * std::cos(t[y])) / 6.0;
+          const double sn = std::sin(t[x] / 2.0);
+          s += sn * sn * A;
+        }
+        if (s > amax) amax = s;
+      }
+  const double omega = p->cs * 2.0 / dx * std::sqrt(amax);
+  out[0] = std::sqrt(3.0) / omega;
+  // viscous: the largest kinematic viscosity of the two phases against
+  // 4/dx^2 times (2 + bulk + (d - 1)) for momentum and d for pressure diffusion
+  const double nuL = p->etaL / p->rhoL, nuG = p->etaG / p->rhoG;
+  const double nu = nuL > nuG ? nuL : nuG;
+  double fac = 2.0 + (p->bulk_visc ? 1.0 : 0.0) + (d - 1);
+  if (fac < d) fac = d;
+  const double lv = nu * 4.0 * fac / (dx * dx);
+  out[1] = lv > 0.0 ? 2.5127 / lv : INFINITY;  // RK3 real-axis limit
+  // Cahn-Hilliard: |z| = dt M lam (8a + kappa lam) with f'' <= 8a on |phi| <= 1
+  const double a = 3.0 / (4.0 * p->W), kappa = 3.0 * p->W / 8.0;
+  const double lam = iso_lambda_max(d, p->iso) / (dx * dx);
+  const double lc = p->M * lam * (8.0 * a + kappa * lam);
+  const double lim = p->ch_scheme == 2 ? 2.0 : 2.7853;  // RK2 / RK4 real-axis limits
+  out[2] = lc > 0.0 ? lim / lc : INFINITY;
+  return GPE2P_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernel parameters
+// ---------------------------------------------------------------------------
+
+template <typename real>
+static KParams<real> kparams(const gpe2p_params& p) {
+  KParams<real> P{};
+  P.n[0] = p.nx;
+  P.n[1] = p.ny;
+  P.n[2] = p.dim == 3 ? p.nz : 1;
+  P.bc[0] = p.bc[0];
+  P.bc[1] = p.bc[1];
+  P.bc[2] = p.dim == 3 ? p.bc[2] : BC_PERIODIC;
+  P.sy = p.nx;
+  P.sz = (long long)p.nx * p.ny;
+  P.dt = (real)p.dt;
+  P.inv_dx = (real)(1.0 / p.dx);
+  P.inv_dx2 = (real)(1.0 / (p.dx * p.dx));
+  P.inv_2dx = (real)(1.0 / (2.0 * p.dx));
+  P.cs2 = (real)(p.cs * p.cs);
+  P.rhoL = (real)p.rhoL;
+  P.rhoG = (real)p.rhoG;
+  P.etaL = (real)p.etaL;
+  P.etaG = (real)p.etaG;
+  P.rho_ref = (real)p.rho_ref;
+  P.sigma = (real)p.sigma;
+  P.M = (real)p.M;
+  const double a = 3.0 / (4.0 * p.W);
+  P.a4 = (real)(4.0 * a);
+  P.kappa = (real)(3.0 * p.W / 8.0);
+  for (int c = 0; c < 3; ++c) P.g[c] = (real)p.g[c];
+  P.bulk = p.bulk_visc;
+  P.pavg = p.p_average;
+  double w0, w1, w2 = 0.0, w3 = 0.0;
+  if (p.iso == 9) { w0 = 4.0 / 9.0; w1 = 1.0 / 9.0; w2 = 1.0 / 36.0; }
+  else if (p.iso == 15) { w0 = 2.0 / 9.0; w1 = 1.0 / 9.0; w3 = 1.0 / 72.0; }
+  else if (p.iso == 19) { w0 = 1.0 / 3.0; w1 = 1.0 / 18.0; w2 = 1.0 / 36.0; }
+  else { w0 = 8.0 / 27.0; w1 = 2.0 / 27.0; w2 = 1.0 / 54.0; w3 = 1.0 / 216.0; }
+  P.w1 = (real)w1;
+  P.w2 = (real)w2;
+  P.w3 = (real)w3;
+  P.one_m_w0 = (real)(1.0 - w0);
+  P.lap_c = (real)(6.0 / (p.dx * p.dx));
+  P.grad_c = (real)(3.0 / p.dx);
+  return P;
+}
+
+// ---------------------------------------------------------------------------
+// one step: three flow stages, then the CH stages
+// ---------------------------------------------------------------------------
+
+// Per-launch timing hook of gpe2p_profile_steps: when set, an event is
+// recorded before the first launch and after every launch of a step.
+struct ProfHook {
+  cudaEvent_t* ev = nullptr;
+  int n = 0;
+  int max = 0;
+  const char** names = nullptr;
+};
+
+template <typename real, int DIM>
+static cudaError_t enqueue_step(gpe2p_ctx* h, int cur, ProfHook* hook = nullptr) {
+  const KParams<real> P = kparams<real>(h->prm);
+  cudaStream_t s = h->stream;
+  auto mark = [&](const char* name) -> cudaError_t {
+    if (!hook) return cudaSuccess;
+    if (hook->n >= hook->max) return cudaErrorInvalidValue;
+    hook->names[hook->n] = name;
+    return cudaEventRecord(hook->ev[++hook->n], s);
+  };
+  if (hook) {
+    hook->n = 0;
+    cudaError_t e0 = cudaEventRecord(hook->ev[0], s);
+    if (e0 != cudaSuccess) return e0;
+  }
+  const int s1 = 1 - cur, s2 = 2;
+  auto q = [&](int set, int f) { return (real*)h->Q[set][f]; };
+  FlowArgs<real> A{};
+  for (int f = 0; f < 4; ++f) {
+    A.q0[f] = q(cur, f);
+    A.q[f] = q(cur, f);
+    A.out[f] = q(s1, f);
+  }
+  A.phi = (const real*)h->phi;
+  A.mu = (const real*)h->mu;
+  A.a = real(0);
+  A.b = real(1);
+  cudaError_t e = launch_flow_stage<real, DIM>(P, A, 1, h->kchunk, s);
+  if (e != cudaSuccess || (e = mark("flow_stage1")) != cudaSuccess) return e;
+  for (int f = 0; f < 4; ++f) { A.q[f] = q(s1, f); A.out[f] = q(s2, f); }
+  A.a = real(0.75);
+  A.b = real(0.25);
+  if ((e = launch_flow_stage<real, DIM>(P, A, 2, h->kchunk, s)) != cudaSuccess) return e;
+  if ((e = mark("flow_stage2")) != cudaSuccess) return e;
+  for (int f = 0; f < 4; ++f) { A.q[f] = q(s2, f); A.out[f] = q(s1, f); }
+  A.a = real(1.0 / 3.0);
+  A.b = real(2.0 / 3.0);
+  if ((e = launch_flow_stage<real, DIM>(P, A, 2, h->kchunk, s)) != cudaSuccess) return e;
+  if ((e = mark("flow_stage3")) != cudaSuccess) return e;
+
+  // Cahn-Hilliard step with the time-centred velocity of Eq. u-center-2d
+  CHArgs<real> C{};
+  for (int a = 0; a < 3; ++a) {
+    C.uh[a] = (real*)h->uh[a];
+    C.u0[a] = q(cur, 1 + a);
+    C.u1[a] = q(s1, 1 + a);
+  }
+  C.scheme = h->prm.ch_scheme;
+  C.conservative = h->prm.ch_advection;
+  C.acc = (real*)h->acc;
+  C.phin = (const real*)h->phi;
+  if (C.conservative) {
+    const real* u0[3] = {C.u0[0], C.u0[1], C.u0[2]};
+    const real* u1[3] = {C.u1[0], C.u1[1], C.u1[2]};
+    real* uh[3] = {C.uh[0], C.uh[1], C.uh[2]};
+    if ((e = launch_center_velocity<real, DIM>(P, u0, u1, uh, s)) != cudaSuccess) return e;
+    if ((e = mark("center_velocity")) != cudaSuccess) return e;
+  }
+  real* phi = (real*)h->phi;
+  real* mu = (real*)h->mu;
+  real* F0 = (real*)h->phis[0];
+  real* F1 = (real*)h->phis[1];
+  real* MS = (real*)h->mus;
+  const int iso = h->prm.iso;
+  if (C.scheme == 2) {
+    C.stage = 1; C.phis = phi; C.mus = mu; C.out = F0; C.compute_uh = !C.conservative;
+    if ((e = launch_ch_stage<real, DIM>(P, C, iso, h->kchunk, s)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
+    if ((e = launch_mu<real, DIM>(P, F0, MS, iso, h->kchunk, s)) != cudaSuccess || (e = mark("mu")) != cudaSuccess) return e;
+    C.stage = 2; C.phis = F0; C.mus = MS; C.out = phi; C.compute_uh = 0;
+    if ((e = launch_ch_stage<real, DIM>(P, C, iso, h->kchunk, s)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
+  } else {
+    C.stage = 1; C.phis = phi; C.mus = mu; C.out = F0; C.compute_uh = !C.conservative;
+    if ((e = launch_ch_stage<real, DIM>(P, C, iso, h->kchunk, s)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
+    if ((e = launch_mu<real, DIM>(P, F0, MS, iso, h->kchunk, s)) != cudaSuccess || (e = mark("mu")) != cudaSuccess) return e;
+    C.stage = 2; C.phis = F0; C.mus = MS; C.out = F1; C.compute_uh = 0;
+    if ((e = launch_ch_stage<real, DIM>(P, C, iso, h->kchunk, s)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
+    if ((e = launch_mu<real, DIM>(P, F1, MS, iso, h->kchunk, s)) != cudaSuccess || (e = mark("mu")) != cudaSuccess) return e;
+    C.stage = 3; C.phis = F1; C.mus = MS; C.out = F0;
+    if ((e = launch_ch_stage<real, DIM>(P, C, iso, h->kchunk, s)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
+    if ((e = launch_mu<real, DIM>(P, F0, MS, iso, h->kchunk, s)) != cudaSuccess || (e = mark("mu")) != cudaSuccess) return e;
+    C.stage = 4; C.phis = F0; C.mus = MS; C.out = phi;
+    if ((e = launch_ch_stage<real, DIM>(P, C, iso, h->kchunk, s)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
+  }
+  if ((e = launch_mu<real, DIM>(P, phi, mu, iso, h->kchunk, s)) != cudaSuccess) return e;
+  return mark("mu");
+}
+
+static cudaError_t enqueue(gpe2p_ctx* h, int cur, ProfHook* hook = nullptr) {
+  if (h->esize == 4)
+    return h->prm.dim == 2 ? enqueue_step<float, 2>(h, cur, hook) : enqueue_step<float, 3>(h, cur, hook);
+  return h->prm.dim == 2 ? enqueue_step<double, 2>(h, cur, hook) : enqueue_step<double, 3>(h, cur, hook);
+}
+
+static int build_graphs(gpe2p_ctx* h) {
+  for (int c = 0; c < 2; ++c) {
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed), "begin capture");
+    cudaError_t e = enqueue(h, c);
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(h, e, "enqueue step");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(h, e2, "end capture");
+    e = cudaGraphInstantiate(&h->gexec[c], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+  }
+  h->have_graph = true;
+  return GPE2P_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+extern "C" int gpe2p_create(const gpe2p_params* p, void* stream, gpe2p_handle* out) {
+  std::string why;
+  if (!out) return fail(nullptr, GPE2P_EINVAL, "out is NULL");
+  *out = nullptr;
+  int rc = validate(p, why);
+  if (rc != GPE2P_OK) return fail(nullptr, rc, why);
+  if (p->check_stability) {
+    double lim[3];
+    gpe2p_stability_limits(p, lim);
+    const char* nm[3] = {"acoustic", "viscous", "Cahn-Hilliard"};
+    for (int i = 0; i < 3; ++i)
+      if (p->dt > lim[i] * (1.0 + 1e-12)) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "dt = %.6g exceeds the %s limit %.6g", p->dt, nm[i], lim[i]);
+        return fail(nullptr, GPE2P_EUNSTABLE, buf);
+      }
+  }
+  gpe2p_ctx* h = new (std::nothrow) gpe2p_ctx();
+  if (!h) return fail(nullptr, GPE2P_ENOMEM, "host allocation failed");
+  h->prm = *p;
+  if (h->prm.dim == 2) { h->prm.nz = 1; h->prm.bc[2] = GPE2P_PERIODIC; }
+  h->esize = p->precision == 32 ? 4 : 8;
+  h->ncell = (long long)h->prm.nx * h->prm.ny * h->prm.nz;
+  cudaError_t e = cudaGetDevice(&h->dev);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(nullptr, GPE2P_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  }
+  if (stream) {
+    h->stream = (cudaStream_t)stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete h;
+      return fail(nullptr, GPE2P_ECUDA, std::string("stream create: ") + cudaGetErrorString(e));
+    }
+    h->own_stream = true;
+  }
+  // layout: 12 velocity/pressure fields, phi, mu, 2 stage phi, mus, acc, 3 uhat
+  const size_t fb = align256((size_t)h->ncell * h->esize);
+  const int nfield = 12 + 2 + 2 + 1 + 1 + 3;
+  const size_t stage_b = align256((size_t)h->ncell * sizeof(double));
+  const long long nb_blocks = (h->ncell + 255) / 256;
+  h->nblk = (int)(nb_blocks < 152 * 8 ? nb_blocks : 152 * 8);
+  const size_t part_b = align256((size_t)h->nblk * 4 * sizeof(double));
+  const size_t out_b = align256(4 * sizeof(double));
+  const size_t total = fb * nfield + stage_b + part_b + out_b;
+  e = cudaMalloc((void**)&h->base, total);
+  if (e != cudaSuccess) {
+    gpe2p_destroy(h);
+    return fail(nullptr, GPE2P_ENOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
+  }
+  char* c = h->base;
+  for (int s = 0; s < 3; ++s)
+    for (int f = 0; f < 4; ++f) { h->Q[s][f] = c; c += fb; }
+  h->phi = c; c += fb;
+  h->mu = c; c += fb;
+  h->phis[0] = c; c += fb;
+  h->phis[1] = c; c += fb;
+  h->mus = c; c += fb;
+  h->acc = c; c += fb;
+  for (int a = 0; a < 3; ++a) { h->uh[a] = c; c += fb; }
+  h->d_stage = (double*)c; c += stage_b;
+  h->d_part = (double*)c; c += part_b;
+  h->d_out = (double*)c;
+  e = cudaMemsetAsync(h->base, 0, total, h->stream);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_out, 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    gpe2p_destroy(h);
+    return fail(nullptr, GPE2P_ECUDA, std::string("set-up: ") + cudaGetErrorString(e));
+  }
+  // z-chunk of the marching kernels: enough blocks to fill the GPU a few times
+  if (h->prm.dim == 3) {
+    const long long bxy = (long long)((h->prm.nx + TX - 1) / TX) * ((h->prm.ny + TY - 1) / TY);
+    long long zch = (152LL * 6 + bxy - 1) / bxy;
+    long long kc = (h->prm.nz + zch - 1) / zch;
+    if (kc < 4) kc = 4;
+    if (kc > h->prm.nz) kc = h->prm.nz;
+    h->kchunk = (int)kc;
+  } else {
+    h->kchunk = 1;
+  }
+  *out = h;
+  return GPE2P_OK;
+}
+
+template <typename real>
+static cudaError_t put_field(gpe2p_ctx* h, const double* src, void* dst, int comp) {
+  const KParams<real> P = kparams<real>(h->prm);
+  cudaError_t e = cudaMemcpyAsync(h->d_stage, src, (size_t)h->ncell * sizeof(double), cudaMemcpyHostToDevice,
+                                  h->stream);
+  if (e != cudaSuccess) return e;
+  return launch_from_double<real>(P, h->d_stage, (real*)dst, comp, h->ncell, h->stream);
+}
+
+template <typename real>
+static cudaError_t init_impl(gpe2p_ctx* h, const double* phi, const double* u, const double* v, const double* w,
+                             const double* p) {
+  const double* src[4] = {p, u, v, w};
+  cudaError_t e;
+  for (int f = 0; f < 1 + h->prm.dim; ++f)
+    if ((e = put_field<real>(h, src[f], h->Q[0][f], f - 1)) != cudaSuccess) return e;
+  if ((e = put_field<real>(h, phi, h->phi, -1)) != cudaSuccess) return e;
+  const KParams<real> P = kparams<real>(h->prm);
+  if (h->prm.dim == 2) e = launch_mu<real, 2>(P, (real*)h->phi, (real*)h->mu, h->prm.iso, h->kchunk, h->stream);
+  else e = launch_mu<real, 3>(P, (real*)h->phi, (real*)h->mu, h->prm.iso, h->kchunk, h->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(h->stream);
+}
+
+extern "C" int gpe2p_init_fields(gpe2p_handle h, const double* phi, const double* u, const double* v,
+                                 const double* w, const double* p) {
+  if (!h) return fail(nullptr, GPE2P_EINVAL, "handle is NULL");
+  if (!phi || !u || !v || !p || (h->prm.dim == 3 && !w)) return fail(h, GPE2P_EINVAL, "a required field is NULL");
+  CK(h, cudaSetDevice(h->dev), "set device");
+  h->cur = 0;
+  cudaError_t e = h->esize == 4 ? init_impl<float>(h, phi, u, v, w, p) : init_impl<double>(h, phi, u, v, w, p);
+  if (e != cudaSuccess) return cuda_fail(h, e, "init_fields");
+  h->step = 0;
+  h->initialized = true;
+  return GPE2P_OK;
+}
+
+static int diag_impl(gpe2p_ctx* h, gpe2p_diag* d) {
+  cudaError_t e;
+  const int cur = h->cur;
+  if (h->esize == 4) {
+    const KParams<float> P = kparams<float>(h->prm);
+    const float* U[3] = {(float*)h->Q[cur][1], (float*)h->Q[cur][2], (float*)h->Q[cur][3]};
+    e = h->prm.dim == 2 ? launch_diag<float, 2>(P, (float*)h->Q[cur][0], U, (float*)h->phi, h->d_part, h->nblk,
+                                                h->d_out, h->stream)
+                        : launch_diag<float, 3>(P, (float*)h->Q[cur][0], U, (float*)h->phi, h->d_part, h->nblk,
+                                                h->d_out, h->stream);
+  } else {
+    const KParams<double> P = kparams<double>(h->prm);
+    const double* U[3] = {(double*)h->Q[cur][1], (double*)h->Q[cur][2], (double*)h->Q[cur][3]};
+    e = h->prm.dim == 2 ? launch_diag<double, 2>(P, (double*)h->Q[cur][0], U, (double*)h->phi, h->d_part,
+                                                 h->nblk, h->d_out, h->stream)
+                        : launch_diag<double, 3>(P, (double*)h->Q[cur][0], U, (double*)h->phi, h->d_part,
+                                                 h->nblk, h->d_out, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics");
+  CK(h, cudaMemcpyAsync(h->h_out, h->d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "diag copy");
+  CK(h, cudaStreamSynchronize(h->stream), "diag sync");
+  d->int_phi = h->h_out[0];
+  d->kinetic = h->h_out[1];
+  d->umax = h->h_out[2];
+  d->nan_flag = h->h_out[3] != 0.0 || !std::isfinite(h->h_out[0]) || !std::isfinite(h->h_out[1]);
+  d->step = h->step;
+  d->t = (double)h->step * h->prm.dt;
+  return GPE2P_OK;
+}
+
+extern "C" int gpe2p_step(gpe2p_handle h) {
+  if (!h) return fail(nullptr, GPE2P_EINVAL, "handle is NULL");
+  if (!h->initialized) return fail(h, GPE2P_ESTATE, "gpe2p_step before gpe2p_init_fields");
+  CK(h, cudaSetDevice(h->dev), "set device");
+  if (!h->have_graph) {
+    int rc = build_graphs(h);
+    if (rc != GPE2P_OK) return rc;
+  }
+  CK(h, cudaGraphLaunch(h->gexec[h->cur], h->stream), "graph launch");
+  h->cur = 1 - h->cur;
+  h->step += 1;
+  return GPE2P_OK;
+}
+
+extern "C" int gpe2p_advance(gpe2p_handle h, long long nsteps, gpe2p_diag* last) {
+  if (!h) return fail(nullptr, GPE2P_EINVAL, "handle is NULL");
+  if (nsteps < 0) return fail(h, GPE2P_EINVAL, "nsteps < 0");
+  if (!h->initialized) return fail(h, GPE2P_ESTATE, "gpe2p_advance before gpe2p_init_fields");
+  gpe2p_diag d{};
+  for (long long s = 0; s < nsteps; ++s) {
+    int rc = gpe2p_step(h);
+    if (rc != GPE2P_OK) return rc;
+    if (h->prm.diag_every > 0 && (s + 1) % h->prm.diag_every == 0 && s + 1 < nsteps) {
+      rc = diag_impl(h, &d);
+      if (rc != GPE2P_OK) return rc;
+      if (d.nan_flag) {
+        if (last) *last = d;
+        return fail(h, GPE2P_EDIVERGED, "NaN/Inf in the state at step " + std::to_string(h->step));
+      }
+    }
+  }
+  int rc = diag_impl(h, &d);
+  if (rc != GPE2P_OK) return rc;
+  if (last) *last = d;
+  if (d.nan_flag) return fail(h, GPE2P_EDIVERGED, "NaN/Inf in the state at step " + std::to_string(h->step));
+  return GPE2P_OK;
+}
+
+extern "C" int gpe2p_diagnostics(gpe2p_handle h, gpe2p_diag* out) {
+  if (!h || !out) return fail(h, GPE2P_EINVAL, "NULL argument");
+  if (!h->initialized) return fail(h, GPE2P_ESTATE, "diagnostics before gpe2p_init_fields");
+  CK(h, cudaSetDevice(h->dev), "set device");
+  return diag_impl(h, out);
+}
+
+template <typename real>
+static cudaError_t get_field(gpe2p_ctx* h, const void* src, double* dst) {
+  cudaError_t e;
+  if (sizeof(real) == 8) {
+    e = cudaMemcpyAsync(dst, src, (size_t)h->ncell * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  } else {
+    e = launch_to_double<real>((const real*)src, h->d_stage, h->ncell, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dst, h->d_stage, (size_t)h->ncell * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  }
+  return e;
+}
+
+static cudaError_t get_any(gpe2p_ctx* h, const void* src, double* dst) {
+  return h->esize == 4 ? get_field<float>(h, src, dst) : get_field<double>(h, src, dst);
+}
+
+extern "C" int gpe2p_read_fields(gpe2p_handle h, double* phi, double* u, double* v, double* w, double* p,
+                                 double* mu) {
+  if (!h) return fail(nullptr, GPE2P_EINVAL, "handle is NULL");
+  if (!h->initialized) return fail(h, GPE2P_ESTATE, "read_fields before gpe2p_init_fields");
+  CK(h, cudaSetDevice(h->dev), "set device");
+  double* dst[6] = {p, u, v, h->prm.dim == 3 ? w : nullptr, phi, mu};
+  const void* src[6] = {h->Q[h->cur][0], h->Q[h->cur][1], h->Q[h->cur][2], h->Q[h->cur][3], h->phi, h->mu};
+  for (int f = 0; f < 6; ++f)
+    if (dst[f]) CK(h, get_any(h, src[f], dst[f]), "read_fields");
+  CK(h, cudaStreamSynchronize(h->stream), "read_fields sync");
+  return GPE2P_OK;
+}
+
+template <typename real, int DIM>
+static cudaError_t rates_impl(gpe2p_ctx* h) {
+  const KParams<real> P = kparams<real>(h->prm);
+  const int cur = h->cur;
+  FlowArgs<real> A{};
+  for (int f = 0; f < 4; ++f) {
+    A.q0[f] = (const real*)h->Q[cur][f];
+    A.q[f] = (const real*)h->Q[cur][f];
+    A.out[f] = (real*)h->Q[2][f];
+  }
+  A.phi = (const real*)h->phi;
+  A.mu = (const real*)h->mu;
+  cudaError_t e = launch_flow_stage<real, DIM>(P, A, 0, h->kchunk, h->stream);
+  if (e != cudaSuccess) return e;
+  CHArgs<real> C{};
+  for (int a = 0; a < 3; ++a) {
+    C.uh[a] = (real*)h->uh[a];
+    C.u0[a] = (const real*)h->Q[cur][1 + a];
+    C.u1[a] = (const real*)h->Q[cur][1 + a];
+  }
+  C.conservative = h->prm.ch_advection;
+  if (C.conservative) {
+    const real* u0[3] = {C.u0[0], C.u0[1], C.u0[2]};
+    real* uh[3] = {C.uh[0], C.uh[1], C.uh[2]};
+    if ((e = launch_center_velocity<real, DIM>(P, u0, u0, uh, h->stream)) != cudaSuccess) return e;
+  }
+  C.scheme = h->prm.ch_scheme;
+  C.stage = 0;
+  C.compute_uh = !C.conservative;
+  C.phis = (const real*)h->phi;
+  C.mus = (const real*)h->mu;
+  C.phin = (const real*)h->phi;
+  C.out = (real*)h->phis[0];
+  return launch_ch_stage<real, DIM>(P, C, h->prm.iso, h->kchunk, h->stream);
+}
+
+extern "C" int gpe2p_eval_rates(gpe2p_handle h, double* Lp, double* Lu, double* Lv, double* Lw, double* Lphi) {
+  if (!h) return fail(nullptr, GPE2P_EINVAL, "handle is NULL");
+  if (!h->initialized) return fail(h, GPE2P_ESTATE, "eval_rates before gpe2p_init_fields");
+  CK(h, cudaSetDevice(h->dev), "set device");
+  cudaError_t e;
+  if (h->esize == 4) e = h->prm.dim == 2 ? rates_impl<float, 2>(h) : rates_impl<float, 3>(h);
+  else e = h->prm.dim == 2 ? rates_impl<double, 2>(h) : rates_impl<double, 3>(h);
+  if (e != cudaSuccess) return cuda_fail(h, e, "eval_rates");
+  double* dst[5] = {Lp, Lu, Lv, h->prm.dim == 3 ? Lw : nullptr, Lphi};
+  const void* src[5] = {h->Q[2][0], h->Q[2][1], h->Q[2][2], h->Q[2][3], h->phis[0]};
+  for (int f = 0; f < 5; ++f)
+    if (dst[f]) CK(h, get_any(h, src[f], dst[f]), "eval_rates copy");
+  CK(h, cudaStreamSynchronize(h->stream), "eval_rates sync");
+  return GPE2P_OK;
+}
+
+extern "C" int gpe2p_profile_steps(gpe2p_handle h, int nsteps, double* ms, int max_launches, int* nlaunches,
+                                   char* names, int names_len) {
+  if (!h || !ms || !nlaunches || nsteps < 1 || max_launches < 1) return fail(h, GPE2P_EINVAL, "bad argument");
+  if (!h->initialized) return fail(h, GPE2P_ESTATE, "profile_steps before gpe2p_init_fields");
+  CK(h, cudaSetDevice(h->dev), "set device");
+  const int cap = 32;
+  cudaEvent_t ev[cap + 1];
+  const char* nm[cap];
+  for (int i = 0; i <= cap; ++i) CK(h, cudaEventCreate(&ev[i]), "event create");
+  ProfHook hook;
+  hook.ev = ev;
+  hook.max = cap;
+  hook.names = nm;
+  for (int i = 0; i < max_launches; ++i) ms[i] = 0.0;
+  int rc = GPE2P_OK;
+  for (int s = 0; s < nsteps && rc == GPE2P_OK; ++s) {
+    cudaError_t e = enqueue(h, h->cur, &hook);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[hook.n]);
+    if (e != cudaSuccess) { rc = cuda_fail(h, e, "profile step"); break; }
+    h->cur = 1 - h->cur;
+    h->step += 1;
+    for (int i = 0; i < hook.n && i < max_launches; ++i) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+      ms[i] += (double)t / nsteps;
+    }
+  }
+  *nlaunches = hook.n;
+  if (names && names_len > 0) {
+    std::string all;
+    for (int i = 0; i < hook.n; ++i) { if (i) all += ","; all += nm[i]; }
+    std::snprintf(names, (size_t)names_len, "%s", all.c_str());
+  }
+  for (int i = 0; i <= cap; ++i) cudaEventDestroy(ev[i]);
+  return rc;
+}
+
+extern "C" int gpe2p_field_ptr(gpe2p_handle h, int which, void** dptr) {
+  if (!h || !dptr) return fail(h, GPE2P_EINVAL, "NULL argument");
+  if (which < 0 || which > 5 || (which == 3 && h->prm.dim == 2)) return fail(h, GPE2P_EINVAL, "bad field index");
+  void* src[6] = {h->Q[h->cur][0], h->Q[h->cur][1], h->Q[h->cur][2], h->Q[h->cur][3], h->phi, h->mu};
+  *dptr = src[which];
+  return GPE2P_OK;
+}
+
+extern "C" const char* gpe2p_last_error(gpe2p_handle h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" void gpe2p_destroy(gpe2p_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->dev);
+  for (int c = 0; c < 2; ++c)
+    if (h->gexec[c]) cudaGraphExecDestroy(h->gexec[c]);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->base) cudaFree(h->base);
+  if (h->h_out) cudaFreeHost(h->h_out);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}

@@ -1,0 +1,183 @@
+// diag.cu -- FP64 diagnostics of the state (sum of phi, kinetic energy with
+// the face density, max |u|, NaN/Inf flag) and the FP64 <-> working-precision
+// copies used at the host boundary.
+//
+// The reduction is deterministic: a fixed grid of blocks walks the cells with
+// a grid-stride loop, each block reduces its partial sums with warp shuffles
+// into a slot of a scratch array, and a single block then sums the slots in
+// a fixed order.
+#include "gpe2p_dev.cuh"
+#include "gpe2p_launch.h"
+
+namespace gpe2p {
+
+constexpr int DIAG_THREADS = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <typename real, int DIM>
+__global__ void __launch_bounds__(DIAG_THREADS) diag_partial_kernel(const KParams<real> P, const real* p,
+                                                                    const real* u0, const real* u1,
+                                                                    const real* u2, const real* phi,
+                                                                    double* partial) {
+  const long long n = (long long)P.n[0] * P.n[1] * P.n[2];
+  double sphi = 0.0, ke = 0.0, umax = 0.0, bad = 0.0;
+  const real* U[3] = {u0, u1, u2};
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(id % P.n[0]);
+    const int j = (int)((id / P.n[0]) % P.n[1]);
+    const int k = (int)(id / ((long long)P.n[0] * P.n[1]));
+    const double f = (double)phi[id];
+    sphi += f;
+    if (!isfinite(f) || !isfinite((double)p[id])) bad = 1.0;
+    const double rho0 = 0.5 * ((double)P.rhoL * (1.0 + f) + (double)P.rhoG * (1.0 - f));
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      const double fm = (double)ld_cen(phi, P, i - (c == 0), j - (c == 1), k - (c == 2));
+      const double rhom = 0.5 * ((double)P.rhoL * (1.0 + fm) + (double)P.rhoG * (1.0 - fm));
+      const double uc = (double)U[c][id];
+      ke += 0.5 * (0.5 * (rhom + rho0)) * uc * uc;
+      umax = fmax(umax, fabs(uc));
+      if (!isfinite(uc)) bad = 1.0;
+    }
+  }
+  __shared__ double red[4][DIAG_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  sphi = warp_sum(sphi);
+  ke = warp_sum(ke);
+  umax = warp_max(umax);
+  bad = warp_max(bad);
+  if (lane == 0) {
+    red[0][wid] = sphi;
+    red[1][wid] = ke;
+    red[2][wid] = umax;
+    red[3][wid] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+    for (int w = 0; w < DIAG_THREADS / 32; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+      c = fmax(c, red[2][w]);
+      d = fmax(d, red[3][w]);
+    }
+    partial[4 * blockIdx.x + 0] = a;
+    partial[4 * blockIdx.x + 1] = b;
+    partial[4 * blockIdx.x + 2] = c;
+    partial[4 * blockIdx.x + 3] = d;
+  }
+}
+
+__global__ void diag_final_kernel(const double* partial, int nblocks, double vol, double* out) {
+  __shared__ double red[4][DIAG_THREADS];
+  double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+  for (int q = threadIdx.x; q < nblocks; q += blockDim.x) {
+    a += partial[4 * q + 0];
+    b += partial[4 * q + 1];
+    c = fmax(c, partial[4 * q + 2]);
+    d = fmax(d, partial[4 * q + 3]);
+  }
+  red[0][threadIdx.x] = a;
+  red[1][threadIdx.x] = b;
+  red[2][threadIdx.x] = c;
+  red[3][threadIdx.x] = d;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + s];
+      red[1][threadIdx.x] += red[1][threadIdx.x + s];
+      red[2][threadIdx.x] = fmax(red[2][threadIdx.x], red[2][threadIdx.x + s]);
+      red[3][threadIdx.x] = fmax(red[3][threadIdx.x], red[3][threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = red[0][0] * vol;
+    out[1] = red[1][0] * vol;
+    out[2] = red[2][0];
+    out[3] = red[3][0];
+  }
+}
+
+template <typename real, int DIM>
+cudaError_t launch_diag(const KParams<real>& P, const real* p, const real* const U[3], const real* phi,
+                        double* partial, int nblocks, double* out, cudaStream_t s) {
+  const double dx = 1.0 / (double)P.inv_dx;
+  const double vol = DIM == 3 ? dx * dx * dx : dx * dx;
+  diag_partial_kernel<real, DIM><<<nblocks, DIAG_THREADS, 0, s>>>(P, p, U[0], U[1], U[2], phi, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  diag_final_kernel<<<1, DIAG_THREADS, 0, s>>>(partial, nblocks, vol, out);
+  return cudaGetLastError();
+}
+
+template <typename real>
+__global__ void from_double_kernel(const KParams<real> P, const double* src, real* dst, int c, long long n) {
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
+       id += (long long)gridDim.x * blockDim.x) {
+    real v = (real)src[id];
+    if (c >= 0 && P.bc[c] != BC_PERIODIC) {
+      const int i = (int)(id % P.n[0]);
+      const int j = (int)((id / P.n[0]) % P.n[1]);
+      const int k = (int)(id / ((long long)P.n[0] * P.n[1]));
+      const int x = c == 0 ? i : (c == 1 ? j : k);
+      if (x == 0) v = real(0);
+    }
+    dst[id] = v;
+  }
+}
+
+template <typename real>
+__global__ void to_double_kernel(const real* src, double* dst, long long n) {
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
+       id += (long long)gridDim.x * blockDim.x)
+    dst[id] = (double)src[id];
+}
+
+static unsigned grid_for(long long n) {
+  long long nb = (n + 255) / 256;
+  if (nb > 152 * 32) nb = 152 * 32;
+  if (nb < 1) nb = 1;
+  return (unsigned)nb;
+}
+
+template <typename real>
+cudaError_t launch_from_double(const KParams<real>& P, const double* src, real* dst, int c, long long n,
+                               cudaStream_t s) {
+  from_double_kernel<real><<<grid_for(n), 256, 0, s>>>(P, src, dst, c, n);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_to_double(const real* src, double* dst, long long n, cudaStream_t s) {
+  to_double_kernel<real><<<grid_for(n), 256, 0, s>>>(src, dst, n);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_diag<float, 2>(const KParams<float>&, const float*, const float* const[3],
+                                           const float*, double*, int, double*, cudaStream_t);
+template cudaError_t launch_diag<float, 3>(const KParams<float>&, const float*, const float* const[3],
+                                           const float*, double*, int, double*, cudaStream_t);
+template cudaError_t launch_diag<double, 2>(const KParams<double>&, const double*, const double* const[3],
+                                            const double*, double*, int, double*, cudaStream_t);
+template cudaError_t launch_diag<double, 3>(const KParams<double>&, const double*, const double* const[3],
+                                            const double*, double*, int, double*, cudaStream_t);
+template cudaError_t launch_from_double<float>(const KParams<float>&, const double*, float*, int, long long,
+                                               cudaStream_t);
+template cudaError_t launch_from_double<double>(const KParams<double>&, const double*, double*, int,
+                                                long long, cudaStream_t);
+template cudaError_t launch_to_double<float>(const float*, double*, long long, cudaStream_t);
+template cudaError_t launch_to_double<double>(const double*, double*, long long, cudaStream_t);
+
+}  // namespace gpe2p

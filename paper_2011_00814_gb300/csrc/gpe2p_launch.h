@@ -1,0 +1,71 @@
+// gpe2p_launch.h -- argument blocks and launchers of the device kernels
+// (internal to the library; the public interface is include/gpe2p.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "gpe2p_dev.cuh"
+
+namespace gpe2p {
+
+// one flow stage: out = a q0 + b (q + dt L(q))   (Eq. tvd-rk3)
+template <typename real>
+struct FlowArgs {
+  const real* q0[4];   // p, u, v, w at t^n (read at the cell only)
+  const real* q[4];    // stage input (read with halo)
+  real* out[4];
+  const real* phi;     // frozen at t^{n+1/2}
+  const real* mu;
+  real a, b;
+};
+
+// one Cahn-Hilliard stage (Eqs. che, tvd-rk2, rk4) or its rate
+template <typename real>
+struct CHArgs {
+  const real* phis;    // stage state phi_s (read with halo)
+  const real* mus;     // mu(phi_s) (read with halo)
+  const real* phin;    // phi^{n+1/2} (read at the cell)
+  real* out;           // stage output (phi_{s+1} or phi^{n+3/2}) or the rate
+  real* acc;           // RK4 accumulator a + 2b + 2c
+  real* uh[3];         // time-centred cell velocity (written when compute_uh)
+  const real* u0[3];   // face velocity at t^n      (read when compute_uh)
+  const real* u1[3];   // face velocity at t^{n+1}  (read when compute_uh)
+  int scheme;          // 2 or 4
+  int stage;           // 1..scheme; 0 = write the rate L only
+  int compute_uh;      // 1: build uhat (Eq. u-center-2d) from u0, u1 and store it
+  int conservative;    // 1: -div(uhat phi) instead of -uhat.grad(phi)
+};
+
+template <typename real, int DIM>
+cudaError_t launch_flow_stage(const KParams<real>& P, const FlowArgs<real>& A, int mode, int kchunk,
+                              cudaStream_t s);
+
+template <typename real, int DIM>
+cudaError_t launch_ch_stage(const KParams<real>& P, const CHArgs<real>& A, int iso, int kchunk,
+                            cudaStream_t s);
+
+// mu = 4 a phi (phi^2 - 1) - kappa lap_iso phi   (Eq. chem-pot)
+template <typename real, int DIM>
+cudaError_t launch_mu(const KParams<real>& P, const real* phi, real* mu, int iso, int kchunk,
+                      cudaStream_t s);
+
+// uhat_a = 1/4 [(u0_a + u0_a(+e_a)) + (u1_a + u1_a(+e_a))]   (Eq. u-center-2d)
+template <typename real, int DIM>
+cudaError_t launch_center_velocity(const KParams<real>& P, const real* const u0[3], const real* const u1[3],
+                                   real* const uh[3], cudaStream_t s);
+
+// FP64 diagnostics: out[0] sum phi, out[1] kinetic energy (per unit volume
+// element), out[2] max |u|, out[3] NaN/Inf flag (as 0/1).  partial must hold
+// 4 * nblocks doubles.
+template <typename real, int DIM>
+cudaError_t launch_diag(const KParams<real>& P, const real* p, const real* const U[3], const real* phi,
+                        double* partial, int nblocks, double* out, cudaStream_t s);
+
+// FP64 <-> working precision copies with the wall faces of component c zeroed (c < 0: none)
+template <typename real>
+cudaError_t launch_from_double(const KParams<real>& P, const double* src, real* dst, int c, long long n,
+                               cudaStream_t s);
+template <typename real>
+cudaError_t launch_to_double(const real* src, double* dst, long long n, cudaStream_t s);
+
+}  // namespace gpe2p

@@ -1,0 +1,224 @@
+"""ctypes binding of ``libgpe2p.so`` (the C ABI of include/gpe2p.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  There is no CPU fallback; if the library is missing the
+import of :func:`lib` raises.
+
+Parameters are a plain ``dict`` (see :mod:`paper_2011_00814_gb300.inputs`)
+plus the solver keys ``precision`` (32 | 64), ``check_stability`` (0 | 1) and
+``diag_every`` (int).  Fields are numpy float64 arrays of shape ``(ny, nx)``
+or ``(nz, ny, nx)``; the library copies them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgpe2p.so")
+
+OK, EINVAL, EUNSTABLE, ENOMEM, ECUDA, EDIVERGED, ETIMEOUT, ESTATE = range(8)
+STATUS = {0: "OK", 1: "EINVAL", 2: "EUNSTABLE", 3: "ENOMEM", 4: "ECUDA", 5: "EDIVERGED", 6: "ETIMEOUT",
+          7: "ESTATE"}
+BC = {"periodic": 0, "noslip": 1, "freeslip": 2}
+FIELD = {"p": 0, "u": 1, "v": 2, "w": 3, "phi": 4, "mu": 5}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("cs", ctypes.c_double),
+        ("rhoL", ctypes.c_double), ("rhoG", ctypes.c_double), ("etaL", ctypes.c_double),
+        ("etaG", ctypes.c_double), ("rho_ref", ctypes.c_double), ("sigma", ctypes.c_double),
+        ("M", ctypes.c_double), ("W", ctypes.c_double), ("g", ctypes.c_double * 3),
+        ("bc", ctypes.c_int * 3), ("precision", ctypes.c_int), ("ch_scheme", ctypes.c_int),
+        ("iso", ctypes.c_int), ("bulk_visc", ctypes.c_int), ("p_average", ctypes.c_int),
+        ("ch_advection", ctypes.c_int), ("check_stability", ctypes.c_int), ("diag_every", ctypes.c_int),
+    ]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("int_phi", ctypes.c_double), ("kinetic", ctypes.c_double), ("umax", ctypes.c_double),
+                ("nan_flag", ctypes.c_int), ("step", ctypes.c_longlong), ("t", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class GPE2PError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2011_00814_gb300.build` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        dp = ctypes.POINTER(ctypes.c_double)
+        vp = ctypes.c_void_p
+        L.gpe2p_stability_limits.argtypes = [ctypes.POINTER(Params), dp]
+        L.gpe2p_create.argtypes = [ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]
+        L.gpe2p_init_fields.argtypes = [vp] + [dp] * 5
+        L.gpe2p_step.argtypes = [vp]
+        L.gpe2p_advance.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(Diag)]
+        L.gpe2p_read_fields.argtypes = [vp] + [dp] * 6
+        L.gpe2p_diagnostics.argtypes = [vp, ctypes.POINTER(Diag)]
+        L.gpe2p_eval_rates.argtypes = [vp] + [dp] * 5
+        L.gpe2p_field_ptr.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp)]
+        L.gpe2p_profile_steps.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.c_char_p, ctypes.c_int]
+        L.gpe2p_last_error.argtypes = [vp]
+        L.gpe2p_last_error.restype = ctypes.c_char_p
+        L.gpe2p_destroy.argtypes = [vp]
+        L.gpe2p_destroy.restype = None
+        for nm in ("gpe2p_stability_limits", "gpe2p_create", "gpe2p_init_fields", "gpe2p_step",
+                   "gpe2p_advance", "gpe2p_read_fields", "gpe2p_diagnostics", "gpe2p_eval_rates",
+                   "gpe2p_field_ptr", "gpe2p_profile_steps"):
+            getattr(L, nm).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def params(prm: dict) -> Params:
+    q = Params()
+    dim = int(prm["dim"])
+    q.dim, q.nx, q.ny = dim, int(prm["nx"]), int(prm["ny"])
+    q.nz = int(prm.get("nz", 1)) if dim == 3 else 1
+    for k in ("dx", "dt", "cs", "rhoL", "rhoG", "etaL", "etaG", "sigma", "M", "W"):
+        setattr(q, k, float(prm[k]))
+    q.rho_ref = float(prm.get("rho_ref", 0.0))
+    g = list(prm.get("g", (0.0, 0.0, 0.0))) + [0.0] * 3
+    bc = list(prm.get("bc", ("periodic",) * 3)) + ["periodic"] * 3
+    for a in range(3):
+        q.g[a] = float(g[a])
+        q.bc[a] = BC[bc[a]] if isinstance(bc[a], str) else int(bc[a])
+    q.precision = int(prm.get("precision", 64))
+    q.ch_scheme = int(prm.get("ch_scheme", 2 if dim == 2 else 4))
+    q.iso = int(prm.get("iso", 9 if dim == 2 else 15))
+    q.bulk_visc = int(prm.get("bulk_visc", 1))
+    q.p_average = int(prm.get("p_average", 1))
+    q.ch_advection = int(prm.get("ch_advection", 0))
+    q.check_stability = int(prm.get("check_stability", 0))
+    q.diag_every = int(prm.get("diag_every", 0))
+    return q
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def stability_limits(prm: dict):
+    out = (ctypes.c_double * 3)()
+    rc = lib().gpe2p_stability_limits(ctypes.byref(params(prm)), out)
+    if rc != OK:
+        raise GPE2PError(rc, lib().gpe2p_last_error(None).decode())
+    return tuple(out)
+
+
+class Solver:
+    """One problem on the current CUDA device (``gpe2p_create`` ... ``gpe2p_destroy``)."""
+
+    def __init__(self, prm: dict, stream: int | None = None):
+        self.prm = dict(prm)
+        self.dim = int(prm["dim"])
+        self.shape = ((int(prm["nz"]), int(prm["ny"]), int(prm["nx"])) if self.dim == 3
+                      else (int(prm["ny"]), int(prm["nx"])))
+        self._p = params(prm)
+        h = ctypes.c_void_p()
+        rc = lib().gpe2p_create(ctypes.byref(self._p), ctypes.c_void_p(stream) if stream else None,
+                                ctypes.byref(h))
+        if rc != OK:
+            raise GPE2PError(rc, lib().gpe2p_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != OK:
+            raise GPE2PError(rc, lib().gpe2p_last_error(self.h).decode())
+
+    def _arr(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        if a.shape != self.shape:
+            raise ValueError(f"field shape {a.shape} != {self.shape}")
+        return a
+
+    def init_fields(self, f: dict):
+        a = {k: self._arr(f[k]) for k in ("phi", "u", "v", "p")}
+        a["w"] = self._arr(f["w"]) if self.dim == 3 else None
+        self._check(lib().gpe2p_init_fields(self.h, _dptr(a["phi"]), _dptr(a["u"]), _dptr(a["v"]),
+                                            _dptr(a["w"]), _dptr(a["p"])))
+
+    def step(self):
+        self._check(lib().gpe2p_step(self.h))
+
+    def advance(self, nsteps: int) -> dict:
+        d = Diag()
+        self._check(lib().gpe2p_advance(self.h, int(nsteps), ctypes.byref(d)))
+        return d.as_dict()
+
+    def diagnostics(self) -> dict:
+        d = Diag()
+        self._check(lib().gpe2p_diagnostics(self.h, ctypes.byref(d)))
+        return d.as_dict()
+
+    def read_fields(self) -> dict:
+        names = ["phi", "u", "v", "w", "p", "mu"]
+        out = {k: np.empty(self.shape) for k in names}
+        if self.dim == 2:
+            out["w"] = None
+        self._check(lib().gpe2p_read_fields(self.h, *[_dptr(out[k]) for k in names]))
+        if self.dim == 2:
+            out.pop("w")
+        return out
+
+    def eval_rates(self) -> dict:
+        names = ["Lp", "Lu", "Lv", "Lw", "Lphi"]
+        out = {k: np.empty(self.shape) for k in names}
+        if self.dim == 2:
+            out["Lw"] = None
+        self._check(lib().gpe2p_eval_rates(self.h, *[_dptr(out[k]) for k in names]))
+        if self.dim == 2:
+            out.pop("Lw")
+        return out
+
+    def profile_steps(self, nsteps: int):
+        """[(kernel name, mean ms per launch)] for the launches of one step."""
+        ms = (ctypes.c_double * 64)()
+        n = ctypes.c_int()
+        names = ctypes.create_string_buffer(2048)
+        self._check(lib().gpe2p_profile_steps(self.h, int(nsteps), ms, 64, ctypes.byref(n), names, 2048))
+        nm = names.value.decode().split(",")
+        return [(nm[i], ms[i]) for i in range(n.value)]
+
+    def field_ptr(self, name: str) -> int:
+        p = ctypes.c_void_p()
+        self._check(lib().gpe2p_field_ptr(self.h, FIELD[name], ctypes.byref(p)))
+        return p.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gpe2p_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

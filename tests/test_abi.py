@@ -1,0 +1,127 @@
+"""Host-side checks of the C ABI: the library builds, loads and exports every
+entry point the header declares, the ctypes structs match the C layout, and
+the host-only entry points (validation, stability limits) behave."""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2011_00814_gb300 import build, gpe2p, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gpe2p.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return gpe2p.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gpe2p_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for nm in ("gpe2p_create", "gpe2p_init_fields", "gpe2p_step", "gpe2p_advance", "gpe2p_read_fields",
+               "gpe2p_destroy", "gpe2p_last_error", "gpe2p_stability_limits"):
+        assert nm in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", gpe2p.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(line.split()[-1] for line in out.splitlines() if line.strip())
+    for nm in declared_functions():
+        assert nm in exported, nm
+        assert hasattr(lib, nm)
+
+
+def _c_layout():
+    """sizeof / offsetof of the header structs, from a C compiler."""
+    prog = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "gpe2p.h"
+#define O(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
+int main(void) {
+  printf("gpe2p_params %zu\n", sizeof(gpe2p_params));
+  printf("gpe2p_diag %zu\n", sizeof(gpe2p_diag));
+  O(gpe2p_params, dx); O(gpe2p_params, g); O(gpe2p_params, bc); O(gpe2p_params, precision);
+  O(gpe2p_params, diag_every); O(gpe2p_diag, nan_flag); O(gpe2p_diag, step); O(gpe2p_diag, t);
+  return 0;
+}
+"""
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "l.c")
+        exe = os.path.join(d, "l")
+        open(c, "w").write(prog)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    return dict((k, int(v)) for k, v in (line.split() for line in out.splitlines()))
+
+
+def test_ctypes_structs_match_header_layout():
+    lay = _c_layout()
+    assert lay["gpe2p_params"] == ctypes.sizeof(gpe2p.Params)
+    assert lay["gpe2p_diag"] == ctypes.sizeof(gpe2p.Diag)
+    for f in ("dx", "g", "bc", "precision", "diag_every"):
+        assert lay[f"gpe2p_params.{f}"] == getattr(gpe2p.Params, f).offset, f
+    for f in ("nan_flag", "step", "t"):
+        assert lay[f"gpe2p_diag.{f}"] == getattr(gpe2p.Diag, f).offset, f
+
+
+def test_stability_limits_of_the_workloads(lib):
+    # the static drop: margins of the reading (acoustic c_s dt/dx = 0.3)
+    prm, _ = inputs.static_drop()
+    ac, vi, ch = gpe2p.stability_limits(prm)
+    assert prm["dt"] < ac and prm["dt"] < vi and prm["dt"] < ch
+    # acoustic limit of the 2D staggered operator with averaging: sqrt(3)/2 dx/c_s
+    assert abs(ac - math.sqrt(3.0) / 2.0) < 1e-12
+    # the 3D bubble is stable only because of the pressure averaging (Sec. 4.5)
+    prm, _ = inputs.bubble3d(32, 32, 64, R=8, gap=8)
+    ac, vi, ch = gpe2p.stability_limits(prm)
+    assert prm["dt"] < min(ac, vi, ch)
+    ac0, _, _ = gpe2p.stability_limits(dict(prm, p_average=0))
+    assert prm["dt"] > ac0
+    # the Rayleigh-Taylor case at Pe = 1000: the CH limit sets dt
+    prm, _ = inputs.rayleigh_taylor()
+    ac, vi, ch = gpe2p.stability_limits(prm)
+    assert prm["dt"] < ch < 2.5 * prm["dt"]
+
+
+@pytest.mark.parametrize("bad", [dict(dim=4), dict(nx=0), dict(nx=70000), dict(dx=0.0), dict(dt=-1.0),
+                                 dict(rhoG=0.0), dict(etaL=-1.0), dict(W=0.0), dict(precision=16),
+                                 dict(ch_scheme=3), dict(iso=15), dict(bc=("wall",) * 3),
+                                 dict(bulk_visc=2), dict(sigma=float("nan"))])
+def test_invalid_parameters_are_rejected_on_the_host(lib, bad):
+    prm = dict(inputs.base_params(2, 8, 8), precision=64)
+    if bad.get("bc") == ("wall",) * 3:
+        q = gpe2p.params(prm)
+        q.bc[0] = 7
+        out = (ctypes.c_double * 3)()
+        assert lib.gpe2p_stability_limits(ctypes.byref(q), out) == gpe2p.EINVAL
+        return
+    prm.update(bad)
+    with pytest.raises(gpe2p.GPE2PError) as e:
+        gpe2p.stability_limits(prm)
+    assert e.value.code == gpe2p.EINVAL
+
+
+def test_null_arguments_do_not_crash(lib):
+    assert lib.gpe2p_step(None) == gpe2p.EINVAL
+    assert lib.gpe2p_advance(None, 1, None) == gpe2p.EINVAL
+    assert lib.gpe2p_read_fields(None, None, None, None, None, None, None) == gpe2p.EINVAL
+    lib.gpe2p_destroy(None)
+    h = ctypes.c_void_p()
+    assert lib.gpe2p_create(None, None, ctypes.byref(h)) == gpe2p.EINVAL
+    assert b"NULL" in lib.gpe2p_last_error(None)
