@@ -150,10 +150,12 @@ int gpe2p_profile_steps(gpe2p_handle h, int nsteps, double *ms, int max_launches
                         char *names, int names_len);
 
 /* Device pointer of a field of the current state, in the handle's precision
- * (float or double), layout above: which = 0 p, 1 u, 2 v, 3 w, 4 phi, 5 mu.
- * Valid until the next call that advances, re-initialises or destroys the
- * handle. */
-int gpe2p_field_ptr(gpe2p_handle h, int which, void **dptr);
+ * (float or double): which = 0 p, 1 u, 2 v, 3 w, 4 phi, 5 mu.  On the device
+ * every field is stored x-fastest with rows padded to *row_pitch elements
+ * (a multiple of 32; row (j, k) starts at element (k ny + j) row_pitch);
+ * row_pitch may be NULL.  Valid until the next call that advances,
+ * re-initialises or destroys the handle. */
+int gpe2p_field_ptr(gpe2p_handle h, int which, void **dptr, long long *row_pitch);
 
 /* Text of the handle's last error ("" if none); with h == NULL, the last
  * error of a failed gpe2p_create on this thread. */

@@ -7,6 +7,8 @@
 #include <new>
 #include <string>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/gpe2p.h"
 #include "gpe2p_launch.h"
 
@@ -38,8 +40,14 @@ struct gpe2p_ctx {
   double* d_stage = nullptr;    // one FP64 field for host transfers
   double* d_part = nullptr;     // reduction scratch: 4 doubles per block
   double* d_out = nullptr;      // 4 reduced values
-  double* h_out = nullptr;      // pinned copy of d_out
+  double* h_out = nullptr;      // pinned copy of d_out (and the error word)
+  int* d_err = nullptr;         // device error word (a timed-out TMA copy)
+  long long pitch = 0;          // row pitch of every field, elements
   int nblk = 0;
+  // TMA tensor maps of the 3D kernels (one per staged field)
+  Maps<6> flow_maps[3];         // stage input Q[set] (p, u, v, w), phi, mu
+  Maps<5> ch_maps[3];           // (phi, mu), (phis0, mus), (phis1, mus), each with uhat
+  Maps<1> mu_maps[3];           // phi, phis0, phis1
   int cur = 0;                  // which Q set holds q^n (0 or 1)
   long long step = 0;
   int kchunk = 8;
@@ -192,6 +200,8 @@ extern "C" int gpe2p_stability_limits(const gpe2p_params* p, double out[3]) {
 // kernel parameters
 // ---------------------------------------------------------------------------
 
+static long long row_pitch(int nx) { return ((long long)nx + 31) / 32 * 32; }
+
 template <typename real>
 static KParams<real> kparams(const gpe2p_params& p) {
   KParams<real> P{};
@@ -201,8 +211,8 @@ static KParams<real> kparams(const gpe2p_params& p) {
   P.bc[0] = p.bc[0];
   P.bc[1] = p.bc[1];
   P.bc[2] = p.dim == 3 ? p.bc[2] : BC_PERIODIC;
-  P.sy = p.nx;
-  P.sz = (long long)p.nx * p.ny;
+  P.sy = row_pitch(p.nx);
+  P.sz = row_pitch(p.nx) * p.ny;
   P.dt = (real)p.dt;
   P.inv_dx = (real)(1.0 / p.dx);
   P.inv_dx2 = (real)(1.0 / (p.dx * p.dx));
@@ -275,17 +285,19 @@ static cudaError_t enqueue_step(gpe2p_ctx* h, int cur, ProfHook* hook = nullptr)
   A.mu = (const real*)h->mu;
   A.a = real(0);
   A.b = real(1);
-  cudaError_t e = launch_flow_stage<real, DIM>(P, A, 1, h->kchunk, s);
+  cudaError_t e = launch_flow_stage<real, DIM>(P, A, 1, h->kchunk, s, &h->flow_maps[cur], h->d_err);
   if (e != cudaSuccess || (e = mark("flow_stage1")) != cudaSuccess) return e;
   for (int f = 0; f < 4; ++f) { A.q[f] = q(s1, f); A.out[f] = q(s2, f); }
   A.a = real(0.75);
   A.b = real(0.25);
-  if ((e = launch_flow_stage<real, DIM>(P, A, 2, h->kchunk, s)) != cudaSuccess) return e;
+  if ((e = launch_flow_stage<real, DIM>(P, A, 2, h->kchunk, s, &h->flow_maps[s1], h->d_err)) != cudaSuccess)
+    return e;
   if ((e = mark("flow_stage2")) != cudaSuccess) return e;
   for (int f = 0; f < 4; ++f) { A.q[f] = q(s2, f); A.out[f] = q(s1, f); }
   A.a = real(1.0 / 3.0);
   A.b = real(2.0 / 3.0);
-  if ((e = launch_flow_stage<real, DIM>(P, A, 2, h->kchunk, s)) != cudaSuccess) return e;
+  if ((e = launch_flow_stage<real, DIM>(P, A, 2, h->kchunk, s, &h->flow_maps[s2], h->d_err)) != cudaSuccess)
+    return e;
   if ((e = mark("flow_stage3")) != cudaSuccess) return e;
 
   // Cahn-Hilliard step with the time-centred velocity of Eq. u-center-2d
@@ -312,26 +324,34 @@ static cudaError_t enqueue_step(gpe2p_ctx* h, int cur, ProfHook* hook = nullptr)
   real* F1 = (real*)h->phis[1];
   real* MS = (real*)h->mus;
   const int iso = h->prm.iso;
+  auto ch = [&](const real* phis) {
+    const int mi = phis == phi ? 0 : (phis == F0 ? 1 : 2);
+    return launch_ch_stage<real, DIM>(P, C, iso, h->kchunk, s, &h->ch_maps[mi], h->d_err);
+  };
+  auto mu_of = [&](const real* f, real* out) {
+    const int mi = f == phi ? 0 : (f == F0 ? 1 : 2);
+    return launch_mu<real, DIM>(P, f, out, iso, h->kchunk, s, &h->mu_maps[mi], h->d_err);
+  };
   if (C.scheme == 2) {
     C.stage = 1; C.phis = phi; C.mus = mu; C.out = F0; C.compute_uh = !C.conservative;
-    if ((e = launch_ch_stage<real, DIM>(P, C, iso, h->kchunk, s)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
-    if ((e = launch_mu<real, DIM>(P, F0, MS, iso, h->kchunk, s)) != cudaSuccess || (e = mark("mu")) != cudaSuccess) return e;
+    if ((e = ch(C.phis)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
+    if ((e = mu_of(F0, MS)) != cudaSuccess || (e = mark("mu")) != cudaSuccess) return e;
     C.stage = 2; C.phis = F0; C.mus = MS; C.out = phi; C.compute_uh = 0;
-    if ((e = launch_ch_stage<real, DIM>(P, C, iso, h->kchunk, s)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
+    if ((e = ch(C.phis)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
   } else {
     C.stage = 1; C.phis = phi; C.mus = mu; C.out = F0; C.compute_uh = !C.conservative;
-    if ((e = launch_ch_stage<real, DIM>(P, C, iso, h->kchunk, s)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
-    if ((e = launch_mu<real, DIM>(P, F0, MS, iso, h->kchunk, s)) != cudaSuccess || (e = mark("mu")) != cudaSuccess) return e;
+    if ((e = ch(C.phis)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
+    if ((e = mu_of(F0, MS)) != cudaSuccess || (e = mark("mu")) != cudaSuccess) return e;
     C.stage = 2; C.phis = F0; C.mus = MS; C.out = F1; C.compute_uh = 0;
-    if ((e = launch_ch_stage<real, DIM>(P, C, iso, h->kchunk, s)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
-    if ((e = launch_mu<real, DIM>(P, F1, MS, iso, h->kchunk, s)) != cudaSuccess || (e = mark("mu")) != cudaSuccess) return e;
+    if ((e = ch(C.phis)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
+    if ((e = mu_of(F1, MS)) != cudaSuccess || (e = mark("mu")) != cudaSuccess) return e;
     C.stage = 3; C.phis = F1; C.mus = MS; C.out = F0;
-    if ((e = launch_ch_stage<real, DIM>(P, C, iso, h->kchunk, s)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
-    if ((e = launch_mu<real, DIM>(P, F0, MS, iso, h->kchunk, s)) != cudaSuccess || (e = mark("mu")) != cudaSuccess) return e;
+    if ((e = ch(C.phis)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
+    if ((e = mu_of(F0, MS)) != cudaSuccess || (e = mark("mu")) != cudaSuccess) return e;
     C.stage = 4; C.phis = F0; C.mus = MS; C.out = phi;
-    if ((e = launch_ch_stage<real, DIM>(P, C, iso, h->kchunk, s)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
+    if ((e = ch(C.phis)) != cudaSuccess || (e = mark("ch_stage")) != cudaSuccess) return e;
   }
-  if ((e = launch_mu<real, DIM>(P, phi, mu, iso, h->kchunk, s)) != cudaSuccess) return e;
+  if ((e = mu_of(phi, mu)) != cudaSuccess) return e;
   return mark("mu");
 }
 
@@ -363,6 +383,58 @@ static int build_graphs(gpe2p_ctx* h) {
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+
+// ---------------------------------------------------------------------------
+// TMA tensor maps of the 3D kernels
+// ---------------------------------------------------------------------------
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// a field as a 3D tensor (x, y, z) with padded rows; box = one staged plane
+static bool encode_map(gpe2p_ctx* h, CUtensorMap* m, void* base) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) return false;
+  const int es = h->esize;
+  cuuint64_t dims[3] = {(cuuint64_t)h->prm.nx, (cuuint64_t)h->prm.ny, (cuuint64_t)h->prm.nz};
+  cuuint64_t strides[2] = {(cuuint64_t)(h->pitch * es), (cuuint64_t)(h->pitch * h->prm.ny * es)};
+  const int bx = es == 4 ? RingGeom<float>::BX : RingGeom<double>::BX;
+  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)SY, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base, dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+static int build_maps(gpe2p_ctx* h) {
+  bool ok = true;
+  for (int s = 0; s < 3; ++s) {
+    for (int f = 0; f < 4; ++f) ok = ok && encode_map(h, &h->flow_maps[s].m[f], h->Q[s][f]);
+    ok = ok && encode_map(h, &h->flow_maps[s].m[4], h->phi);
+    ok = ok && encode_map(h, &h->flow_maps[s].m[5], h->mu);
+  }
+  void* phis[3] = {h->phi, h->phis[0], h->phis[1]};
+  void* mus[3] = {h->mu, h->mus, h->mus};
+  for (int c = 0; c < 3; ++c) {
+    ok = ok && encode_map(h, &h->ch_maps[c].m[0], phis[c]);
+    ok = ok && encode_map(h, &h->ch_maps[c].m[1], mus[c]);
+    for (int a = 0; a < 3; ++a) ok = ok && encode_map(h, &h->ch_maps[c].m[2 + a], h->uh[a]);
+    ok = ok && encode_map(h, &h->mu_maps[c].m[0], phis[c]);
+  }
+  if (!ok) return fail(h, GPE2P_ECUDA, "cuTensorMapEncodeTiled failed or is unavailable");
+  return GPE2P_OK;
+}
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -404,14 +476,16 @@ extern "C" int gpe2p_create(const gpe2p_params* p, void* stream, gpe2p_handle* o
     }
     h->own_stream = true;
   }
-  // layout: 12 velocity/pressure fields, phi, mu, 2 stage phi, mus, acc, 3 uhat
-  const size_t fb = align256((size_t)h->ncell * h->esize);
+  // layout: 12 velocity/pressure fields, phi, mu, 2 stage phi, mus, acc, 3 uhat;
+  // every field has rows padded to a multiple of 32 elements (TMA strides)
+  h->pitch = row_pitch(h->prm.nx);
+  const size_t fb = align256((size_t)h->pitch * h->prm.ny * h->prm.nz * h->esize);
   const int nfield = 12 + 2 + 2 + 1 + 1 + 3;
   const size_t stage_b = align256((size_t)h->ncell * sizeof(double));
   const long long nb_blocks = (h->ncell + 255) / 256;
   h->nblk = (int)(nb_blocks < 152 * 8 ? nb_blocks : 152 * 8);
   const size_t part_b = align256((size_t)h->nblk * 4 * sizeof(double));
-  const size_t out_b = align256(4 * sizeof(double));
+  const size_t out_b = align256(4 * sizeof(double) + sizeof(int));
   const size_t total = fb * nfield + stage_b + part_b + out_b;
   e = cudaMalloc((void**)&h->base, total);
   if (e != cudaSuccess) {
@@ -431,12 +505,21 @@ extern "C" int gpe2p_create(const gpe2p_params* p, void* stream, gpe2p_handle* o
   h->d_stage = (double*)c; c += stage_b;
   h->d_part = (double*)c; c += part_b;
   h->d_out = (double*)c;
+  h->d_err = (int*)(h->d_out + 4);
   e = cudaMemsetAsync(h->base, 0, total, h->stream);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_out, 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&h->h_out, 5 * sizeof(double));
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     gpe2p_destroy(h);
     return fail(nullptr, GPE2P_ECUDA, std::string("set-up: ") + cudaGetErrorString(e));
+  }
+  if (h->prm.dim == 3) {
+    int rc = build_maps(h);
+    if (rc != GPE2P_OK) {
+      std::string why = h->err;
+      gpe2p_destroy(h);
+      return fail(nullptr, rc, why);
+    }
   }
   // z-chunk of the marching kernels: enough blocks to fill the GPU a few times
   if (h->prm.dim == 3) {
@@ -471,8 +554,11 @@ static cudaError_t init_impl(gpe2p_ctx* h, const double* phi, const double* u, c
     if ((e = put_field<real>(h, src[f], h->Q[0][f], f - 1)) != cudaSuccess) return e;
   if ((e = put_field<real>(h, phi, h->phi, -1)) != cudaSuccess) return e;
   const KParams<real> P = kparams<real>(h->prm);
-  if (h->prm.dim == 2) e = launch_mu<real, 2>(P, (real*)h->phi, (real*)h->mu, h->prm.iso, h->kchunk, h->stream);
-  else e = launch_mu<real, 3>(P, (real*)h->phi, (real*)h->mu, h->prm.iso, h->kchunk, h->stream);
+  if (h->prm.dim == 2)
+    e = launch_mu<real, 2>(P, (real*)h->phi, (real*)h->mu, h->prm.iso, h->kchunk, h->stream, nullptr, h->d_err);
+  else
+    e = launch_mu<real, 3>(P, (real*)h->phi, (real*)h->mu, h->prm.iso, h->kchunk, h->stream, &h->mu_maps[0],
+                           h->d_err);
   if (e != cudaSuccess) return e;
   return cudaStreamSynchronize(h->stream);
 }
@@ -509,8 +595,12 @@ static int diag_impl(gpe2p_ctx* h, gpe2p_diag* d) {
                                                  h->nblk, h->d_out, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics");
-  CK(h, cudaMemcpyAsync(h->h_out, h->d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream), "diag copy");
+  CK(h, cudaMemcpyAsync(h->h_out, h->d_out, 4 * sizeof(double) + sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+     "diag copy");
   CK(h, cudaStreamSynchronize(h->stream), "diag sync");
+  int errw = 0;
+  std::memcpy(&errw, h->h_out + 4, sizeof(int));
+  if (errw != 0) return fail(h, GPE2P_ETIMEOUT, "a device-side copy did not complete within its bounded wait");
   d->int_phi = h->h_out[0];
   d->kinetic = h->h_out[1];
   d->umax = h->h_out[2];
@@ -568,10 +658,10 @@ extern "C" int gpe2p_diagnostics(gpe2p_handle h, gpe2p_diag* out) {
 template <typename real>
 static cudaError_t get_field(gpe2p_ctx* h, const void* src, double* dst) {
   cudaError_t e;
-  if (sizeof(real) == 8) {
+  if (sizeof(real) == 8 && h->pitch == h->prm.nx) {
     e = cudaMemcpyAsync(dst, src, (size_t)h->ncell * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   } else {
-    e = launch_to_double<real>((const real*)src, h->d_stage, h->ncell, h->stream);
+    e = launch_to_double<real>(kparams<real>(h->prm), (const real*)src, h->d_stage, h->ncell, h->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dst, h->d_stage, (size_t)h->ncell * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   }
@@ -607,7 +697,7 @@ static cudaError_t rates_impl(gpe2p_ctx* h) {
   }
   A.phi = (const real*)h->phi;
   A.mu = (const real*)h->mu;
-  cudaError_t e = launch_flow_stage<real, DIM>(P, A, 0, h->kchunk, h->stream);
+  cudaError_t e = launch_flow_stage<real, DIM>(P, A, 0, h->kchunk, h->stream, &h->flow_maps[cur], h->d_err);
   if (e != cudaSuccess) return e;
   CHArgs<real> C{};
   for (int a = 0; a < 3; ++a) {
@@ -628,7 +718,7 @@ static cudaError_t rates_impl(gpe2p_ctx* h) {
   C.mus = (const real*)h->mu;
   C.phin = (const real*)h->phi;
   C.out = (real*)h->phis[0];
-  return launch_ch_stage<real, DIM>(P, C, h->prm.iso, h->kchunk, h->stream);
+  return launch_ch_stage<real, DIM>(P, C, h->prm.iso, h->kchunk, h->stream, &h->ch_maps[0], h->d_err);
 }
 
 extern "C" int gpe2p_eval_rates(gpe2p_handle h, double* Lp, double* Lu, double* Lv, double* Lw, double* Lphi) {
@@ -684,8 +774,9 @@ extern "C" int gpe2p_profile_steps(gpe2p_handle h, int nsteps, double* ms, int m
   return rc;
 }
 
-extern "C" int gpe2p_field_ptr(gpe2p_handle h, int which, void** dptr) {
+extern "C" int gpe2p_field_ptr(gpe2p_handle h, int which, void** dptr, long long* row_pitch) {
   if (!h || !dptr) return fail(h, GPE2P_EINVAL, "NULL argument");
+  if (row_pitch) *row_pitch = h->pitch;
   if (which < 0 || which > 5 || (which == 3 && h->prm.dim == 2)) return fail(h, GPE2P_EINVAL, "bad field index");
   void* src[6] = {h->Q[h->cur][0], h->Q[h->cur][1], h->Q[h->cur][2], h->Q[h->cur][3], h->phi, h->mu};
   *dptr = src[which];

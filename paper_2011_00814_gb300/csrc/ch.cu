@@ -6,6 +6,7 @@
 // halo in shared memory and marches along z in 3D.
 #include "gpe2p_dev.cuh"
 #include "gpe2p_launch.h"
+#include "ring3d.cuh"
 
 namespace gpe2p {
 
@@ -16,8 +17,8 @@ struct Shells {
   static constexpr bool s3 = ISO == 15 || ISO == 27;
 };
 
-template <typename real, int DIM, int ISO, int NPL>
-__device__ __forceinline__ real lap_iso(const Tile<real, NPL>& S, const KParams<real>& P, int f) {
+template <typename real, int DIM, int ISO, typename T>
+__device__ __forceinline__ real lap_iso(const T& S, const KParams<real>& P, int f) {
   real s = real(0);
 #pragma unroll
   for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
@@ -35,8 +36,8 @@ __device__ __forceinline__ real lap_iso(const Tile<real, NPL>& S, const KParams<
 }
 
 // the DIM components of the isotropic gradient of staged field f
-template <typename real, int DIM, int ISO, int NPL>
-__device__ __forceinline__ void grad_iso(const Tile<real, NPL>& S, const KParams<real>& P, int f, real g[3]) {
+template <typename real, int DIM, int ISO, typename T>
+__device__ __forceinline__ void grad_iso(const T& S, const KParams<real>& P, int f, real g[3]) {
   real s[3] = {real(0), real(0), real(0)};
 #pragma unroll
   for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
@@ -59,6 +60,104 @@ __device__ __forceinline__ void grad_iso(const Tile<real, NPL>& S, const KParams
 }
 
 enum { C_PHI = 0, C_MU = 1, C_UH = 2, C_N = 5 };
+
+// face value of component C on the high face of cell (i,j,k) (the low face of
+// the next cell along C): zero on a wall, wrapped when periodic
+template <int C, typename real>
+__device__ __forceinline__ real face_next(const real* __restrict__ f, const KParams<real>& P, int i, int j, int k,
+                                          long long id) {
+  const int x = C == 0 ? i : (C == 1 ? j : k);
+  const long long st = C == 0 ? 1 : (C == 1 ? P.sy : P.sz);
+  if (x + 1 < P.n[C]) return f[id + st];
+  if (P.bc[C] == BC_PERIODIC) return f[id + st - (long long)P.n[C] * st];
+  return real(0);
+}
+
+// the values a CH stage reads at the cell itself (no halo): the stage-1
+// time-centred velocity from the two face velocities (Eq. u-center-2d) or the
+// stored one, phi^{n+1/2} and the RK4 accumulator; loaded before the stencil
+// so that their latency overlaps the wait for the staged planes
+template <typename real>
+struct CHPoint {
+  real uh[3];
+  real pn, acc;
+};
+
+template <typename real, int DIM>
+__device__ __forceinline__ void ch_point_load(const KParams<real>& P, const CHArgs<real>& A, int i, int j, int k,
+                                              CHPoint<real>& c) {
+  const long long id = lin(P, i, j, k);
+  if (!A.conservative) {
+    if (A.compute_uh) {
+      c.uh[0] = real(0.25) * ((A.u0[0][id] + face_next<0>(A.u0[0], P, i, j, k, id)) +
+                              (A.u1[0][id] + face_next<0>(A.u1[0], P, i, j, k, id)));
+      c.uh[1] = real(0.25) * ((A.u0[1][id] + face_next<1>(A.u0[1], P, i, j, k, id)) +
+                              (A.u1[1][id] + face_next<1>(A.u1[1], P, i, j, k, id)));
+      if (DIM == 3)
+        c.uh[2] = real(0.25) * ((A.u0[2][id] + face_next<2>(A.u0[2], P, i, j, k, id)) +
+                                (A.u1[2][id] + face_next<2>(A.u1[2], P, i, j, k, id)));
+    } else {
+      for (int a = 0; a < DIM; ++a) c.uh[a] = A.uh[a][id];
+    }
+  }
+  if (A.stage != 0) c.pn = A.phin[id];
+  if (A.scheme == 4 && A.stage >= 2) c.acc = A.acc[id];
+}
+
+// one cell of a CH stage: the rate -uhat.grad(phi_s) + M lap(mu_s) (or its
+// conservative form) and the RK combination of the stage
+template <typename real, int DIM, int ISO, typename T>
+__device__ __forceinline__ void ch_cell(const T& S, const KParams<real>& P, const CHArgs<real>& A, int i, int j,
+                                        int k, const CHPoint<real>& c) {
+  const long long id = lin(P, i, j, k);
+  const real lapmu = lap_iso<real, DIM, ISO>(S, P, C_MU);
+  real adv = real(0);
+  if (!A.conservative) {
+    if (A.compute_uh && A.stage != 0)
+      for (int a = 0; a < DIM; ++a) A.uh[a][id] = c.uh[a];
+    real g[3];
+    grad_iso<real, DIM, ISO>(S, P, C_PHI, g);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) adv += c.uh[a] * g[a];
+  } else {
+    // -div_iso(uhat phi): the isotropic first derivative of the product
+    real s[3] = {real(0), real(0), real(0)};
+#pragma unroll
+    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int sh = dx * dx + dy * dy + dz * dz;
+          if (sh == 0) continue;
+          if (sh == 2 && !Shells<ISO>::s2) continue;
+          if (sh == 3 && !Shells<ISO>::s3) continue;
+          const real w = shell_w(P, sh);
+          const real ph = S(C_PHI, dx, dy, dz);
+          if (dx != 0) s[0] += (dx > 0 ? w : -w) * S(C_UH + 0, dx, dy, dz) * ph;
+          if (dy != 0) s[1] += (dy > 0 ? w : -w) * S(C_UH + 1, dx, dy, dz) * ph;
+          if (DIM == 3 && dz != 0) s[2] += (dz > 0 ? w : -w) * S(C_UH + 2, dx, dy, dz) * ph;
+        }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) adv += P.grad_c * s[a];
+  }
+  const real L = -adv + P.M * lapmu;
+  real o;
+  if (A.stage == 0) {
+    o = L;
+  } else if (A.scheme == 2) {
+    if (A.stage == 1) o = c.pn + P.dt * L;
+    else o = real(0.5) * c.pn + real(0.5) * (S(C_PHI, 0, 0, 0) + P.dt * L);
+  } else {
+    const real d = P.dt * L;
+    const real pn = c.pn;
+    if (A.stage == 1) { A.acc[id] = d; o = pn + real(0.5) * d; }
+    else if (A.stage == 2) { A.acc[id] = c.acc + real(2) * d; o = pn + real(0.5) * d; }
+    else if (A.stage == 3) { A.acc[id] = c.acc + real(2) * d; o = pn + d; }
+    else { o = pn + (c.acc + d) / real(6); }
+  }
+  A.out[id] = o;
+}
 
 template <typename real, int DIM, int ISO>
 __global__ void __launch_bounds__(NTHR) ch_stage_kernel(const KParams<real> P, const CHArgs<real> A,
@@ -106,66 +205,9 @@ __global__ void __launch_bounds__(NTHR) ch_stage_kernel(const KParams<real> P, c
       S.s0 = DIM == 3 ? k % 3 : 0;
       S.sm1 = DIM == 3 ? (k + 2) % 3 : 0;
       S.sp1 = DIM == 3 ? (k + 1) % 3 : 0;
-      const long long id = lin(P, i, j, k);
-      const real lapmu = lap_iso<real, DIM, ISO, NPL>(S, P, C_MU);
-      real adv = real(0);
-      if (!cons) {
-        real uh[3];
-        if (A.compute_uh) {
-          uh[0] = real(0.25) * ((ld_face<0>(A.u0[0], P, i, j, k) + ld_face<0>(A.u0[0], P, i + 1, j, k)) +
-                                (ld_face<0>(A.u1[0], P, i, j, k) + ld_face<0>(A.u1[0], P, i + 1, j, k)));
-          uh[1] = real(0.25) * ((ld_face<1>(A.u0[1], P, i, j, k) + ld_face<1>(A.u0[1], P, i, j + 1, k)) +
-                                (ld_face<1>(A.u1[1], P, i, j, k) + ld_face<1>(A.u1[1], P, i, j + 1, k)));
-          if (DIM == 3)
-            uh[2] = real(0.25) * ((ld_face<2>(A.u0[2], P, i, j, k) + ld_face<2>(A.u0[2], P, i, j, k + 1)) +
-                                  (ld_face<2>(A.u1[2], P, i, j, k) + ld_face<2>(A.u1[2], P, i, j, k + 1)));
-          if (A.stage != 0)
-            for (int a = 0; a < DIM; ++a) A.uh[a][id] = uh[a];
-        } else {
-          for (int a = 0; a < DIM; ++a) uh[a] = A.uh[a][id];
-        }
-        real g[3];
-        grad_iso<real, DIM, ISO, NPL>(S, P, C_PHI, g);
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) adv += uh[a] * g[a];
-      } else {
-        // -div_iso(uhat phi): the isotropic first derivative of the product
-        real s[3] = {real(0), real(0), real(0)};
-#pragma unroll
-        for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
-#pragma unroll
-          for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-            for (int dx = -1; dx <= 1; ++dx) {
-              const int sh = dx * dx + dy * dy + dz * dz;
-              if (sh == 0) continue;
-              if (sh == 2 && !Shells<ISO>::s2) continue;
-              if (sh == 3 && !Shells<ISO>::s3) continue;
-              const real w = shell_w(P, sh);
-              const real ph = S(C_PHI, dx, dy, dz);
-              if (dx != 0) s[0] += (dx > 0 ? w : -w) * S(C_UH + 0, dx, dy, dz) * ph;
-              if (dy != 0) s[1] += (dy > 0 ? w : -w) * S(C_UH + 1, dx, dy, dz) * ph;
-              if (DIM == 3 && dz != 0) s[2] += (dz > 0 ? w : -w) * S(C_UH + 2, dx, dy, dz) * ph;
-            }
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) adv += P.grad_c * s[a];
-      }
-      const real L = -adv + P.M * lapmu;
-      real o;
-      if (A.stage == 0) {
-        o = L;
-      } else if (A.scheme == 2) {
-        if (A.stage == 1) o = A.phin[id] + P.dt * L;
-        else o = real(0.5) * A.phin[id] + real(0.5) * (S(C_PHI, 0, 0, 0) + P.dt * L);
-      } else {
-        const real d = P.dt * L;
-        const real pn = A.phin[id];
-        if (A.stage == 1) { A.acc[id] = d; o = pn + real(0.5) * d; }
-        else if (A.stage == 2) { A.acc[id] = A.acc[id] + real(2) * d; o = pn + real(0.5) * d; }
-        else if (A.stage == 3) { A.acc[id] = A.acc[id] + real(2) * d; o = pn + d; }
-        else { o = pn + (A.acc[id] + d) / real(6); }
-      }
-      A.out[id] = o;
+      CHPoint<real> c;
+      ch_point_load<real, DIM>(P, A, i, j, k, c);
+      ch_cell<real, DIM, ISO>(S, P, A, i, j, k, c);
     }
     __syncthreads();
   }
@@ -207,22 +249,151 @@ __global__ void __launch_bounds__(NTHR) mu_kernel(const KParams<real> P, const r
       S.sm1 = DIM == 3 ? (k + 2) % 3 : 0;
       S.sp1 = DIM == 3 ? (k + 1) % 3 : 0;
       const real f = S(0, 0, 0, 0);
-      mu[lin(P, i, j, k)] = P.a4 * f * (f * f - real(1)) - P.kappa * lap_iso<real, DIM, ISO, NPL>(S, P, 0);
+      mu[lin(P, i, j, k)] = P.a4 * f * (f * f - real(1)) - P.kappa * lap_iso<real, DIM, ISO>(S, P, 0);
     }
     __syncthreads();
   }
 }
+
+// ---------------------------------------------------------------------------
+// 3D: the CH stage and mu fed by the TMA plane ring of ring3d.cuh
+// ---------------------------------------------------------------------------
+
+template <typename real, int NRAW>
+struct RawTile {
+  using G = RingGeom<real>;
+  const real* r[3];
+  int c;
+  __device__ __forceinline__ real operator()(int f, int dx, int dy, int dz) const {
+    return r[dz + 1][f * G::PE + c + dy * G::BX + dx];
+  }
+};
+
+// wait for plane kk, refill the slot of plane kk - 3 + RING, overwrite the
+// out-of-domain cells of the staged fields with the boundary rules
+template <typename real, int NRAW, int RING, typename Fix>
+__device__ __forceinline__ bool ring_acquire(Ring<real, NRAW, RING>& R, const KParams<real>& P,
+                                             const CUtensorMap* maps, int kk, bool refill, bool edge_tile,
+                                             Fix fix) {
+  using G = RingGeom<real>;
+  if (!R.wait(kk)) return false;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  if (refill && tid == 0) R.refill(P, maps, kk);
+  const bool ghost_plane = kk < 0 || kk >= P.n[2];
+  if (ghost_plane || edge_tile) {
+    const int ncell = ghost_plane ? SX * SY : PERIM;
+    for (int q = tid; q < ncell; q += NTHR) {
+      int lx, ly;
+      if (ghost_plane) { ly = q / SX; lx = q - ly * SX; }
+      else perim_cell(q, lx, ly);
+      const int gi = R.i0 - 1 + lx, gj = R.j0 - 1 + ly;
+      if (ghost_plane || gi < 0 || gi >= P.n[0] || gj < 0 || gj >= P.n[1]) {
+        const int ci = clampi(gi, -1, P.n[0]), cj = clampi(gj, -1, P.n[1]);
+        const int e = G::at(lx, ly);
+#pragma unroll
+        for (int f = 0; f < NRAW; ++f) R.plane(kk, f)[e] = fix(f, ci, cj, kk);
+      }
+    }
+    fence_proxy_async_smem();
+  }
+  return true;
+}
+
+template <typename real, int ISO, int CONS, int RING>
+__global__ void __launch_bounds__(NTHR) ch3d_kernel(const __grid_constant__ Maps<5> maps, const KParams<real> P,
+                                                    const CHArgs<real> A, const int kchunk, int* err) {
+  constexpr int NRAW = CONS ? 5 : 2;
+  using G = RingGeom<real>;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  Ring<real, NRAW, RING> R;
+  unsigned char* sbase = smem_base128(smraw);
+  R.bar = reinterpret_cast<uint64_t*>(sbase);
+  R.raw = reinterpret_cast<real*>(sbase + 128);
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(kbeg + kchunk, P.n[2]);
+  const int nx = P.n[0], ny = P.n[1];
+  const bool edge_tile = i0 == 0 || i0 + TX + 1 > nx || j0 == 0 || j0 + TY + 1 > ny;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool active = i < nx && j < ny;
+  auto fix = [&](int f, int ci, int cj, int kk) -> real {
+    switch (f) {
+      case C_PHI: return ld_cen(A.phis, P, ci, cj, kk);
+      case C_MU: return ld_cen(A.mus, P, ci, cj, kk);
+      case C_UH + 0: return ld_cvec<0>(A.uh[0], P, ci, cj, kk);
+      case C_UH + 1: return ld_cvec<1>(A.uh[1], P, ci, cj, kk);
+      default: return ld_cvec<2>(A.uh[2], P, ci, cj, kk);
+    }
+  };
+  R.start(P, maps.m, kbeg, kend, i0, j0);
+  if (!ring_acquire(R, P, maps.m, kbeg - 1, false, edge_tile, fix)) { R.fail(err, kbeg - 1); return; }
+  if (!ring_acquire(R, P, maps.m, kbeg, false, edge_tile, fix)) { R.fail(err, kbeg); return; }
+  for (int k = kbeg; k < kend; ++k) {
+    CHPoint<real> c;
+    if (active) ch_point_load<real, 3>(P, A, i, j, k, c);
+    if (!ring_acquire(R, P, maps.m, k + 1, true, edge_tile, fix)) { R.fail(err, k + 1); return; }
+    __syncthreads();
+    if (active) {
+      RawTile<real, NRAW> S;
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz) S.r[dz + 1] = R.plane(k + dz, 0);
+      S.c = G::at(tx + 1, ty + 1);
+      ch_cell<real, 3, ISO>(S, P, A, i, j, k, c);
+    }
+  }
+}
+
+template <typename real, int ISO, int RING>
+__global__ void __launch_bounds__(NTHR) mu3d_kernel(const __grid_constant__ Maps<1> maps, const KParams<real> P,
+                                                    const real* __restrict__ phi, real* __restrict__ mu,
+                                                    const int kchunk, int* err) {
+  using G = RingGeom<real>;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  Ring<real, 1, RING> R;
+  unsigned char* sbase = smem_base128(smraw);
+  R.bar = reinterpret_cast<uint64_t*>(sbase);
+  R.raw = reinterpret_cast<real*>(sbase + 128);
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(kbeg + kchunk, P.n[2]);
+  const int nx = P.n[0], ny = P.n[1];
+  const bool edge_tile = i0 == 0 || i0 + TX + 1 > nx || j0 == 0 || j0 + TY + 1 > ny;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool active = i < nx && j < ny;
+  auto fix = [&](int, int ci, int cj, int kk) -> real { return ld_cen(phi, P, ci, cj, kk); };
+  R.start(P, maps.m, kbeg, kend, i0, j0);
+  if (!ring_acquire(R, P, maps.m, kbeg - 1, false, edge_tile, fix)) { R.fail(err, kbeg - 1); return; }
+  if (!ring_acquire(R, P, maps.m, kbeg, false, edge_tile, fix)) { R.fail(err, kbeg); return; }
+  for (int k = kbeg; k < kend; ++k) {
+    if (!ring_acquire(R, P, maps.m, k + 1, true, edge_tile, fix)) { R.fail(err, k + 1); return; }
+    __syncthreads();
+    if (active) {
+      RawTile<real, 1> S;
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz) S.r[dz + 1] = R.plane(k + dz, 0);
+      S.c = G::at(tx + 1, ty + 1);
+      const real f = S(0, 0, 0, 0);
+      mu[lin(P, i, j, k)] = P.a4 * f * (f * f - real(1)) - P.kappa * lap_iso<real, 3, ISO>(S, P, 0);
+    }
+  }
+}
+
+template <typename real>
+constexpr int ch_ring() { return 8; }
 
 template <typename real, int DIM>
 __global__ void center_velocity_kernel(const KParams<real> P, const real* u00, const real* u01,
                                        const real* u02, const real* u10, const real* u11, const real* u12,
                                        real* uh0, real* uh1, real* uh2) {
   const long long n = (long long)P.n[0] * P.n[1] * P.n[2];
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
-       id += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(id % P.n[0]);
-    const int j = (int)((id / P.n[0]) % P.n[1]);
-    const int k = (int)(id / ((long long)P.n[0] * P.n[1]));
+  for (long long d = blockIdx.x * (long long)blockDim.x + threadIdx.x; d < n;
+       d += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(d % P.n[0]);
+    const int j = (int)((d / P.n[0]) % P.n[1]);
+    const int k = (int)(d / ((long long)P.n[0] * P.n[1]));
+    const long long id = lin(P, i, j, k);
     uh0[id] = real(0.25) * ((ld_face<0>(u00, P, i, j, k) + ld_face<0>(u00, P, i + 1, j, k)) +
                             (ld_face<0>(u10, P, i, j, k) + ld_face<0>(u10, P, i + 1, j, k)));
     uh1[id] = real(0.25) * ((ld_face<1>(u01, P, i, j, k) + ld_face<1>(u01, P, i, j + 1, k)) +
@@ -239,48 +410,78 @@ static size_t ch_smem() {
 }
 
 template <typename real, int DIM, int ISO>
-static cudaError_t ch_go(const KParams<real>& P, const CHArgs<real>& A, int kchunk, cudaStream_t s) {
-  const size_t sm = ch_smem<real, DIM>();
-  cudaError_t e = cudaFuncSetAttribute(ch_stage_kernel<real, DIM, ISO>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
+static cudaError_t ch_go(const KParams<real>& P, const CHArgs<real>& A, int kchunk, cudaStream_t s,
+                         const Maps<5>* maps, int* err) {
   dim3 blk(TX, TY, 1);
   dim3 grd((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY, DIM == 3 ? (P.n[2] + kchunk - 1) / kchunk : 1);
-  ch_stage_kernel<real, DIM, ISO><<<grd, blk, sm, s>>>(P, A, kchunk);
+  cudaError_t e;
+  if constexpr (DIM == 3) {
+    constexpr int RING = ch_ring<real>();
+    if (A.conservative) {
+      const size_t sm = ring_smem_bytes<real, 5, 0, RING>();
+      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 1, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sm);
+      if (e != cudaSuccess) return e;
+      ch3d_kernel<real, ISO, 1, RING><<<grd, blk, sm, s>>>(*maps, P, A, kchunk, err);
+    } else {
+      const size_t sm = ring_smem_bytes<real, 2, 0, RING>();
+      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 0, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sm);
+      if (e != cudaSuccess) return e;
+      ch3d_kernel<real, ISO, 0, RING><<<grd, blk, sm, s>>>(*maps, P, A, kchunk, err);
+    }
+  } else {
+    const size_t sm = ch_smem<real, DIM>();
+    e = cudaFuncSetAttribute(ch_stage_kernel<real, DIM, ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm);
+    if (e != cudaSuccess) return e;
+    ch_stage_kernel<real, DIM, ISO><<<grd, blk, sm, s>>>(P, A, kchunk);
+  }
   return cudaGetLastError();
 }
 
 template <typename real, int DIM>
 cudaError_t launch_ch_stage(const KParams<real>& P, const CHArgs<real>& A, int iso, int kchunk,
-                            cudaStream_t s) {
+                            cudaStream_t s, const Maps<5>* maps, int* err) {
   if constexpr (DIM == 2) {
-    return ch_go<real, DIM, 9>(P, A, kchunk, s);
+    return ch_go<real, DIM, 9>(P, A, kchunk, s, maps, err);
   } else {
     switch (iso) {
-      case 15: return ch_go<real, DIM, 15>(P, A, kchunk, s);
-      case 19: return ch_go<real, DIM, 19>(P, A, kchunk, s);
-      default: return ch_go<real, DIM, 27>(P, A, kchunk, s);
+      case 15: return ch_go<real, DIM, 15>(P, A, kchunk, s, maps, err);
+      case 19: return ch_go<real, DIM, 19>(P, A, kchunk, s, maps, err);
+      default: return ch_go<real, DIM, 27>(P, A, kchunk, s, maps, err);
     }
   }
 }
 
 template <typename real, int DIM, int ISO>
-static cudaError_t mu_go(const KParams<real>& P, const real* phi, real* mu, int kchunk, cudaStream_t s) {
+static cudaError_t mu_go(const KParams<real>& P, const real* phi, real* mu, int kchunk, cudaStream_t s,
+                         const Maps<1>* maps, int* err) {
   dim3 blk(TX, TY, 1);
   dim3 grd((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY, DIM == 3 ? (P.n[2] + kchunk - 1) / kchunk : 1);
-  mu_kernel<real, DIM, ISO><<<grd, blk, 0, s>>>(P, phi, mu, kchunk);
+  if constexpr (DIM == 3) {
+    constexpr int RING = ch_ring<real>();
+    const size_t sm = ring_smem_bytes<real, 1, 0, RING>();
+    cudaError_t e = cudaFuncSetAttribute(mu3d_kernel<real, ISO, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    mu3d_kernel<real, ISO, RING><<<grd, blk, sm, s>>>(*maps, P, phi, mu, kchunk, err);
+  } else {
+    mu_kernel<real, DIM, ISO><<<grd, blk, 0, s>>>(P, phi, mu, kchunk);
+  }
   return cudaGetLastError();
 }
 
 template <typename real, int DIM>
-cudaError_t launch_mu(const KParams<real>& P, const real* phi, real* mu, int iso, int kchunk, cudaStream_t s) {
+cudaError_t launch_mu(const KParams<real>& P, const real* phi, real* mu, int iso, int kchunk, cudaStream_t s,
+                      const Maps<1>* maps, int* err) {
   if constexpr (DIM == 2) {
-    return mu_go<real, DIM, 9>(P, phi, mu, kchunk, s);
+    return mu_go<real, DIM, 9>(P, phi, mu, kchunk, s, maps, err);
   } else {
     switch (iso) {
-      case 15: return mu_go<real, DIM, 15>(P, phi, mu, kchunk, s);
-      case 19: return mu_go<real, DIM, 19>(P, phi, mu, kchunk, s);
-      default: return mu_go<real, DIM, 27>(P, phi, mu, kchunk, s);
+      case 15: return mu_go<real, DIM, 15>(P, phi, mu, kchunk, s, maps, err);
+      case 19: return mu_go<real, DIM, 19>(P, phi, mu, kchunk, s, maps, err);
+      default: return mu_go<real, DIM, 27>(P, phi, mu, kchunk, s, maps, err);
     }
   }
 }
@@ -297,8 +498,10 @@ cudaError_t launch_center_velocity(const KParams<real>& P, const real* const u0[
 }
 
 #define GPE2P_CH_INST(R, D)                                                                                 \
-  template cudaError_t launch_ch_stage<R, D>(const KParams<R>&, const CHArgs<R>&, int, int, cudaStream_t); \
-  template cudaError_t launch_mu<R, D>(const KParams<R>&, const R*, R*, int, int, cudaStream_t);           \
+  template cudaError_t launch_ch_stage<R, D>(const KParams<R>&, const CHArgs<R>&, int, int, cudaStream_t,   \
+                                             const Maps<5>*, int*);                                        \
+  template cudaError_t launch_mu<R, D>(const KParams<R>&, const R*, R*, int, int, cudaStream_t, const Maps<1>*, \
+                                       int*);                                                              \
   template cudaError_t launch_center_velocity<R, D>(const KParams<R>&, const R* const[3], const R* const[3], \
                                                     R* const[3], cudaStream_t);
 GPE2P_CH_INST(float, 2)

@@ -37,15 +37,16 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_partial_kernel(const KParam
     const int i = (int)(id % P.n[0]);
     const int j = (int)((id / P.n[0]) % P.n[1]);
     const int k = (int)(id / ((long long)P.n[0] * P.n[1]));
-    const double f = (double)phi[id];
+    const long long q = lin(P, i, j, k);
+    const double f = (double)phi[q];
     sphi += f;
-    if (!isfinite(f) || !isfinite((double)p[id])) bad = 1.0;
+    if (!isfinite(f) || !isfinite((double)p[q])) bad = 1.0;
     const double rho0 = 0.5 * ((double)P.rhoL * (1.0 + f) + (double)P.rhoG * (1.0 - f));
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
       const double fm = (double)ld_cen(phi, P, i - (c == 0), j - (c == 1), k - (c == 2));
       const double rhom = 0.5 * ((double)P.rhoL * (1.0 + fm) + (double)P.rhoG * (1.0 - fm));
-      const double uc = (double)U[c][id];
+      const double uc = (double)U[c][q];
       ke += 0.5 * (0.5 * (rhom + rho0)) * uc * uc;
       umax = fmax(umax, fabs(uc));
       if (!isfinite(uc)) bad = 1.0;
@@ -122,27 +123,33 @@ cudaError_t launch_diag(const KParams<real>& P, const real* p, const real* const
   return cudaGetLastError();
 }
 
+// dense FP64 (host layout) -> padded rows in the working precision
 template <typename real>
 __global__ void from_double_kernel(const KParams<real> P, const double* src, real* dst, int c, long long n) {
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
        id += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(id % P.n[0]);
+    const int j = (int)((id / P.n[0]) % P.n[1]);
+    const int k = (int)(id / ((long long)P.n[0] * P.n[1]));
     real v = (real)src[id];
     if (c >= 0 && P.bc[c] != BC_PERIODIC) {
-      const int i = (int)(id % P.n[0]);
-      const int j = (int)((id / P.n[0]) % P.n[1]);
-      const int k = (int)(id / ((long long)P.n[0] * P.n[1]));
       const int x = c == 0 ? i : (c == 1 ? j : k);
       if (x == 0) v = real(0);
     }
-    dst[id] = v;
+    dst[lin(P, i, j, k)] = v;
   }
 }
 
+// padded rows -> dense FP64
 template <typename real>
-__global__ void to_double_kernel(const real* src, double* dst, long long n) {
+__global__ void to_double_kernel(const KParams<real> P, const real* src, double* dst, long long n) {
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
-       id += (long long)gridDim.x * blockDim.x)
-    dst[id] = (double)src[id];
+       id += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(id % P.n[0]);
+    const int j = (int)((id / P.n[0]) % P.n[1]);
+    const int k = (int)(id / ((long long)P.n[0] * P.n[1]));
+    dst[id] = (double)src[lin(P, i, j, k)];
+  }
 }
 
 static unsigned grid_for(long long n) {
@@ -160,8 +167,8 @@ cudaError_t launch_from_double(const KParams<real>& P, const double* src, real* 
 }
 
 template <typename real>
-cudaError_t launch_to_double(const real* src, double* dst, long long n, cudaStream_t s) {
-  to_double_kernel<real><<<grid_for(n), 256, 0, s>>>(src, dst, n);
+cudaError_t launch_to_double(const KParams<real>& P, const real* src, double* dst, long long n, cudaStream_t s) {
+  to_double_kernel<real><<<grid_for(n), 256, 0, s>>>(P, src, dst, n);
   return cudaGetLastError();
 }
 
@@ -177,7 +184,9 @@ template cudaError_t launch_from_double<float>(const KParams<float>&, const doub
                                                cudaStream_t);
 template cudaError_t launch_from_double<double>(const KParams<double>&, const double*, double*, int,
                                                 long long, cudaStream_t);
-template cudaError_t launch_to_double<float>(const float*, double*, long long, cudaStream_t);
-template cudaError_t launch_to_double<double>(const double*, double*, long long, cudaStream_t);
+template cudaError_t launch_to_double<float>(const KParams<float>&, const float*, double*, long long,
+                                             cudaStream_t);
+template cudaError_t launch_to_double<double>(const KParams<double>&, const double*, double*, long long,
+                                              cudaStream_t);
 
 }  // namespace gpe2p

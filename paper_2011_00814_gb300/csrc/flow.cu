@@ -14,21 +14,57 @@
 // once per tile.
 #include "gpe2p_dev.cuh"
 #include "gpe2p_launch.h"
+#include "ring3d.cuh"
 
 namespace gpe2p {
 
 enum { F_P = 0, F_U = 1, F_V = 2, F_W = 3, F_PHI = 4, F_RHO = 5, F_ETA = 6, F_NU = 7, F_MU = 8, F_N = 9 };
+// precomputed per-cell quantities offered by the 3D ring accessor: the
+// divergence of the cell and the viscosity of the cell's low edge in each
+// coordinate plane (mean of eta over the four cells around the edge)
+enum { F_DIV = 9, F_EXY = 10, F_EXZ = 11, F_EYZ = 12 };
 
-template <typename real, int DIM>
+// accessors that stage only the raw fields (the 2D plane kernel)
+template <typename T>
+struct HasPre {
+  static constexpr bool value = false;
+};
+
+template <typename real, int DIM, typename T>
 struct FlowOps {
-  static constexpr int NPL = DIM == 3 ? 3 : 1;
-  using T = Tile<real, NPL>;
+  static constexpr bool PRE = HasPre<T>::value;
 
   // velocity divergence of the cell at offset (ox,oy,oz), Eq. div-v-discretization
   __device__ __forceinline__ static real div(const T& S, const KParams<real>& P, int ox, int oy, int oz) {
-    real d = (S(F_U, ox + 1, oy, oz) - S(F_U, ox, oy, oz)) + (S(F_V, ox, oy + 1, oz) - S(F_V, ox, oy, oz));
-    if (DIM == 3) d += S(F_W, ox, oy, oz + 1) - S(F_W, ox, oy, oz);
-    return d * P.inv_dx;
+    if constexpr (PRE) {
+      return S(F_DIV, ox, oy, oz);
+    } else {
+      real d = (S(F_U, ox + 1, oy, oz) - S(F_U, ox, oy, oz)) + (S(F_V, ox, oy + 1, oz) - S(F_V, ox, oy, oz));
+      if (DIM == 3) d += S(F_W, ox, oy, oz + 1) - S(F_W, ox, oy, oz);
+      return d * P.inv_dx;
+    }
+  }
+
+  // eta averaged over the four cells around the edge shared by the faces of
+  // components C and t (Eq. u-stress-discretization, eta bar at i, j+-1/2):
+  // the edge on the +t side (etp) or on the -t side (etm) of the C face
+  template <int C>
+  __device__ __forceinline__ static void edge_eta(const T& S, int t, real& etp, real& etm) {
+    const int cx = C == 0, cy = C == 1, cz = C == 2;
+    const int tx = t == 0, ty = t == 1, tz = t == 2;
+    if constexpr (PRE) {
+      const int a = C < t ? C : t, b = C < t ? t : C;
+      const int FE = (a == 0 && b == 1) ? F_EXY : ((a == 0 && b == 2) ? F_EXZ : F_EYZ);
+      etp = S(FE, tx, ty, tz);
+      etm = S(FE, 0, 0, 0);
+    } else {
+      etp = (S(F_ETA, 0, 0, 0) + S(F_ETA, tx, ty, tz) + S(F_ETA, -cx, -cy, -cz) +
+             S(F_ETA, tx - cx, ty - cy, tz - cz)) *
+            real(0.25);
+      etm = (S(F_ETA, 0, 0, 0) + S(F_ETA, -tx, -ty, -tz) + S(F_ETA, -cx, -cy, -cz) +
+             S(F_ETA, -tx - cx, -ty - cy, -tz - cz)) *
+            real(0.25);
+    }
   }
 
   // averaged pressure of the cell at offset o for the gradient along C
@@ -85,12 +121,8 @@ struct FlowOps {
       if (t == C) continue;
       const int tx = t == 0, ty = t == 1, tz = t == 2;
       const int FT = F_U + t;
-      const real etp = (S(F_ETA, 0, 0, 0) + S(F_ETA, tx, ty, tz) + S(F_ETA, -cx, -cy, -cz) +
-                        S(F_ETA, tx - cx, ty - cy, tz - cz)) *
-                       real(0.25);
-      const real etm = (S(F_ETA, 0, 0, 0) + S(F_ETA, -tx, -ty, -tz) + S(F_ETA, -cx, -cy, -cz) +
-                        S(F_ETA, -tx - cx, -ty - cy, -tz - cz)) *
-                       real(0.25);
+      real etp, etm;
+      edge_eta<C>(S, t, etp, etm);
       const real t_tt = (etp * (S(FC, tx, ty, tz) - uc0) - etm * (uc0 - S(FC, -tx, -ty, -tz))) * P.inv_dx2;
       const real t_tc = (etp * (S(FT, tx, ty, tz) - S(FT, tx - cx, ty - cy, tz - cz)) -
                          etm * (S(FT, 0, 0, 0) - S(FT, -cx, -cy, -cz))) *
@@ -108,7 +140,7 @@ struct FlowOps {
     const real grav = (rb - P.rho_ref) * P.g[C];
     const real force = -gradp + real(2) * t_cc + t_tr + t_b + st + grav;
     const real conv = uc0 * (S(FC, cx, cy, cz) - S(FC, -cx, -cy, -cz)) * P.inv_2dx + conv_tr;
-    return force / rb - conv;
+    return fdiv(force, rb) - conv;
   }
 };
 
@@ -139,7 +171,7 @@ __global__ void __launch_bounds__(NTHR) flow_stage_kernel(const KParams<real> P,
       b[(F_PHI * NPL) * PL] = phi;
       b[(F_RHO * NPL) * PL] = rho;
       b[(F_ETA * NPL) * PL] = eta;
-      b[(F_NU * NPL) * PL] = eta / rho;
+      b[(F_NU * NPL) * PL] = fdiv(eta, rho);
       b[(F_MU * NPL) * PL] = ld_cen(A.mu, P, gi, gj, kk);
     }
   };
@@ -162,7 +194,7 @@ __global__ void __launch_bounds__(NTHR) flow_stage_kernel(const KParams<real> P,
       S.s0 = DIM == 3 ? k % 3 : 0;
       S.sm1 = DIM == 3 ? (k + 2) % 3 : 0;
       S.sp1 = DIM == 3 ? (k + 1) % 3 : 0;
-      using Ops = FlowOps<real, DIM>;
+      using Ops = FlowOps<real, DIM, Tile<real, NPL>>;
       const real D0 = Ops::div(S, P, 0, 0, 0);
       real L[4];
       L[0] = Ops::rate_p(S, P, D0);
@@ -188,6 +220,173 @@ __global__ void __launch_bounds__(NTHR) flow_stage_kernel(const KParams<real> P,
   }
 }
 
+// ---------------------------------------------------------------------------
+// 3D: the same stage fed by the TMA plane ring of ring3d.cuh
+// ---------------------------------------------------------------------------
+
+// raw (copied) fields of the ring and the derived planes rho, eta, nu, the
+// divergence and the three edge viscosities
+enum { R_P = 0, R_U = 1, R_V = 2, R_W = 3, R_PHI = 4, R_MU = 5, NRAW_FLOW = 6 };
+enum { D_RHO = 0, D_ETA = 1, D_NU = 2, D_DIV = 3, D_EXY = 4, D_EXZ = 5, D_EYZ = 6, NDER_FLOW = 7 };
+
+template <typename real>
+struct RingTile {
+  using G = RingGeom<real>;
+  const real* r[3];  // raw plane of field 0 for planes k-1, k, k+1
+  const real* d[3];  // derived plane of rho for planes k-1, k, k+1
+  int c;             // the thread's cell within a plane
+  __device__ __forceinline__ real operator()(int f, int dx, int dy, int dz) const {
+    const int o = c + dy * G::BX + dx;
+    switch (f) {
+      case F_P: return r[dz + 1][R_P * G::PE + o];
+      case F_U: return r[dz + 1][R_U * G::PE + o];
+      case F_V: return r[dz + 1][R_V * G::PE + o];
+      case F_W: return r[dz + 1][R_W * G::PE + o];
+      case F_PHI: return r[dz + 1][R_PHI * G::PE + o];
+      case F_MU: return r[dz + 1][R_MU * G::PE + o];
+      case F_RHO: return d[dz + 1][D_RHO * G::PE + o];
+      case F_ETA: return d[dz + 1][D_ETA * G::PE + o];
+      case F_NU: return d[dz + 1][D_NU * G::PE + o];
+      case F_DIV: return d[dz + 1][D_DIV * G::PE + o];
+      case F_EXY: return d[dz + 1][D_EXY * G::PE + o];
+      case F_EXZ: return d[dz + 1][D_EXZ * G::PE + o];
+      default: return d[dz + 1][D_EYZ * G::PE + o];
+    }
+  }
+};
+template <typename real>
+struct HasPre<RingTile<real>> {
+  static constexpr bool value = true;
+};
+
+template <typename real, int MODE, int RING>
+__global__ void __launch_bounds__(NTHR) flow3d_kernel(const __grid_constant__ Maps<NRAW_FLOW> maps,
+                                                      const KParams<real> P, const FlowArgs<real> A,
+                                                      const int kchunk, int* err) {
+  using G = RingGeom<real>;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  Ring<real, NRAW_FLOW, RING> R;
+  unsigned char* sbase = smem_base128(smraw);
+  R.bar = reinterpret_cast<uint64_t*>(sbase);
+  R.raw = reinterpret_cast<real*>(sbase + 128);
+  real* der = R.raw + (size_t)RING * NRAW_FLOW * G::PE;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(kbeg + kchunk, P.n[2]);
+  const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+  const bool edge_tile = i0 == 0 || i0 + TX + 1 > nx || j0 == 0 || j0 + TY + 1 > ny;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool active = i < nx && j < ny;
+  auto dplane = [&](int kk) { return der + (size_t)((unsigned)(kk + 4) & 3u) * NDER_FLOW * G::PE; };
+
+  R.start(P, maps.m, kbeg, kend, i0, j0);
+
+  // wait for plane kk; overwrite its out-of-domain cells; derive rho, eta, nu
+  // of plane kk, then the divergence of plane kk - 1 and the edge viscosities
+  // of plane kk
+  auto acquire = [&](int kk, bool refill) -> bool {
+    if (!R.wait(kk)) return false;
+    if (refill && tid == 0) R.refill(P, maps.m, kk);
+    const bool ghost_plane = kk < 0 || kk >= nz;
+    real* pl[NRAW_FLOW];
+#pragma unroll
+    for (int f = 0; f < NRAW_FLOW; ++f) pl[f] = R.plane(kk, f);
+    real* dk = dplane(kk);
+    for (int idx = tid; idx < SX * SY; idx += NTHR) {
+      const int ly = idx / SX, lx = idx - ly * SX;
+      const int e = G::at(lx, ly);
+      if (ghost_plane || edge_tile) {
+        const int gi = i0 - 1 + lx, gj = j0 - 1 + ly;
+        if (ghost_plane || gi < 0 || gi >= nx || gj < 0 || gj >= ny) {
+          const int ci = clampi(gi, -1, nx), cj = clampi(gj, -1, ny);
+          pl[R_P][e] = ld_cen(A.q[0], P, ci, cj, kk);
+          pl[R_U][e] = ld_face<0>(A.q[1], P, ci, cj, kk);
+          pl[R_V][e] = ld_face<1>(A.q[2], P, ci, cj, kk);
+          pl[R_W][e] = ld_face<2>(A.q[3], P, ci, cj, kk);
+          pl[R_PHI][e] = ld_cen(A.phi, P, ci, cj, kk);
+          pl[R_MU][e] = ld_cen(A.mu, P, ci, cj, kk);
+        }
+      }
+      const real phi = pl[R_PHI][e];
+      const real rho = rho_of(P, phi), eta = eta_of(P, phi);
+      dk[D_RHO * G::PE + e] = rho;
+      dk[D_ETA * G::PE + e] = eta;
+      dk[D_NU * G::PE + e] = fdiv(eta, rho);
+    }
+    if (ghost_plane || edge_tile) fence_proxy_async_smem();
+    __syncthreads();
+    const bool have_prev = kk > R.first;
+    const real* um = R.plane(kk - 1, R_U);
+    const real* vm = R.plane(kk - 1, R_V);
+    const real* wm = R.plane(kk - 1, R_W);
+    const real* wk = pl[R_W];
+    real* dm = dplane(kk - 1);
+    const real* em = dplane(kk - 1) + D_ETA * G::PE;
+    const real* ek = dk + D_ETA * G::PE;
+    for (int idx = tid; idx < SX * SY; idx += NTHR) {
+      const int ly = idx / SX, lx = idx - ly * SX;
+      const int e = G::at(lx, ly);
+      if (have_prev && lx < SX - 1 && ly < SY - 1)
+        dm[D_DIV * G::PE + e] =
+            ((um[e + 1] - um[e]) + (vm[e + G::BX] - vm[e]) + (wk[e] - wm[e])) * P.inv_dx;
+      if (lx > 0 && ly > 0) {
+        dk[D_EXY * G::PE + e] = ((ek[e] + ek[e - 1]) + (ek[e - G::BX] + ek[e - 1 - G::BX])) * real(0.25);
+        if (have_prev) {
+          dk[D_EXZ * G::PE + e] = ((ek[e] + ek[e - 1]) + (em[e] + em[e - 1])) * real(0.25);
+          dk[D_EYZ * G::PE + e] = ((ek[e] + ek[e - G::BX]) + (em[e] + em[e - G::BX])) * real(0.25);
+        }
+      }
+    }
+    return true;
+  };
+
+  if (!acquire(kbeg - 1, false)) { R.fail(err, kbeg - 1); return; }
+  if (!acquire(kbeg, false)) { R.fail(err, kbeg); return; }
+  for (int k = kbeg; k < kend; ++k) {
+    const long long id = lin(P, i, j, k);
+    real q0v[4];
+    if (MODE == 2 && active) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) q0v[f] = A.q0[f][id];
+    }
+    if (!acquire(k + 1, true)) { R.fail(err, k + 1); return; }
+    __syncthreads();
+    if (active) {
+      RingTile<real> S;
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz) {
+        S.r[dz + 1] = R.plane(k + dz, 0);
+        S.d[dz + 1] = dplane(k + dz);
+      }
+      S.c = G::at(tx + 1, ty + 1);
+      using Ops = FlowOps<real, 3, RingTile<real>>;
+      const real D0 = Ops::div(S, P, 0, 0, 0);
+      real L[4];
+      L[0] = Ops::rate_p(S, P, D0);
+      L[1] = (P.bc[0] != BC_PERIODIC && i == 0) ? real(0) : Ops::template rate_vel<0>(S, P, D0);
+      L[2] = (P.bc[1] != BC_PERIODIC && j == 0) ? real(0) : Ops::template rate_vel<1>(S, P, D0);
+      L[3] = (P.bc[2] != BC_PERIODIC && k == 0) ? real(0) : Ops::template rate_vel<2>(S, P, D0);
+      const int F[4] = {F_P, F_U, F_V, F_W};
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        real o;
+        if (MODE == 0) {
+          o = L[f];
+        } else {
+          const real q = S(F[f], 0, 0, 0);
+          if (MODE == 1) o = q + P.dt * L[f];
+          else o = A.a * q0v[f] + A.b * (q + P.dt * L[f]);
+        }
+        A.out[f][id] = o;
+      }
+    }
+  }
+}
+
+template <typename real>
+constexpr int flow_ring() { return sizeof(real) == 4 ? 4 : 4; }
+
 template <typename real, int DIM>
 static size_t flow_smem() {
   return sizeof(real) * (size_t)F_N * (DIM == 3 ? 3 : 1) * PL;
@@ -195,30 +394,43 @@ static size_t flow_smem() {
 
 template <typename real, int DIM>
 cudaError_t launch_flow_stage(const KParams<real>& P, const FlowArgs<real>& A, int mode, int kchunk,
-                              cudaStream_t s) {
-  const size_t sm = flow_smem<real, DIM>();
+                              cudaStream_t s, const Maps<6>* maps, int* err) {
   dim3 blk(TX, TY, 1);
   dim3 grd((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY, DIM == 3 ? (P.n[2] + kchunk - 1) / kchunk : 1);
   cudaError_t e;
+  if constexpr (DIM == 3) {
+    constexpr int RING = flow_ring<real>();
+    const size_t sm = ring_smem_bytes<real, NRAW_FLOW, NDER_FLOW, RING>();
+#define GPE2P_FLOW3_CASE(M)                                                                                 \
+  e = cudaFuncSetAttribute(flow3d_kernel<real, M, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+  if (e != cudaSuccess) return e;                                                                           \
+  flow3d_kernel<real, M, RING><<<grd, blk, sm, s>>>(*maps, P, A, kchunk, err);
+    if (mode == 0) { GPE2P_FLOW3_CASE(0) }
+    else if (mode == 1) { GPE2P_FLOW3_CASE(1) }
+    else { GPE2P_FLOW3_CASE(2) }
+#undef GPE2P_FLOW3_CASE
+  } else {
+    const size_t sm = flow_smem<real, DIM>();
 #define GPE2P_FLOW_CASE(M)                                                                                \
   e = cudaFuncSetAttribute(flow_stage_kernel<real, DIM, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                            (int)sm);                                                                      \
   if (e != cudaSuccess) return e;                                                                         \
   flow_stage_kernel<real, DIM, M><<<grd, blk, sm, s>>>(P, A, kchunk);
-  if (mode == 0) { GPE2P_FLOW_CASE(0) }
-  else if (mode == 1) { GPE2P_FLOW_CASE(1) }
-  else { GPE2P_FLOW_CASE(2) }
+    if (mode == 0) { GPE2P_FLOW_CASE(0) }
+    else if (mode == 1) { GPE2P_FLOW_CASE(1) }
+    else { GPE2P_FLOW_CASE(2) }
 #undef GPE2P_FLOW_CASE
+  }
   return cudaGetLastError();
 }
 
-template cudaError_t launch_flow_stage<float, 2>(const KParams<float>&, const FlowArgs<float>&, int, int,
-                                                 cudaStream_t);
-template cudaError_t launch_flow_stage<float, 3>(const KParams<float>&, const FlowArgs<float>&, int, int,
-                                                 cudaStream_t);
-template cudaError_t launch_flow_stage<double, 2>(const KParams<double>&, const FlowArgs<double>&, int, int,
-                                                  cudaStream_t);
-template cudaError_t launch_flow_stage<double, 3>(const KParams<double>&, const FlowArgs<double>&, int, int,
-                                                  cudaStream_t);
+#define GPE2P_FLOW_INST(R, D)                                                                      \
+  template cudaError_t launch_flow_stage<R, D>(const KParams<R>&, const FlowArgs<R>&, int, int, cudaStream_t, \
+                                               const Maps<6>*, int*);
+GPE2P_FLOW_INST(float, 2)
+GPE2P_FLOW_INST(float, 3)
+GPE2P_FLOW_INST(double, 2)
+GPE2P_FLOW_INST(double, 3)
+#undef GPE2P_FLOW_INST
 
 }  // namespace gpe2p

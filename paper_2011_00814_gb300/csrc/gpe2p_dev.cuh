@@ -122,6 +122,11 @@ __device__ __forceinline__ real eta_of(const KParams<real>& P, real phi) {
   return real(0.5) * (P.etaL * (real(1) + phi) + P.etaG * (real(1) - phi));
 }
 
+// division: the FP32 path uses the fast approximate quotient (2 ulp), the
+// FP64 path the IEEE one
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+
 // ---------------------------------------------------------------------------
 // shared-memory tile: NF fields x NPL planes x (SX*SY)
 // ---------------------------------------------------------------------------

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "gpe2p_dev.cuh"
+#include "ring3d.cuh"
 
 namespace gpe2p {
 
@@ -36,18 +37,21 @@ struct CHArgs {
   int conservative;    // 1: -div(uhat phi) instead of -uhat.grad(phi)
 };
 
+// 3D launches read their haloed inputs through TMA tensor maps (one per
+// staged field, in the order the kernel stages them) and report a timed-out
+// copy in *err; 2D launches ignore both.
 template <typename real, int DIM>
 cudaError_t launch_flow_stage(const KParams<real>& P, const FlowArgs<real>& A, int mode, int kchunk,
-                              cudaStream_t s);
+                              cudaStream_t s, const Maps<6>* maps, int* err);
 
 template <typename real, int DIM>
 cudaError_t launch_ch_stage(const KParams<real>& P, const CHArgs<real>& A, int iso, int kchunk,
-                            cudaStream_t s);
+                            cudaStream_t s, const Maps<5>* maps, int* err);
 
 // mu = 4 a phi (phi^2 - 1) - kappa lap_iso phi   (Eq. chem-pot)
 template <typename real, int DIM>
 cudaError_t launch_mu(const KParams<real>& P, const real* phi, real* mu, int iso, int kchunk,
-                      cudaStream_t s);
+                      cudaStream_t s, const Maps<1>* maps, int* err);
 
 // uhat_a = 1/4 [(u0_a + u0_a(+e_a)) + (u1_a + u1_a(+e_a))]   (Eq. u-center-2d)
 template <typename real, int DIM>
@@ -66,6 +70,6 @@ template <typename real>
 cudaError_t launch_from_double(const KParams<real>& P, const double* src, real* dst, int c, long long n,
                                cudaStream_t s);
 template <typename real>
-cudaError_t launch_to_double(const real* src, double* dst, long long n, cudaStream_t s);
+cudaError_t launch_to_double(const KParams<real>& P, const real* src, double* dst, long long n, cudaStream_t s);
 
 }  // namespace gpe2p

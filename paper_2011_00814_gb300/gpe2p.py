@@ -74,7 +74,7 @@ def lib():
         L.gpe2p_read_fields.argtypes = [vp] + [dp] * 6
         L.gpe2p_diagnostics.argtypes = [vp, ctypes.POINTER(Diag)]
         L.gpe2p_eval_rates.argtypes = [vp] + [dp] * 5
-        L.gpe2p_field_ptr.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp)]
+        L.gpe2p_field_ptr.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_longlong)]
         L.gpe2p_profile_steps.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                           ctypes.c_char_p, ctypes.c_int]
         L.gpe2p_last_error.argtypes = [vp]
@@ -201,10 +201,12 @@ class Solver:
         nm = names.value.decode().split(",")
         return [(nm[i], ms[i]) for i in range(n.value)]
 
-    def field_ptr(self, name: str) -> int:
+    def field_ptr(self, name: str):
+        """(device pointer, row pitch in elements) of a field of the current state."""
         p = ctypes.c_void_p()
-        self._check(lib().gpe2p_field_ptr(self.h, FIELD[name], ctypes.byref(p)))
-        return p.value
+        pitch = ctypes.c_longlong()
+        self._check(lib().gpe2p_field_ptr(self.h, FIELD[name], ctypes.byref(p), ctypes.byref(pitch)))
+        return p.value, pitch.value
 
     def close(self):
         if getattr(self, "h", None):
