@@ -281,10 +281,14 @@ __device__ __forceinline__ bool ring_acquire(Ring<real, NRAW, RING>& R, const KP
   if (refill && tid == 0) R.refill(P, maps, kk);
   const bool ghost_plane = kk < 0 || kk >= P.n[2];
   if (ghost_plane || edge_tile) {
-    const int ncell = ghost_plane ? SX * SY : PERIM;
+    // a full tile can reach outside the domain only on the staged region's
+    // perimeter; a tile that overhangs the domain end has its ghost column or
+    // row inside the region, so it and a ghost plane are scanned in full
+    const bool full = ghost_plane || R.i0 + TX > P.n[0] || R.j0 + TY > P.n[1];
+    const int ncell = full ? SX * SY : PERIM;
     for (int q = tid; q < ncell; q += NTHR) {
       int lx, ly;
-      if (ghost_plane) { ly = q / SX; lx = q - ly * SX; }
+      if (full) { ly = q / SX; lx = q - ly * SX; }
       else perim_cell(q, lx, ly);
       const int gi = R.i0 - 1 + lx, gj = R.j0 - 1 + ly;
       if (ghost_plane || gi < 0 || gi >= P.n[0] || gj < 0 || gj >= P.n[1]) {

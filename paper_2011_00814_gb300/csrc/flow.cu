@@ -384,8 +384,11 @@ __global__ void __launch_bounds__(NTHR) flow3d_kernel(const __grid_constant__ Ma
   }
 }
 
+#ifndef GPE2P_FLOW_RING
+#define GPE2P_FLOW_RING 4
+#endif
 template <typename real>
-constexpr int flow_ring() { return sizeof(real) == 4 ? 4 : 4; }
+constexpr int flow_ring() { return GPE2P_FLOW_RING; }
 
 template <typename real, int DIM>
 static size_t flow_smem() {
