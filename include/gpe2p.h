@@ -157,6 +157,34 @@ int gpe2p_profile_steps(gpe2p_handle h, int nsteps, double *ms, int max_launches
  * re-initialises or destroys the handle. */
 int gpe2p_field_ptr(gpe2p_handle h, int which, void **dptr, long long *row_pitch);
 
+/* Largest number of cells gpe2p_diagnostics_noalloc accepts. */
+#define GPE2P_NOALLOC_MAX_CELLS 67108864LL
+
+/* The paper has no counterpart to this entry point: it serves callers that
+ * cannot allocate device memory when they need the diagnostics (inside a
+ * CUDA-graph capture or a custom memory pool, a device handed over to
+ * another allocator, a loop that must not block in cudaMalloc).  It computes
+ * the four values of gpe2p_diagnostics (sum of phi dx^dim, kinetic energy,
+ * max |velocity component|, NaN/Inf flag as 0.0/1.0, in that order) of a
+ * state the caller holds on the current device and writes them to out, a
+ * caller-owned device array of 4 doubles.
+ *   p, u, v, w, phi: device arrays in the precision p->precision (32: float,
+ *   64: double), in the layout of gpe2p_field_ptr with rows of row_pitch
+ *   elements (>= nx); w may be NULL in 2D.  Only the dim, nx, ny, nz, dx,
+ *   rhoL, rhoG, bc and precision members of *p are used.
+ *   stream: a cudaStream_t, or NULL for the legacy default stream.  The call
+ *   is asynchronous; out is valid once the stream has reached it.
+ * It allocates nothing: its scratch is a fixed device array of 512 KiB in the
+ * library, held by every GPU that loads the library until the process
+ * exits.  The first call on a device (with that device current) looks up
+ * that array's device address, so it should come before any stream capture.
+ * All calls share the array: calls whose work overlaps on the GPU race.
+ * Returns GPE2P_EINVAL for a NULL pointer, bad parameters or more than
+ * GPE2P_NOALLOC_MAX_CELLS cells, GPE2P_ECUDA if a launch fails; it records
+ * no error text. */
+int gpe2p_diagnostics_noalloc(const gpe2p_params *p, const void *pfield, const void *u, const void *v,
+                              const void *w, const void *phi, long long row_pitch, double *out, void *stream);
+
 /* Text of the handle's last error ("" if none); with h == NULL, the last
  * error of a failed gpe2p_create on this thread. */
 const char *gpe2p_last_error(gpe2p_handle h);

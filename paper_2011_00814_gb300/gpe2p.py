@@ -77,6 +77,9 @@ def lib():
         L.gpe2p_field_ptr.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_longlong)]
         L.gpe2p_profile_steps.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                           ctypes.c_char_p, ctypes.c_int]
+        L.gpe2p_diagnostics_noalloc.argtypes = [ctypes.POINTER(Params), vp, vp, vp, vp, vp, ctypes.c_longlong,
+                                                vp, vp]
+        L.gpe2p_diagnostics_noalloc.restype = ctypes.c_int
         L.gpe2p_last_error.argtypes = [vp]
         L.gpe2p_last_error.restype = ctypes.c_char_p
         L.gpe2p_destroy.argtypes = [vp]
