@@ -262,10 +262,10 @@ __global__ void __launch_bounds__(NTHR) mu_kernel(const KParams<real> P, const r
 template <typename real, int NRAW>
 struct RawTile {
   using G = RingGeom<real>;
-  const real* r[3];
-  int c;
+  const real* sm;  // the block's shared memory
+  int r[3];        // index of the thread's cell in field 0 of planes k-1, k, k+1
   __device__ __forceinline__ real operator()(int f, int dx, int dy, int dz) const {
-    return r[dz + 1][f * G::PE + c + dy * G::BX + dx];
+    return sm[r[dz + 1] + f * G::PE + dy * G::BX + dx];
   }
 };
 
@@ -340,9 +340,10 @@ __global__ void __launch_bounds__(NTHR) ch3d_kernel(const __grid_constant__ Maps
     __syncthreads();
     if (active) {
       RawTile<real, NRAW> S;
+      S.sm = reinterpret_cast<const real*>(smraw);
+      const int raw0 = (int)(R.raw - S.sm), cell = G::at(tx + 1, ty + 1);
 #pragma unroll
-      for (int dz = -1; dz <= 1; ++dz) S.r[dz + 1] = R.plane(k + dz, 0);
-      S.c = G::at(tx + 1, ty + 1);
+      for (int dz = -1; dz <= 1; ++dz) S.r[dz + 1] = raw0 + R.slot(k + dz) * NRAW * G::PE + cell;
       ch_cell<real, 3, ISO>(S, P, A, i, j, k, c);
     }
   }
@@ -375,9 +376,10 @@ __global__ void __launch_bounds__(NTHR) mu3d_kernel(const __grid_constant__ Maps
     __syncthreads();
     if (active) {
       RawTile<real, 1> S;
+      S.sm = reinterpret_cast<const real*>(smraw);
+      const int raw0 = (int)(R.raw - S.sm), cell = G::at(tx + 1, ty + 1);
 #pragma unroll
-      for (int dz = -1; dz <= 1; ++dz) S.r[dz + 1] = R.plane(k + dz, 0);
-      S.c = G::at(tx + 1, ty + 1);
+      for (int dz = -1; dz <= 1; ++dz) S.r[dz + 1] = raw0 + R.slot(k + dz) * G::PE + cell;
       const real f = S(0, 0, 0, 0);
       mu[lin(P, i, j, k)] = P.a4 * f * (f * f - real(1)) - P.kappa * lap_iso<real, 3, ISO>(S, P, 0);
     }

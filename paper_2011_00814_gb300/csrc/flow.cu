@@ -71,7 +71,11 @@ struct FlowOps {
   // (Eq. gradp-u-discretization in 2D, Eq. gradp-u-p-ave-3d in 3D)
   template <int C>
   __device__ __forceinline__ static real pbar(const T& S, const KParams<real>& P, int ox, int oy, int oz) {
-    if (!P.pavg) return S(F_P, ox, oy, oz);
+    if constexpr (T::PAVG == 0) {
+      return S(F_P, ox, oy, oz);
+    } else if constexpr (T::PAVG < 0) {
+      if (!P.pavg) return S(F_P, ox, oy, oz);
+    }
     if (DIM == 2) {
       constexpr int tx = C == 1, ty = C == 0;
       return (real(4) * S(F_P, ox, oy, oz) + S(F_P, ox + tx, oy + ty, oz) + S(F_P, ox - tx, oy - ty, oz)) *
@@ -229,38 +233,39 @@ __global__ void __launch_bounds__(NTHR) flow_stage_kernel(const KParams<real> P,
 enum { R_P = 0, R_U = 1, R_V = 2, R_W = 3, R_PHI = 4, R_MU = 5, NRAW_FLOW = 6 };
 enum { D_RHO = 0, D_ETA = 1, D_NU = 2, D_DIV = 3, D_EXY = 4, D_EXZ = 5, D_EYZ = 6, NDER_FLOW = 7 };
 
-template <typename real>
+template <typename real, int PAVG_>
 struct RingTile {
+  static constexpr int PAVG = PAVG_;
   using G = RingGeom<real>;
-  const real* r[3];  // raw plane of field 0 for planes k-1, k, k+1
-  const real* d[3];  // derived plane of rho for planes k-1, k, k+1
-  int c;             // the thread's cell within a plane
+  const real* sm;  // the block's shared memory
+  int r[3];        // index of the thread's cell in raw field 0 of planes k-1, k, k+1
+  int d[3];        // index of the thread's cell in derived field 0 of planes k-1, k, k+1
   __device__ __forceinline__ real operator()(int f, int dx, int dy, int dz) const {
-    const int o = c + dy * G::BX + dx;
+    const int o = dy * G::BX + dx;
     switch (f) {
-      case F_P: return r[dz + 1][R_P * G::PE + o];
-      case F_U: return r[dz + 1][R_U * G::PE + o];
-      case F_V: return r[dz + 1][R_V * G::PE + o];
-      case F_W: return r[dz + 1][R_W * G::PE + o];
-      case F_PHI: return r[dz + 1][R_PHI * G::PE + o];
-      case F_MU: return r[dz + 1][R_MU * G::PE + o];
-      case F_RHO: return d[dz + 1][D_RHO * G::PE + o];
-      case F_ETA: return d[dz + 1][D_ETA * G::PE + o];
-      case F_NU: return d[dz + 1][D_NU * G::PE + o];
-      case F_DIV: return d[dz + 1][D_DIV * G::PE + o];
-      case F_EXY: return d[dz + 1][D_EXY * G::PE + o];
-      case F_EXZ: return d[dz + 1][D_EXZ * G::PE + o];
-      default: return d[dz + 1][D_EYZ * G::PE + o];
+      case F_P: return sm[r[dz + 1] + R_P * G::PE + o];
+      case F_U: return sm[r[dz + 1] + R_U * G::PE + o];
+      case F_V: return sm[r[dz + 1] + R_V * G::PE + o];
+      case F_W: return sm[r[dz + 1] + R_W * G::PE + o];
+      case F_PHI: return sm[r[dz + 1] + R_PHI * G::PE + o];
+      case F_MU: return sm[r[dz + 1] + R_MU * G::PE + o];
+      case F_RHO: return sm[d[dz + 1] + D_RHO * G::PE + o];
+      case F_ETA: return sm[d[dz + 1] + D_ETA * G::PE + o];
+      case F_NU: return sm[d[dz + 1] + D_NU * G::PE + o];
+      case F_DIV: return sm[d[dz + 1] + D_DIV * G::PE + o];
+      case F_EXY: return sm[d[dz + 1] + D_EXY * G::PE + o];
+      case F_EXZ: return sm[d[dz + 1] + D_EXZ * G::PE + o];
+      default: return sm[d[dz + 1] + D_EYZ * G::PE + o];
     }
   }
 };
-template <typename real>
-struct HasPre<RingTile<real>> {
+template <typename real, int PAVG_>
+struct HasPre<RingTile<real, PAVG_>> {
   static constexpr bool value = true;
 };
 
-template <typename real, int MODE, int RING>
-__global__ void __launch_bounds__(NTHR) flow3d_kernel(const __grid_constant__ Maps<NRAW_FLOW> maps,
+template <typename real, int MODE, int RING, int PAVG>
+__global__ void __launch_bounds__(NTHR, 2) flow3d_kernel(const __grid_constant__ Maps<NRAW_FLOW> maps,
                                                       const KParams<real> P, const FlowArgs<real> A,
                                                       const int kchunk, int* err) {
   using G = RingGeom<real>;
@@ -343,8 +348,11 @@ __global__ void __launch_bounds__(NTHR) flow3d_kernel(const __grid_constant__ Ma
 
   if (!acquire(kbeg - 1, false)) { R.fail(err, kbeg - 1); return; }
   if (!acquire(kbeg, false)) { R.fail(err, kbeg); return; }
-  for (int k = kbeg; k < kend; ++k) {
-    const long long id = lin(P, i, j, k);
+  const real* smr = reinterpret_cast<const real*>(smraw);
+  const int raw0 = (int)(R.raw - smr), der0 = (int)(der - smr);
+  const int cell = G::at(tx + 1, ty + 1);
+  long long id = lin(P, i, j, kbeg);
+  for (int k = kbeg; k < kend; ++k, id += P.sz) {
     real q0v[4];
     if (MODE == 2 && active) {
 #pragma unroll
@@ -353,20 +361,24 @@ __global__ void __launch_bounds__(NTHR) flow3d_kernel(const __grid_constant__ Ma
     if (!acquire(k + 1, true)) { R.fail(err, k + 1); return; }
     __syncthreads();
     if (active) {
-      RingTile<real> S;
+      RingTile<real, PAVG> S;
+      S.sm = smr;
 #pragma unroll
       for (int dz = -1; dz <= 1; ++dz) {
-        S.r[dz + 1] = R.plane(k + dz, 0);
-        S.d[dz + 1] = dplane(k + dz);
+        S.r[dz + 1] = raw0 + R.slot(k + dz) * NRAW_FLOW * G::PE + cell;
+        S.d[dz + 1] = der0 + (int)((unsigned)(k + dz + 4) & 3u) * NDER_FLOW * G::PE + cell;
       }
-      S.c = G::at(tx + 1, ty + 1);
-      using Ops = FlowOps<real, 3, RingTile<real>>;
+      using Ops = FlowOps<real, 3, RingTile<real, PAVG>>;
       const real D0 = Ops::div(S, P, 0, 0, 0);
       real L[4];
       L[0] = Ops::rate_p(S, P, D0);
-      L[1] = (P.bc[0] != BC_PERIODIC && i == 0) ? real(0) : Ops::template rate_vel<0>(S, P, D0);
-      L[2] = (P.bc[1] != BC_PERIODIC && j == 0) ? real(0) : Ops::template rate_vel<1>(S, P, D0);
-      L[3] = (P.bc[2] != BC_PERIODIC && k == 0) ? real(0) : Ops::template rate_vel<2>(S, P, D0);
+      L[1] = Ops::template rate_vel<0>(S, P, D0);
+      L[2] = Ops::template rate_vel<1>(S, P, D0);
+      L[3] = Ops::template rate_vel<2>(S, P, D0);
+      // faces on a wall are never updated
+      if (P.bc[0] != BC_PERIODIC && i == 0) L[1] = real(0);
+      if (P.bc[1] != BC_PERIODIC && j == 0) L[2] = real(0);
+      if (P.bc[2] != BC_PERIODIC && k == 0) L[3] = real(0);
       const int F[4] = {F_P, F_U, F_V, F_W};
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
@@ -405,9 +417,17 @@ cudaError_t launch_flow_stage(const KParams<real>& P, const FlowArgs<real>& A, i
     constexpr int RING = flow_ring<real>();
     const size_t sm = ring_smem_bytes<real, NRAW_FLOW, NDER_FLOW, RING>();
 #define GPE2P_FLOW3_CASE(M)                                                                                 \
-  e = cudaFuncSetAttribute(flow3d_kernel<real, M, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-  if (e != cudaSuccess) return e;                                                                           \
-  flow3d_kernel<real, M, RING><<<grd, blk, sm, s>>>(*maps, P, A, kchunk, err);
+  if (P.pavg) {                                                                                             \
+    e = cudaFuncSetAttribute(flow3d_kernel<real, M, RING, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                             (int)sm);                                                                      \
+    if (e != cudaSuccess) return e;                                                                         \
+    flow3d_kernel<real, M, RING, 1><<<grd, blk, sm, s>>>(*maps, P, A, kchunk, err);                         \
+  } else {                                                                                                  \
+    e = cudaFuncSetAttribute(flow3d_kernel<real, M, RING, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                             (int)sm);                                                                      \
+    if (e != cudaSuccess) return e;                                                                         \
+    flow3d_kernel<real, M, RING, 0><<<grd, blk, sm, s>>>(*maps, P, A, kchunk, err);                         \
+  }
     if (mode == 0) { GPE2P_FLOW3_CASE(0) }
     else if (mode == 1) { GPE2P_FLOW3_CASE(1) }
     else { GPE2P_FLOW3_CASE(2) }

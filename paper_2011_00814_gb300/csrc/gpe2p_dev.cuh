@@ -133,6 +133,7 @@ __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 
 template <typename real, int NPL>
 struct Tile {
+  static constexpr int PAVG = -1;  // pressure averaging decided at run time
   const real* sm;
   int c;                 // index of the thread's cell within a plane
   int s0, sm1, sp1;      // plane slots of k, k-1, k+1
