@@ -16,6 +16,13 @@
 #include "gpe2p_launch.h"
 #include "ring3d.cuh"
 
+// Whether the 3D flow stage precomputes the divergence and the edge
+// viscosities per staged cell (fewer instructions per cell, but four more
+// shared-memory planes per derived slot, which costs occupancy).
+#ifndef GPE2P_FLOW_PRECOMPUTE
+#define GPE2P_FLOW_PRECOMPUTE 0
+#endif
+
 namespace gpe2p {
 
 enum { F_P = 0, F_U = 1, F_V = 2, F_W = 3, F_PHI = 4, F_RHO = 5, F_ETA = 6, F_NU = 7, F_MU = 8, F_N = 9 };
@@ -231,7 +238,8 @@ __global__ void __launch_bounds__(NTHR) flow_stage_kernel(const KParams<real> P,
 // raw (copied) fields of the ring and the derived planes rho, eta, nu, the
 // divergence and the three edge viscosities
 enum { R_P = 0, R_U = 1, R_V = 2, R_W = 3, R_PHI = 4, R_MU = 5, NRAW_FLOW = 6 };
-enum { D_RHO = 0, D_ETA = 1, D_NU = 2, D_DIV = 3, D_EXY = 4, D_EXZ = 5, D_EYZ = 6, NDER_FLOW = 7 };
+enum { D_RHO = 0, D_ETA = 1, D_NU = 2, D_DIV = 3, D_EXY = 4, D_EXZ = 5, D_EYZ = 6 };
+constexpr int NDER_FLOW = GPE2P_FLOW_PRECOMPUTE ? 7 : 3;
 
 template <typename real, int PAVG_>
 struct RingTile {
@@ -261,7 +269,7 @@ struct RingTile {
 };
 template <typename real, int PAVG_>
 struct HasPre<RingTile<real, PAVG_>> {
-  static constexpr bool value = true;
+  static constexpr bool value = GPE2P_FLOW_PRECOMPUTE != 0;
 };
 
 template <typename real, int MODE, int RING, int PAVG>
@@ -320,6 +328,7 @@ __global__ void __launch_bounds__(NTHR, 2) flow3d_kernel(const __grid_constant__
       dk[D_NU * G::PE + e] = fdiv(eta, rho);
     }
     if (ghost_plane || edge_tile) fence_proxy_async_smem();
+    if (!GPE2P_FLOW_PRECOMPUTE) return true;
     __syncthreads();
     const bool have_prev = kk > R.first;
     const real* um = R.plane(kk - 1, R_U);
