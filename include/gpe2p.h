@@ -157,6 +157,50 @@ int gpe2p_profile_steps(gpe2p_handle h, int nsteps, double *ms, int max_launches
  * re-initialises or destroys the handle. */
 int gpe2p_field_ptr(gpe2p_handle h, int which, void **dptr, long long *row_pitch);
 
+/* ---- batches of independent 2D problems ------------------------------ */
+
+/* Creates one handle for n independent 2D problems p[0..n-1] (uneven sizes,
+ * their own physical parameters and boundaries; one precision; TVD-RK2 for
+ * the CH step).  All instances advance together: gpe2p_step and
+ * gpe2p_advance run every sweep of the method over the tiles of all
+ * instances, either as one cooperative persistent launch per step whose
+ * blocks meet at a bounded grid barrier between sweeps, or as one launch per
+ * sweep; both are captured into CUDA graphs.  The tile shape and the form
+ * are chosen at creation by timing each candidate on the zero state (the
+ * state is zeroed again afterwards).  gpe2p_diagnostics of a batch sums
+ * int_phi and kinetic over the instances and takes the max of umax and the
+ * NaN flags; gpe2p_init_fields and gpe2p_read_fields do not apply to a batch
+ * (GPE2P_EINVAL): use the per-instance calls below. */
+int gpe2p_create_batch(const gpe2p_params *p, int n, void *stream, gpe2p_handle *out);
+
+/* Sets instance inst of a batch from host arrays (nx*ny doubles each, the
+ * layout of the single-problem calls; w is ignored) and computes its mu.
+ * Resets the batch's step counter.  Synchronises. */
+int gpe2p_init_instance(gpe2p_handle h, int inst, const double *phi, const double *u, const double *v,
+                        const double *w, const double *p);
+
+/* Copies instance inst of a batch to host arrays; NULL pointers are skipped. */
+int gpe2p_read_instance(gpe2p_handle h, int inst, double *phi, double *u, double *v, double *w, double *p,
+                        double *mu);
+
+/* Diagnostics of one instance of a batch. */
+int gpe2p_diagnostics_instance(gpe2p_handle h, int inst, gpe2p_diag *out);
+
+/* The configuration the autotuner chose for a batch: tile shape, 1 for the
+ * persistent form (0: one launch per sweep), and its measured ms per step. */
+int gpe2p_batch_config(gpe2p_handle h, int *tile_x, int *tile_y, int *persistent, double *ms_per_step);
+
+/* Host-side fault injection and test switches of a batch (rebuilds its step
+ * graphs): GPE2P_FAULT_SKIP_BARRIER (value = block index that never arrives
+ * at the grid barrier; -1 none), GPE2P_FAULT_WAIT_LIMIT (barrier wait limit
+ * in SM clock cycles), GPE2P_FAULT_FORCE_PERSISTENT (1: persistent form,
+ * 0: one launch per sweep), GPE2P_FAULT_CLEAR (defaults, and clears the
+ * error word).  A barrier wait that runs out makes every block return and
+ * the next diagnostics report GPE2P_ETIMEOUT; the state is then undefined. */
+enum { GPE2P_FAULT_SKIP_BARRIER = 1, GPE2P_FAULT_WAIT_LIMIT = 2, GPE2P_FAULT_FORCE_PERSISTENT = 3,
+       GPE2P_FAULT_CLEAR = 4 };
+int gpe2p_set_fault_injection(gpe2p_handle h, int what, long long value);
+
 /* Largest number of cells gpe2p_diagnostics_noalloc accepts. */
 #define GPE2P_NOALLOC_MAX_CELLS 67108864LL
 

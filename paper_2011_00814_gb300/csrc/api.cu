@@ -10,6 +10,7 @@
 #include <cudaTypedefs.h>
 
 #include "../../include/gpe2p.h"
+#include "batch.h"
 #include "gpe2p_launch.h"
 
 using namespace gpe2p;
@@ -54,6 +55,7 @@ struct gpe2p_ctx {
   bool initialized = false;
   bool have_graph = false;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  BatchCtx* batch = nullptr;    // set for a batch of 2D instances
   std::string err;
 };
 
@@ -566,6 +568,7 @@ static cudaError_t init_impl(gpe2p_ctx* h, const double* phi, const double* u, c
 extern "C" int gpe2p_init_fields(gpe2p_handle h, const double* phi, const double* u, const double* v,
                                  const double* w, const double* p) {
   if (!h) return fail(nullptr, GPE2P_EINVAL, "handle is NULL");
+  if (h->batch) return fail(h, GPE2P_EINVAL, "a batch handle: use the per-instance calls");
   if (!phi || !u || !v || !p || (h->prm.dim == 3 && !w)) return fail(h, GPE2P_EINVAL, "a required field is NULL");
   CK(h, cudaSetDevice(h->dev), "set device");
   h->cur = 0;
@@ -612,6 +615,11 @@ static int diag_impl(gpe2p_ctx* h, gpe2p_diag* d) {
 
 extern "C" int gpe2p_step(gpe2p_handle h) {
   if (!h) return fail(nullptr, GPE2P_EINVAL, "handle is NULL");
+  if (h->batch) {
+    std::string why;
+    const int rc = batch_step(h->batch, why);
+    return rc == GPE2P_OK ? rc : fail(h, rc, why);
+  }
   if (!h->initialized) return fail(h, GPE2P_ESTATE, "gpe2p_step before gpe2p_init_fields");
   CK(h, cudaSetDevice(h->dev), "set device");
   if (!h->have_graph) {
@@ -624,16 +632,25 @@ extern "C" int gpe2p_step(gpe2p_handle h) {
   return GPE2P_OK;
 }
 
+static int any_diag(gpe2p_ctx* h, gpe2p_diag* d) {
+  if (h->batch) {
+    std::string why;
+    const int rc = batch_diag(h->batch, -1, d, why);
+    return rc == GPE2P_OK ? rc : fail(h, rc, why);
+  }
+  return diag_impl(h, d);
+}
+
 extern "C" int gpe2p_advance(gpe2p_handle h, long long nsteps, gpe2p_diag* last) {
   if (!h) return fail(nullptr, GPE2P_EINVAL, "handle is NULL");
   if (nsteps < 0) return fail(h, GPE2P_EINVAL, "nsteps < 0");
-  if (!h->initialized) return fail(h, GPE2P_ESTATE, "gpe2p_advance before gpe2p_init_fields");
+  if (!h->initialized && !h->batch) return fail(h, GPE2P_ESTATE, "gpe2p_advance before gpe2p_init_fields");
   gpe2p_diag d{};
   for (long long s = 0; s < nsteps; ++s) {
     int rc = gpe2p_step(h);
     if (rc != GPE2P_OK) return rc;
     if (h->prm.diag_every > 0 && (s + 1) % h->prm.diag_every == 0 && s + 1 < nsteps) {
-      rc = diag_impl(h, &d);
+      rc = any_diag(h, &d);
       if (rc != GPE2P_OK) return rc;
       if (d.nan_flag) {
         if (last) *last = d;
@@ -641,15 +658,16 @@ extern "C" int gpe2p_advance(gpe2p_handle h, long long nsteps, gpe2p_diag* last)
       }
     }
   }
-  int rc = diag_impl(h, &d);
+  int rc = any_diag(h, &d);
   if (rc != GPE2P_OK) return rc;
   if (last) *last = d;
-  if (d.nan_flag) return fail(h, GPE2P_EDIVERGED, "NaN/Inf in the state at step " + std::to_string(h->step));
+  if (d.nan_flag) return fail(h, GPE2P_EDIVERGED, "NaN/Inf in the state at step " + std::to_string(d.step));
   return GPE2P_OK;
 }
 
 extern "C" int gpe2p_diagnostics(gpe2p_handle h, gpe2p_diag* out) {
   if (!h || !out) return fail(h, GPE2P_EINVAL, "NULL argument");
+  if (h->batch) return any_diag(h, out);
   if (!h->initialized) return fail(h, GPE2P_ESTATE, "diagnostics before gpe2p_init_fields");
   CK(h, cudaSetDevice(h->dev), "set device");
   return diag_impl(h, out);
@@ -675,6 +693,7 @@ static cudaError_t get_any(gpe2p_ctx* h, const void* src, double* dst) {
 extern "C" int gpe2p_read_fields(gpe2p_handle h, double* phi, double* u, double* v, double* w, double* p,
                                  double* mu) {
   if (!h) return fail(nullptr, GPE2P_EINVAL, "handle is NULL");
+  if (h->batch) return fail(h, GPE2P_EINVAL, "a batch handle: use the per-instance calls");
   if (!h->initialized) return fail(h, GPE2P_ESTATE, "read_fields before gpe2p_init_fields");
   CK(h, cudaSetDevice(h->dev), "set device");
   double* dst[6] = {p, u, v, h->prm.dim == 3 ? w : nullptr, phi, mu};
@@ -723,6 +742,7 @@ static cudaError_t rates_impl(gpe2p_ctx* h) {
 
 extern "C" int gpe2p_eval_rates(gpe2p_handle h, double* Lp, double* Lu, double* Lv, double* Lw, double* Lphi) {
   if (!h) return fail(nullptr, GPE2P_EINVAL, "handle is NULL");
+  if (h->batch) return fail(h, GPE2P_EINVAL, "a batch handle: use the per-instance calls");
   if (!h->initialized) return fail(h, GPE2P_ESTATE, "eval_rates before gpe2p_init_fields");
   CK(h, cudaSetDevice(h->dev), "set device");
   cudaError_t e;
@@ -740,6 +760,7 @@ extern "C" int gpe2p_eval_rates(gpe2p_handle h, double* Lp, double* Lu, double* 
 extern "C" int gpe2p_profile_steps(gpe2p_handle h, int nsteps, double* ms, int max_launches, int* nlaunches,
                                    char* names, int names_len) {
   if (!h || !ms || !nlaunches || nsteps < 1 || max_launches < 1) return fail(h, GPE2P_EINVAL, "bad argument");
+  if (h->batch) return fail(h, GPE2P_EINVAL, "a batch handle has no per-launch profile");
   if (!h->initialized) return fail(h, GPE2P_ESTATE, "profile_steps before gpe2p_init_fields");
   CK(h, cudaSetDevice(h->dev), "set device");
   const int cap = 32;
@@ -776,6 +797,7 @@ extern "C" int gpe2p_profile_steps(gpe2p_handle h, int nsteps, double* ms, int m
 
 extern "C" int gpe2p_field_ptr(gpe2p_handle h, int which, void** dptr, long long* row_pitch) {
   if (!h || !dptr) return fail(h, GPE2P_EINVAL, "NULL argument");
+  if (h->batch) return fail(h, GPE2P_EINVAL, "a batch handle: use the per-instance calls");
   if (row_pitch) *row_pitch = h->pitch;
   if (which < 0 || which > 5 || (which == 3 && h->prm.dim == 2)) return fail(h, GPE2P_EINVAL, "bad field index");
   void* src[6] = {h->Q[h->cur][0], h->Q[h->cur][1], h->Q[h->cur][2], h->Q[h->cur][3], h->phi, h->mu};
@@ -789,6 +811,11 @@ extern "C" const char* gpe2p_last_error(gpe2p_handle h) {
 
 extern "C" void gpe2p_destroy(gpe2p_handle h) {
   if (!h) return;
+  if (h->batch) {
+    batch_destroy(h->batch);
+    delete h;
+    return;
+  }
   cudaSetDevice(h->dev);
   for (int c = 0; c < 2; ++c)
     if (h->gexec[c]) cudaGraphExecDestroy(h->gexec[c]);
@@ -797,4 +824,74 @@ extern "C" void gpe2p_destroy(gpe2p_handle h) {
   if (h->h_out) cudaFreeHost(h->h_out);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
+}
+
+// ---------------------------------------------------------------------------
+// batches of 2D problems
+// ---------------------------------------------------------------------------
+
+extern "C" int gpe2p_create_batch(const gpe2p_params* p, int n, void* stream, gpe2p_handle* out) {
+  if (!out || !p) return fail(nullptr, GPE2P_EINVAL, "NULL argument");
+  *out = nullptr;
+  if (n < 1) return fail(nullptr, GPE2P_EINVAL, "n must be >= 1");
+  for (int k = 0; k < n; ++k) {
+    std::string why;
+    int rc = validate(&p[k], why);
+    if (rc != GPE2P_OK) return fail(nullptr, rc, "instance " + std::to_string(k) + ": " + why);
+    if (p[k].check_stability) {
+      double lim[3];
+      gpe2p_stability_limits(&p[k], lim);
+      for (int i = 0; i < 3; ++i)
+        if (p[k].dt > lim[i] * (1.0 + 1e-12))
+          return fail(nullptr, GPE2P_EUNSTABLE, "instance " + std::to_string(k) + ": dt beyond a stability limit");
+    }
+  }
+  gpe2p_ctx* h = new (std::nothrow) gpe2p_ctx();
+  if (!h) return fail(nullptr, GPE2P_ENOMEM, "host allocation failed");
+  h->prm = p[0];
+  std::string why;
+  const int rc = batch_create(p, n, stream, &h->batch, why);
+  if (rc != GPE2P_OK) {
+    delete h;
+    return fail(nullptr, rc, why);
+  }
+  cudaGetDevice(&h->dev);
+  *out = h;
+  return GPE2P_OK;
+}
+
+extern "C" int gpe2p_init_instance(gpe2p_handle h, int inst, const double* phi, const double* u, const double* v,
+                                   const double*, const double* p) {
+  if (!h || !h->batch) return fail(h, GPE2P_EINVAL, "not a batch handle");
+  std::string why;
+  const int rc = batch_init(h->batch, inst, phi, u, v, p, why);
+  return rc == GPE2P_OK ? rc : fail(h, rc, why);
+}
+
+extern "C" int gpe2p_read_instance(gpe2p_handle h, int inst, double* phi, double* u, double* v, double*, double* p,
+                                   double* mu) {
+  if (!h || !h->batch) return fail(h, GPE2P_EINVAL, "not a batch handle");
+  std::string why;
+  const int rc = batch_read(h->batch, inst, phi, u, v, p, mu, why);
+  return rc == GPE2P_OK ? rc : fail(h, rc, why);
+}
+
+extern "C" int gpe2p_diagnostics_instance(gpe2p_handle h, int inst, gpe2p_diag* out) {
+  if (!h || !h->batch || !out) return fail(h, GPE2P_EINVAL, "not a batch handle or NULL output");
+  if (inst < 0) return fail(h, GPE2P_EINVAL, "instance index out of range");
+  std::string why;
+  const int rc = batch_diag(h->batch, inst, out, why);
+  return rc == GPE2P_OK ? rc : fail(h, rc, why);
+}
+
+extern "C" int gpe2p_batch_config(gpe2p_handle h, int* tile_x, int* tile_y, int* persistent, double* ms_per_step) {
+  if (!h || !h->batch) return fail(h, GPE2P_EINVAL, "not a batch handle");
+  return batch_config(h->batch, tile_x, tile_y, persistent, ms_per_step);
+}
+
+extern "C" int gpe2p_set_fault_injection(gpe2p_handle h, int what, long long value) {
+  if (!h || !h->batch) return fail(h, GPE2P_EINVAL, "fault injection applies to batch handles");
+  std::string why;
+  const int rc = batch_fault(h->batch, what, value, why);
+  return rc == GPE2P_OK ? rc : fail(h, rc, why);
 }

@@ -1,0 +1,29 @@
+// batch.h -- host interface of the batched 2D engine (batch.cu), used by the
+// C ABI in api.cu.
+#pragma once
+
+#include <string>
+
+#include "../../include/gpe2p.h"
+
+namespace gpe2p {
+
+struct BatchCtx;
+
+// default bounded-wait limit of the grid barrier, in SM clock cycles (~2 s)
+constexpr long long WAIT_LIMIT_DEFAULT = 4000000000LL;
+
+int batch_create(const gpe2p_params* p, int n, void* stream, BatchCtx** out, std::string& why);
+void batch_destroy(BatchCtx* b);
+int batch_init(BatchCtx* b, int k, const double* phi, const double* u, const double* v, const double* p,
+               std::string& why);
+int batch_read(BatchCtx* b, int k, double* phi, double* u, double* v, double* p, double* mu, std::string& why);
+int batch_step(BatchCtx* b, std::string& why);
+// k < 0: all instances (sums, max, any)
+int batch_diag(BatchCtx* b, int k, gpe2p_diag* d, std::string& why);
+int batch_config(BatchCtx* b, int* tile_x, int* tile_y, int* persistent, double* ms);
+int batch_fault(BatchCtx* b, int what, long long value, std::string& why);
+long long batch_cells(const BatchCtx* b);
+int batch_size(const BatchCtx* b);
+
+}  // namespace gpe2p

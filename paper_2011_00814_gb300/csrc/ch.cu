@@ -4,255 +4,25 @@
 // Eq. u-center-2d.  Same tiling as the flow stage: a block stages phi_s and
 // mu_s (and, for the conservative form, the cell velocity) with a one-cell
 // halo in shared memory and marches along z in 3D.
+#include "ch_ops.cuh"
 #include "gpe2p_dev.cuh"
 #include "gpe2p_launch.h"
 #include "ring3d.cuh"
 
 namespace gpe2p {
 
-// which lattice shells a model uses: D2Q9 {1,2}, D3Q15 {1,3}, D3Q19 {1,2}, D3Q27 {1,2,3}
-template <int ISO>
-struct Shells {
-  static constexpr bool s2 = ISO == 9 || ISO == 19 || ISO == 27;
-  static constexpr bool s3 = ISO == 15 || ISO == 27;
-};
-
-template <typename real, int DIM, int ISO, typename T>
-__device__ __forceinline__ real lap_iso(const T& S, const KParams<real>& P, int f) {
-  real s = real(0);
-#pragma unroll
-  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int sh = dx * dx + dy * dy + dz * dz;
-        if (sh == 0) continue;
-        if (sh == 2 && !Shells<ISO>::s2) continue;
-        if (sh == 3 && !Shells<ISO>::s3) continue;
-        s += shell_w(P, sh) * S(f, dx, dy, dz);
-      }
-  return P.lap_c * (s - P.one_m_w0 * S(f, 0, 0, 0));
-}
-
-// the DIM components of the isotropic gradient of staged field f
-template <typename real, int DIM, int ISO, typename T>
-__device__ __forceinline__ void grad_iso(const T& S, const KParams<real>& P, int f, real g[3]) {
-  real s[3] = {real(0), real(0), real(0)};
-#pragma unroll
-  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int sh = dx * dx + dy * dy + dz * dz;
-        if (sh == 0) continue;
-        if (sh == 2 && !Shells<ISO>::s2) continue;
-        if (sh == 3 && !Shells<ISO>::s3) continue;
-        const real w = shell_w(P, sh);
-        const real v = S(f, dx, dy, dz);
-        if (dx != 0) s[0] += (dx > 0 ? w : -w) * v;
-        if (dy != 0) s[1] += (dy > 0 ? w : -w) * v;
-        if (DIM == 3 && dz != 0) s[2] += (dz > 0 ? w : -w) * v;
-      }
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) g[a] = P.grad_c * s[a];
-}
-
-enum { C_PHI = 0, C_MU = 1, C_UH = 2, C_N = 5 };
-
-// face value of component C on the high face of cell (i,j,k) (the low face of
-// the next cell along C): zero on a wall, wrapped when periodic
-template <int C, typename real>
-__device__ __forceinline__ real face_next(const real* __restrict__ f, const KParams<real>& P, int i, int j, int k,
-                                          long long id) {
-  const int x = C == 0 ? i : (C == 1 ? j : k);
-  const long long st = C == 0 ? 1 : (C == 1 ? P.sy : P.sz);
-  if (x + 1 < P.n[C]) return f[id + st];
-  if (P.bc[C] == BC_PERIODIC) return f[id + st - (long long)P.n[C] * st];
-  return real(0);
-}
-
-// the values a CH stage reads at the cell itself (no halo): the stage-1
-// time-centred velocity from the two face velocities (Eq. u-center-2d) or the
-// stored one, phi^{n+1/2} and the RK4 accumulator; loaded before the stencil
-// so that their latency overlaps the wait for the staged planes
+// The single-instance 2D CH stage and mu: one tile per block.
 template <typename real>
-struct CHPoint {
-  real uh[3];
-  real pn, acc;
-};
-
-template <typename real, int DIM>
-__device__ __forceinline__ void ch_point_load(const KParams<real>& P, const CHArgs<real>& A, int i, int j, int k,
-                                              CHPoint<real>& c) {
-  const long long id = lin(P, i, j, k);
-  if (!A.conservative) {
-    if (A.compute_uh) {
-      c.uh[0] = real(0.25) * ((A.u0[0][id] + face_next<0>(A.u0[0], P, i, j, k, id)) +
-                              (A.u1[0][id] + face_next<0>(A.u1[0], P, i, j, k, id)));
-      c.uh[1] = real(0.25) * ((A.u0[1][id] + face_next<1>(A.u0[1], P, i, j, k, id)) +
-                              (A.u1[1][id] + face_next<1>(A.u1[1], P, i, j, k, id)));
-      if (DIM == 3)
-        c.uh[2] = real(0.25) * ((A.u0[2][id] + face_next<2>(A.u0[2], P, i, j, k, id)) +
-                                (A.u1[2][id] + face_next<2>(A.u1[2], P, i, j, k, id)));
-    } else {
-      for (int a = 0; a < DIM; ++a) c.uh[a] = A.uh[a][id];
-    }
-  }
-  if (A.stage != 0) c.pn = A.phin[id];
-  if (A.scheme == 4 && A.stage >= 2) c.acc = A.acc[id];
-}
-
-// one cell of a CH stage: the rate -uhat.grad(phi_s) + M lap(mu_s) (or its
-// conservative form) and the RK combination of the stage
-template <typename real, int DIM, int ISO, typename T>
-__device__ __forceinline__ void ch_cell(const T& S, const KParams<real>& P, const CHArgs<real>& A, int i, int j,
-                                        int k, const CHPoint<real>& c) {
-  const long long id = lin(P, i, j, k);
-  const real lapmu = lap_iso<real, DIM, ISO>(S, P, C_MU);
-  real adv = real(0);
-  if (!A.conservative) {
-    if (A.compute_uh && A.stage != 0)
-      for (int a = 0; a < DIM; ++a) A.uh[a][id] = c.uh[a];
-    real g[3];
-    grad_iso<real, DIM, ISO>(S, P, C_PHI, g);
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) adv += c.uh[a] * g[a];
-  } else {
-    // -div_iso(uhat phi): the isotropic first derivative of the product
-    real s[3] = {real(0), real(0), real(0)};
-#pragma unroll
-    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
-#pragma unroll
-      for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int sh = dx * dx + dy * dy + dz * dz;
-          if (sh == 0) continue;
-          if (sh == 2 && !Shells<ISO>::s2) continue;
-          if (sh == 3 && !Shells<ISO>::s3) continue;
-          const real w = shell_w(P, sh);
-          const real ph = S(C_PHI, dx, dy, dz);
-          if (dx != 0) s[0] += (dx > 0 ? w : -w) * S(C_UH + 0, dx, dy, dz) * ph;
-          if (dy != 0) s[1] += (dy > 0 ? w : -w) * S(C_UH + 1, dx, dy, dz) * ph;
-          if (DIM == 3 && dz != 0) s[2] += (dz > 0 ? w : -w) * S(C_UH + 2, dx, dy, dz) * ph;
-        }
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) adv += P.grad_c * s[a];
-  }
-  const real L = -adv + P.M * lapmu;
-  real o;
-  if (A.stage == 0) {
-    o = L;
-  } else if (A.scheme == 2) {
-    if (A.stage == 1) o = c.pn + P.dt * L;
-    else o = real(0.5) * c.pn + real(0.5) * (S(C_PHI, 0, 0, 0) + P.dt * L);
-  } else {
-    const real d = P.dt * L;
-    const real pn = c.pn;
-    if (A.stage == 1) { A.acc[id] = d; o = pn + real(0.5) * d; }
-    else if (A.stage == 2) { A.acc[id] = c.acc + real(2) * d; o = pn + real(0.5) * d; }
-    else if (A.stage == 3) { A.acc[id] = c.acc + real(2) * d; o = pn + d; }
-    else { o = pn + (c.acc + d) / real(6); }
-  }
-  A.out[id] = o;
-}
-
-template <typename real, int DIM, int ISO>
-__global__ void __launch_bounds__(NTHR) ch_stage_kernel(const KParams<real> P, const CHArgs<real> A,
-                                                        const int kchunk) {
-  constexpr int NPL = DIM == 3 ? 3 : 1;
+__global__ void __launch_bounds__(NTHR) ch2d_kernel(const KParams<real> P, const CHArgs<real> A) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  real* sm = reinterpret_cast<real*>(smraw);
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int kbeg = DIM == 3 ? blockIdx.z * kchunk : 0;
-  const int kend = DIM == 3 ? min(kbeg + kchunk, P.n[2]) : 1;
-  const int nx = P.n[0], ny = P.n[1];
-  const bool cons = A.conservative != 0;
-
-  auto load_plane = [&](int kk, int slot) {
-    for (int idx = tid; idx < PL; idx += NTHR) {
-      const int ly = idx / SX, lx = idx - ly * SX;
-      const int gi = clampi(i0 - 1 + lx, -1, nx), gj = clampi(j0 - 1 + ly, -1, ny);
-      real* b = sm + slot * PL + idx;
-      b[(C_PHI * NPL) * PL] = ld_cen(A.phis, P, gi, gj, kk);
-      b[(C_MU * NPL) * PL] = ld_cen(A.mus, P, gi, gj, kk);
-      if (cons) {
-        b[((C_UH + 0) * NPL) * PL] = ld_cvec<0>(A.uh[0], P, gi, gj, kk);
-        b[((C_UH + 1) * NPL) * PL] = ld_cvec<1>(A.uh[1], P, gi, gj, kk);
-        if (DIM == 3) b[((C_UH + 2) * NPL) * PL] = ld_cvec<2>(A.uh[2], P, gi, gj, kk);
-      }
-    }
-  };
-
-  if (DIM == 3) {
-    load_plane(kbeg - 1, (kbeg + 2) % 3);
-    load_plane(kbeg, kbeg % 3);
-  } else {
-    load_plane(0, 0);
-  }
-  const int i = i0 + tx, j = j0 + ty;
-  const bool active = i < nx && j < ny;
-  for (int k = kbeg; k < kend; ++k) {
-    if (DIM == 3) load_plane(k + 1, (k + 1) % 3);
-    __syncthreads();
-    if (active) {
-      Tile<real, NPL> S;
-      S.sm = sm;
-      S.c = (ty + 1) * SX + (tx + 1);
-      S.s0 = DIM == 3 ? k % 3 : 0;
-      S.sm1 = DIM == 3 ? (k + 2) % 3 : 0;
-      S.sp1 = DIM == 3 ? (k + 1) % 3 : 0;
-      CHPoint<real> c;
-      ch_point_load<real, DIM>(P, A, i, j, k, c);
-      ch_cell<real, DIM, ISO>(S, P, A, i, j, k, c);
-    }
-    __syncthreads();
-  }
+  ch2d_tile<real, TX, TY>(P, A, blockIdx.x * TX, blockIdx.y * TY, reinterpret_cast<real*>(smraw));
 }
 
-template <typename real, int DIM, int ISO>
-__global__ void __launch_bounds__(NTHR) mu_kernel(const KParams<real> P, const real* __restrict__ phi,
-                                                  real* __restrict__ mu, const int kchunk) {
-  constexpr int NPL = DIM == 3 ? 3 : 1;
-  __shared__ real sm[NPL * PL];
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int kbeg = DIM == 3 ? blockIdx.z * kchunk : 0;
-  const int kend = DIM == 3 ? min(kbeg + kchunk, P.n[2]) : 1;
-  const int nx = P.n[0], ny = P.n[1];
-  auto load_plane = [&](int kk, int slot) {
-    for (int idx = tid; idx < PL; idx += NTHR) {
-      const int ly = idx / SX, lx = idx - ly * SX;
-      const int gi = clampi(i0 - 1 + lx, -1, nx), gj = clampi(j0 - 1 + ly, -1, ny);
-      sm[slot * PL + idx] = ld_cen(phi, P, gi, gj, kk);
-    }
-  };
-  if (DIM == 3) {
-    load_plane(kbeg - 1, (kbeg + 2) % 3);
-    load_plane(kbeg, kbeg % 3);
-  } else {
-    load_plane(0, 0);
-  }
-  const int i = i0 + tx, j = j0 + ty;
-  const bool active = i < nx && j < ny;
-  for (int k = kbeg; k < kend; ++k) {
-    if (DIM == 3) load_plane(k + 1, (k + 1) % 3);
-    __syncthreads();
-    if (active) {
-      Tile<real, NPL> S;
-      S.sm = sm;
-      S.c = (ty + 1) * SX + (tx + 1);
-      S.s0 = DIM == 3 ? k % 3 : 0;
-      S.sm1 = DIM == 3 ? (k + 2) % 3 : 0;
-      S.sp1 = DIM == 3 ? (k + 1) % 3 : 0;
-      const real f = S(0, 0, 0, 0);
-      mu[lin(P, i, j, k)] = P.a4 * f * (f * f - real(1)) - P.kappa * lap_iso<real, DIM, ISO>(S, P, 0);
-    }
-    __syncthreads();
-  }
+template <typename real>
+__global__ void __launch_bounds__(NTHR) mu2d_kernel(const KParams<real> P, const real* __restrict__ phi,
+                                                    real* __restrict__ mu) {
+  __shared__ real sm[PL];
+  mu2d_tile<real, TX, TY>(P, phi, mu, blockIdx.x * TX, blockIdx.y * TY, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -410,9 +180,9 @@ __global__ void center_velocity_kernel(const KParams<real> P, const real* u00, c
   }
 }
 
-template <typename real, int DIM>
-static size_t ch_smem() {
-  return sizeof(real) * (size_t)C_N * (DIM == 3 ? 3 : 1) * PL;
+template <typename real>
+static size_t ch2d_smem() {
+  return sizeof(real) * (size_t)C_N * PL;
 }
 
 template <typename real, int DIM, int ISO>
@@ -437,11 +207,10 @@ static cudaError_t ch_go(const KParams<real>& P, const CHArgs<real>& A, int kchu
       ch3d_kernel<real, ISO, 0, RING><<<grd, blk, sm, s>>>(*maps, P, A, kchunk, err);
     }
   } else {
-    const size_t sm = ch_smem<real, DIM>();
-    e = cudaFuncSetAttribute(ch_stage_kernel<real, DIM, ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sm);
+    const size_t sm = ch2d_smem<real>();
+    e = cudaFuncSetAttribute(ch2d_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    ch_stage_kernel<real, DIM, ISO><<<grd, blk, sm, s>>>(P, A, kchunk);
+    ch2d_kernel<real><<<grd, blk, sm, s>>>(P, A);
   }
   return cudaGetLastError();
 }
@@ -473,7 +242,7 @@ static cudaError_t mu_go(const KParams<real>& P, const real* phi, real* mu, int 
     if (e != cudaSuccess) return e;
     mu3d_kernel<real, ISO, RING><<<grd, blk, sm, s>>>(*maps, P, phi, mu, kchunk, err);
   } else {
-    mu_kernel<real, DIM, ISO><<<grd, blk, 0, s>>>(P, phi, mu, kchunk);
+    mu2d_kernel<real><<<grd, blk, 0, s>>>(P, phi, mu);
   }
   return cudaGetLastError();
 }

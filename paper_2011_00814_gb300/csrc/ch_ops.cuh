@@ -1,0 +1,222 @@
+// ch_ops.cuh -- the Cahn-Hilliard step of one cell (Sec. 3): chemical
+// potential (Eq. chem-pot), one RK stage of Eq. che with the isotropic
+// stencils of Eqs. 1st-der-iso and laplacian-iso, the time-centred cell
+// velocity of Eq. u-center-2d; and the 2D CH stage and mu on one tile, shared
+// by the single-instance and the batched 2D kernels.
+#pragma once
+
+#include "flow_ops.cuh"
+#include "gpe2p_dev.cuh"
+#include "gpe2p_launch.h"
+
+namespace gpe2p {
+
+// which lattice shells a model uses: D2Q9 {1,2}, D3Q15 {1,3}, D3Q19 {1,2}, D3Q27 {1,2,3}
+template <int ISO>
+struct Shells {
+  static constexpr bool s2 = ISO == 9 || ISO == 19 || ISO == 27;
+  static constexpr bool s3 = ISO == 15 || ISO == 27;
+};
+
+template <typename real, int DIM, int ISO, typename T>
+__device__ __forceinline__ real lap_iso(const T& S, const KParams<real>& P, int f) {
+  real s = real(0);
+#pragma unroll
+  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int sh = dx * dx + dy * dy + dz * dz;
+        if (sh == 0) continue;
+        if (sh == 2 && !Shells<ISO>::s2) continue;
+        if (sh == 3 && !Shells<ISO>::s3) continue;
+        s += shell_w(P, sh) * S(f, dx, dy, dz);
+      }
+  return P.lap_c * (s - P.one_m_w0 * S(f, 0, 0, 0));
+}
+
+// the DIM components of the isotropic gradient of staged field f
+template <typename real, int DIM, int ISO, typename T>
+__device__ __forceinline__ void grad_iso(const T& S, const KParams<real>& P, int f, real g[3]) {
+  real s[3] = {real(0), real(0), real(0)};
+#pragma unroll
+  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int sh = dx * dx + dy * dy + dz * dz;
+        if (sh == 0) continue;
+        if (sh == 2 && !Shells<ISO>::s2) continue;
+        if (sh == 3 && !Shells<ISO>::s3) continue;
+        const real w = shell_w(P, sh);
+        const real v = S(f, dx, dy, dz);
+        if (dx != 0) s[0] += (dx > 0 ? w : -w) * v;
+        if (dy != 0) s[1] += (dy > 0 ? w : -w) * v;
+        if (DIM == 3 && dz != 0) s[2] += (dz > 0 ? w : -w) * v;
+      }
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) g[a] = P.grad_c * s[a];
+}
+
+enum { C_PHI = 0, C_MU = 1, C_UH = 2, C_N = 5 };
+
+// face value of component C on the high face of cell (i,j,k) (the low face of
+// the next cell along C): zero on a wall, wrapped when periodic
+template <int C, typename real>
+__device__ __forceinline__ real face_next(const real* __restrict__ f, const KParams<real>& P, int i, int j, int k,
+                                          long long id) {
+  const int x = C == 0 ? i : (C == 1 ? j : k);
+  const long long st = C == 0 ? 1 : (C == 1 ? P.sy : P.sz);
+  if (x + 1 < P.n[C]) return f[id + st];
+  if (P.bc[C] == BC_PERIODIC) return f[id + st - (long long)P.n[C] * st];
+  return real(0);
+}
+
+// the values a CH stage reads at the cell itself (no halo): the stage-1
+// time-centred velocity from the two face velocities (Eq. u-center-2d) or the
+// stored one, phi^{n+1/2} and the RK4 accumulator; loaded before the stencil
+// so that their latency overlaps the wait for the staged planes
+template <typename real>
+struct CHPoint {
+  real uh[3];
+  real pn, acc;
+};
+
+template <typename real, int DIM>
+__device__ __forceinline__ void ch_point_load(const KParams<real>& P, const CHArgs<real>& A, int i, int j, int k,
+                                              CHPoint<real>& c) {
+  const long long id = lin(P, i, j, k);
+  if (!A.conservative) {
+    if (A.compute_uh) {
+      c.uh[0] = real(0.25) * ((A.u0[0][id] + face_next<0>(A.u0[0], P, i, j, k, id)) +
+                              (A.u1[0][id] + face_next<0>(A.u1[0], P, i, j, k, id)));
+      c.uh[1] = real(0.25) * ((A.u0[1][id] + face_next<1>(A.u0[1], P, i, j, k, id)) +
+                              (A.u1[1][id] + face_next<1>(A.u1[1], P, i, j, k, id)));
+      if (DIM == 3)
+        c.uh[2] = real(0.25) * ((A.u0[2][id] + face_next<2>(A.u0[2], P, i, j, k, id)) +
+                                (A.u1[2][id] + face_next<2>(A.u1[2], P, i, j, k, id)));
+    } else {
+      for (int a = 0; a < DIM; ++a) c.uh[a] = A.uh[a][id];
+    }
+  }
+  if (A.stage != 0) c.pn = A.phin[id];
+  if (A.scheme == 4 && A.stage >= 2) c.acc = A.acc[id];
+}
+
+// one cell of a CH stage: the rate -uhat.grad(phi_s) + M lap(mu_s) (or its
+// conservative form) and the RK combination of the stage
+template <typename real, int DIM, int ISO, typename T>
+__device__ __forceinline__ void ch_cell(const T& S, const KParams<real>& P, const CHArgs<real>& A, int i, int j,
+                                        int k, const CHPoint<real>& c) {
+  const long long id = lin(P, i, j, k);
+  const real lapmu = lap_iso<real, DIM, ISO>(S, P, C_MU);
+  real adv = real(0);
+  if (!A.conservative) {
+    if (A.compute_uh && A.stage != 0)
+      for (int a = 0; a < DIM; ++a) A.uh[a][id] = c.uh[a];
+    real g[3];
+    grad_iso<real, DIM, ISO>(S, P, C_PHI, g);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) adv += c.uh[a] * g[a];
+  } else {
+    // -div_iso(uhat phi): the isotropic first derivative of the product
+    real s[3] = {real(0), real(0), real(0)};
+#pragma unroll
+    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int sh = dx * dx + dy * dy + dz * dz;
+          if (sh == 0) continue;
+          if (sh == 2 && !Shells<ISO>::s2) continue;
+          if (sh == 3 && !Shells<ISO>::s3) continue;
+          const real w = shell_w(P, sh);
+          const real ph = S(C_PHI, dx, dy, dz);
+          if (dx != 0) s[0] += (dx > 0 ? w : -w) * S(C_UH + 0, dx, dy, dz) * ph;
+          if (dy != 0) s[1] += (dy > 0 ? w : -w) * S(C_UH + 1, dx, dy, dz) * ph;
+          if (DIM == 3 && dz != 0) s[2] += (dz > 0 ? w : -w) * S(C_UH + 2, dx, dy, dz) * ph;
+        }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) adv += P.grad_c * s[a];
+  }
+  const real L = -adv + P.M * lapmu;
+  real o;
+  if (A.stage == 0) {
+    o = L;
+  } else if (A.scheme == 2) {
+    if (A.stage == 1) o = c.pn + P.dt * L;
+    else o = real(0.5) * c.pn + real(0.5) * (S(C_PHI, 0, 0, 0) + P.dt * L);
+  } else {
+    const real d = P.dt * L;
+    const real pn = c.pn;
+    if (A.stage == 1) { A.acc[id] = d; o = pn + real(0.5) * d; }
+    else if (A.stage == 2) { A.acc[id] = c.acc + real(2) * d; o = pn + real(0.5) * d; }
+    else if (A.stage == 3) { A.acc[id] = c.acc + real(2) * d; o = pn + d; }
+    else { o = pn + (c.acc + d) / real(6); }
+  }
+  A.out[id] = o;
+}
+
+// One 2D CH stage on the tile of TXv x TYv cells at (i0, j0), by a block of
+// TXv*TYv threads.  sm holds C_N * (TXv+2)*(TYv+2) reals.
+template <typename real, int TXv, int TYv>
+__device__ __forceinline__ void ch2d_tile(const KParams<real>& P, const CHArgs<real>& A, int i0, int j0,
+                                          real* sm) {
+  constexpr int SXv = TXv + 2, SYv = TYv + 2, PLv = SXv * SYv, NT = TXv * TYv;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int tx = tid % TXv, ty = tid / TXv;
+  const int nx = P.n[0], ny = P.n[1];
+  const bool cons = A.conservative != 0;
+  for (int idx = tid; idx < PLv; idx += NT) {
+    const int ly = idx / SXv, lx = idx - ly * SXv;
+    const int gi = clampi(i0 - 1 + lx, -1, nx), gj = clampi(j0 - 1 + ly, -1, ny);
+    real* b = sm + idx;
+    b[C_PHI * PLv] = ld_cen(A.phis, P, gi, gj, 0);
+    b[C_MU * PLv] = ld_cen(A.mus, P, gi, gj, 0);
+    if (cons) {
+      b[(C_UH + 0) * PLv] = ld_cvec<0>(A.uh[0], P, gi, gj, 0);
+      b[(C_UH + 1) * PLv] = ld_cvec<1>(A.uh[1], P, gi, gj, 0);
+    }
+  }
+  __syncthreads();
+  const int i = i0 + tx, j = j0 + ty;
+  if (i < nx && j < ny) {
+    Tile2<real, SXv, PLv> S;
+    S.sm = sm;
+    S.c = (ty + 1) * SXv + (tx + 1);
+    CHPoint<real> c;
+    ch_point_load<real, 2>(P, A, i, j, 0, c);
+    ch_cell<real, 2, 9>(S, P, A, i, j, 0, c);
+  }
+  __syncthreads();
+}
+
+// mu of a 2D tile (Eq. chem-pot with the D2Q9 Laplacian); sm holds (TXv+2)*(TYv+2) reals
+template <typename real, int TXv, int TYv>
+__device__ __forceinline__ void mu2d_tile(const KParams<real>& P, const real* __restrict__ phi,
+                                          real* __restrict__ mu, int i0, int j0, real* sm) {
+  constexpr int SXv = TXv + 2, SYv = TYv + 2, PLv = SXv * SYv, NT = TXv * TYv;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int tx = tid % TXv, ty = tid / TXv;
+  const int nx = P.n[0], ny = P.n[1];
+  for (int idx = tid; idx < PLv; idx += NT) {
+    const int ly = idx / SXv, lx = idx - ly * SXv;
+    const int gi = clampi(i0 - 1 + lx, -1, nx), gj = clampi(j0 - 1 + ly, -1, ny);
+    sm[idx] = ld_cen(phi, P, gi, gj, 0);
+  }
+  __syncthreads();
+  const int i = i0 + tx, j = j0 + ty;
+  if (i < nx && j < ny) {
+    Tile2<real, SXv, PLv> S;
+    S.sm = sm;
+    S.c = (ty + 1) * SXv + (tx + 1);
+    const real f = S(0, 0, 0, 0);
+    mu[lin(P, i, j, 0)] = P.a4 * f * (f * f - real(1)) - P.kappa * lap_iso<real, 2, 9>(S, P, 0);
+  }
+  __syncthreads();
+}
+
+}  // namespace gpe2p

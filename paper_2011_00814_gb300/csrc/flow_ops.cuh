@@ -1,0 +1,215 @@
+// flow_ops.cuh -- the semi-discrete flow operators of one cell (Sec. 3) and
+// the 2D flow stage on one tile, shared by the single-instance and the
+// batched 2D kernels so that both compute bit-identical results.
+//
+//   out = a q^n + b (q + dt L(q)),  q = (p, u, v[, w]),
+// with L of Eq. p-u-v-semidiscrete-2d built from Eqs. div-v-discretization,
+// diff-p-discretization, conv-u-discretization, u-stress-discretization
+// (a)-(d), st-u-discretization, gradp-u-discretization and gradp-u-p-ave-3d,
+// phi and mu frozen (Sec. 3, after Eq. tvd-rk3).
+#pragma once
+
+#include "gpe2p_dev.cuh"
+#include "gpe2p_launch.h"
+
+namespace gpe2p {
+
+enum { F_P = 0, F_U = 1, F_V = 2, F_W = 3, F_PHI = 4, F_RHO = 5, F_ETA = 6, F_NU = 7, F_MU = 8, F_N = 9 };
+// precomputed per-cell quantities offered by the 3D ring accessor: the
+// divergence of the cell and the viscosity of the cell's low edge in each
+// coordinate plane (mean of eta over the four cells around the edge)
+enum { F_DIV = 9, F_EXY = 10, F_EXZ = 11, F_EYZ = 12 };
+
+// accessors that stage only the raw fields (the 2D plane kernel)
+template <typename T>
+struct HasPre {
+  static constexpr bool value = false;
+};
+
+template <typename real, int DIM, typename T>
+struct FlowOps {
+  static constexpr bool PRE = HasPre<T>::value;
+
+  // velocity divergence of the cell at offset (ox,oy,oz), Eq. div-v-discretization
+  __device__ __forceinline__ static real div(const T& S, const KParams<real>& P, int ox, int oy, int oz) {
+    if constexpr (PRE) {
+      return S(F_DIV, ox, oy, oz);
+    } else {
+      real d = (S(F_U, ox + 1, oy, oz) - S(F_U, ox, oy, oz)) + (S(F_V, ox, oy + 1, oz) - S(F_V, ox, oy, oz));
+      if (DIM == 3) d += S(F_W, ox, oy, oz + 1) - S(F_W, ox, oy, oz);
+      return d * P.inv_dx;
+    }
+  }
+
+  // eta averaged over the four cells around the edge shared by the faces of
+  // components C and t (Eq. u-stress-discretization, eta bar at i, j+-1/2):
+  // the edge on the +t side (etp) or on the -t side (etm) of the C face
+  template <int C>
+  __device__ __forceinline__ static void edge_eta(const T& S, int t, real& etp, real& etm) {
+    const int cx = C == 0, cy = C == 1, cz = C == 2;
+    const int tx = t == 0, ty = t == 1, tz = t == 2;
+    if constexpr (PRE) {
+      const int a = C < t ? C : t, b = C < t ? t : C;
+      const int FE = (a == 0 && b == 1) ? F_EXY : ((a == 0 && b == 2) ? F_EXZ : F_EYZ);
+      etp = S(FE, tx, ty, tz);
+      etm = S(FE, 0, 0, 0);
+    } else {
+      etp = (S(F_ETA, 0, 0, 0) + S(F_ETA, tx, ty, tz) + S(F_ETA, -cx, -cy, -cz) +
+             S(F_ETA, tx - cx, ty - cy, tz - cz)) *
+            real(0.25);
+      etm = (S(F_ETA, 0, 0, 0) + S(F_ETA, -tx, -ty, -tz) + S(F_ETA, -cx, -cy, -cz) +
+             S(F_ETA, -tx - cx, -ty - cy, -tz - cz)) *
+            real(0.25);
+    }
+  }
+
+  // averaged pressure of the cell at offset o for the gradient along C
+  // (Eq. gradp-u-discretization in 2D, Eq. gradp-u-p-ave-3d in 3D)
+  template <int C>
+  __device__ __forceinline__ static real pbar(const T& S, const KParams<real>& P, int ox, int oy, int oz) {
+    if constexpr (T::PAVG == 0) {
+      return S(F_P, ox, oy, oz);
+    } else if constexpr (T::PAVG < 0) {
+      if (!P.pavg) return S(F_P, ox, oy, oz);
+    }
+    if (DIM == 2) {
+      constexpr int tx = C == 1, ty = C == 0;
+      return (real(4) * S(F_P, ox, oy, oz) + S(F_P, ox + tx, oy + ty, oz) + S(F_P, ox - tx, oy - ty, oz)) *
+             real(1.0 / 6.0);
+    } else {
+      constexpr int T1 = (C + 1) % 3, T2 = (C + 2) % 3;
+      constexpr int ax = T1 == 0, ay = T1 == 1, az = T1 == 2;  // unit vector t1
+      constexpr int bx = T2 == 0, by = T2 == 1, bz = T2 == 2;  // unit vector t2
+      const real s4 = S(F_P, ox + ax, oy + ay, oz + az) + S(F_P, ox - ax, oy - ay, oz - az) +
+                      S(F_P, ox + bx, oy + by, oz + bz) + S(F_P, ox - bx, oy - by, oz - bz);
+      const real s1 = S(F_P, ox + ax + bx, oy + ay + by, oz + az + bz) +
+                      S(F_P, ox - ax - bx, oy - ay - by, oz - az - bz) +
+                      S(F_P, ox - ax + bx, oy - ay + by, oz - az + bz) +
+                      S(F_P, ox + ax - bx, oy + ay - by, oz + az - bz);
+      return (real(16) * S(F_P, ox, oy, oz) + real(4) * s4 + s1) * real(1.0 / 36.0);
+    }
+  }
+
+  // pressure rate at the cell centre: -rho c_s^2 div u + div(nu grad p)
+  __device__ __forceinline__ static real rate_p(const T& S, const KParams<real>& P, real D0) {
+    real diff = real(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const int ex = a == 0, ey = a == 1, ez = a == 2;
+      const real nup = real(0.5) * (S(F_NU, 0, 0, 0) + S(F_NU, ex, ey, ez));
+      const real num = real(0.5) * (S(F_NU, 0, 0, 0) + S(F_NU, -ex, -ey, -ez));
+      diff += (nup * (S(F_P, ex, ey, ez) - S(F_P, 0, 0, 0)) - num * (S(F_P, 0, 0, 0) - S(F_P, -ex, -ey, -ez))) *
+              P.inv_dx2;
+    }
+    return -S(F_RHO, 0, 0, 0) * P.cs2 * D0 + diff;
+  }
+
+  // rate of velocity component C on the cell's low face along C
+  template <int C>
+  __device__ __forceinline__ static real rate_vel(const T& S, const KParams<real>& P, real D0) {
+    constexpr int cx = C == 0, cy = C == 1, cz = C == 2;
+    const int FC = F_U + C;
+    const real rb = real(0.5) * (S(F_RHO, -cx, -cy, -cz) + S(F_RHO, 0, 0, 0));
+    const real gradp = (pbar<C>(S, P, 0, 0, 0) - pbar<C>(S, P, -cx, -cy, -cz)) * P.inv_dx;
+    const real uc0 = S(FC, 0, 0, 0);
+    const real t_cc = (S(F_ETA, 0, 0, 0) * (S(FC, cx, cy, cz) - uc0) -
+                       S(F_ETA, -cx, -cy, -cz) * (uc0 - S(FC, -cx, -cy, -cz))) *
+                      P.inv_dx2;
+    real t_tr = real(0), conv_tr = real(0);
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) {
+      if (t == C) continue;
+      const int tx = t == 0, ty = t == 1, tz = t == 2;
+      const int FT = F_U + t;
+      real etp, etm;
+      edge_eta<C>(S, t, etp, etm);
+      const real t_tt = (etp * (S(FC, tx, ty, tz) - uc0) - etm * (uc0 - S(FC, -tx, -ty, -tz))) * P.inv_dx2;
+      const real t_tc = (etp * (S(FT, tx, ty, tz) - S(FT, tx - cx, ty - cy, tz - cz)) -
+                         etm * (S(FT, 0, 0, 0) - S(FT, -cx, -cy, -cz))) *
+                        P.inv_dx2;
+      t_tr += t_tt + t_tc;
+      const real ubar = (S(FT, 0, 0, 0) + S(FT, -cx, -cy, -cz) + S(FT, tx, ty, tz) +
+                         S(FT, tx - cx, ty - cy, tz - cz)) *
+                        real(0.25);
+      conv_tr += ubar * (S(FC, tx, ty, tz) - S(FC, -tx, -ty, -tz)) * P.inv_2dx;
+    }
+    real t_b = real(0);
+    if (P.bulk) t_b = (S(F_ETA, 0, 0, 0) * D0 - S(F_ETA, -cx, -cy, -cz) * div(S, P, -cx, -cy, -cz)) * P.inv_dx;
+    const real st = -P.sigma * (S(F_PHI, 0, 0, 0) + S(F_PHI, -cx, -cy, -cz)) *
+                    (S(F_MU, 0, 0, 0) - S(F_MU, -cx, -cy, -cz)) * P.inv_2dx;
+    const real grav = (rb - P.rho_ref) * P.g[C];
+    const real force = -gradp + real(2) * t_cc + t_tr + t_b + st + grav;
+    const real conv = uc0 * (S(FC, cx, cy, cz) - S(FC, -cx, -cy, -cz)) * P.inv_2dx + conv_tr;
+    return fdiv(force, rb) - conv;
+  }
+};
+
+// 2D tile accessor: NF staged fields of (TXv+2) x (TYv+2) elements
+template <typename real, int SXv, int PLv>
+struct Tile2 {
+  static constexpr int PAVG = -1;  // pressure averaging decided at run time
+  const real* sm;
+  int c;  // the thread's cell within a staged field
+  __device__ __forceinline__ real operator()(int f, int dx, int dy, int) const {
+    return sm[f * PLv + c + dy * SXv + dx];
+  }
+};
+
+// MODE 0: out = L(q);  MODE 1: out = q + dt L(q);  MODE 2: out = a q0 + b (q + dt L(q)).
+// One 2D flow stage on the tile of TXv x TYv cells at (i0, j0), by a block of
+// TXv*TYv threads (thread t owns cell (t % TXv, t / TXv)).  The block stages
+// p, u, v, phi, rho, eta, nu = eta/rho and mu with a one-cell halo (ghosts
+// mapped by the boundary rules) in sm, F_N * (TXv+2)*(TYv+2) reals.
+template <typename real, int MODE, int TXv, int TYv>
+__device__ __forceinline__ void flow2d_tile(const KParams<real>& P, const FlowArgs<real>& A, int i0, int j0,
+                                            real* sm) {
+  constexpr int SXv = TXv + 2, SYv = TYv + 2, PLv = SXv * SYv, NT = TXv * TYv;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int tx = tid % TXv, ty = tid / TXv;
+  const int nx = P.n[0], ny = P.n[1];
+  for (int idx = tid; idx < PLv; idx += NT) {
+    const int ly = idx / SXv, lx = idx - ly * SXv;
+    const int gi = clampi(i0 - 1 + lx, -1, nx), gj = clampi(j0 - 1 + ly, -1, ny);
+    const real phi = ld_cen(A.phi, P, gi, gj, 0);
+    const real rho = rho_of(P, phi), eta = eta_of(P, phi);
+    real* b = sm + idx;
+    b[F_P * PLv] = ld_cen(A.q[0], P, gi, gj, 0);
+    b[F_U * PLv] = ld_face<0>(A.q[1], P, gi, gj, 0);
+    b[F_V * PLv] = ld_face<1>(A.q[2], P, gi, gj, 0);
+    b[F_PHI * PLv] = phi;
+    b[F_RHO * PLv] = rho;
+    b[F_ETA * PLv] = eta;
+    b[F_NU * PLv] = fdiv(eta, rho);
+    b[F_MU * PLv] = ld_cen(A.mu, P, gi, gj, 0);
+  }
+  __syncthreads();
+  const int i = i0 + tx, j = j0 + ty;
+  if (i < nx && j < ny) {
+    Tile2<real, SXv, PLv> S;
+    S.sm = sm;
+    S.c = (ty + 1) * SXv + (tx + 1);
+    using Ops = FlowOps<real, 2, Tile2<real, SXv, PLv>>;
+    const real D0 = Ops::div(S, P, 0, 0, 0);
+    real L[3];
+    L[0] = Ops::rate_p(S, P, D0);
+    L[1] = (P.bc[0] != BC_PERIODIC && i == 0) ? real(0) : Ops::template rate_vel<0>(S, P, D0);
+    L[2] = (P.bc[1] != BC_PERIODIC && j == 0) ? real(0) : Ops::template rate_vel<1>(S, P, D0);
+    const long long id = lin(P, i, j, 0);
+    const int F[3] = {F_P, F_U, F_V};
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      real o;
+      if (MODE == 0) {
+        o = L[f];
+      } else {
+        const real q = S(F[f], 0, 0, 0);
+        if (MODE == 1) o = q + P.dt * L[f];
+        else o = A.a * A.q0[f][id] + A.b * (q + P.dt * L[f]);
+      }
+      A.out[f][id] = o;
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace gpe2p

@@ -80,6 +80,16 @@ def lib():
         L.gpe2p_diagnostics_noalloc.argtypes = [ctypes.POINTER(Params), vp, vp, vp, vp, vp, ctypes.c_longlong,
                                                 vp, vp]
         L.gpe2p_diagnostics_noalloc.restype = ctypes.c_int
+        L.gpe2p_create_batch.argtypes = [ctypes.POINTER(Params), ctypes.c_int, vp, ctypes.POINTER(vp)]
+        L.gpe2p_init_instance.argtypes = [vp, ctypes.c_int] + [dp] * 5
+        L.gpe2p_read_instance.argtypes = [vp, ctypes.c_int] + [dp] * 6
+        L.gpe2p_diagnostics_instance.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Diag)]
+        L.gpe2p_batch_config.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), dp]
+        L.gpe2p_set_fault_injection.argtypes = [vp, ctypes.c_int, ctypes.c_longlong]
+        for nm in ("gpe2p_create_batch", "gpe2p_init_instance", "gpe2p_read_instance",
+                   "gpe2p_diagnostics_instance", "gpe2p_batch_config", "gpe2p_set_fault_injection"):
+            getattr(L, nm).restype = ctypes.c_int
         L.gpe2p_last_error.argtypes = [vp]
         L.gpe2p_last_error.restype = ctypes.c_char_p
         L.gpe2p_destroy.argtypes = [vp]
@@ -210,6 +220,86 @@ class Solver:
         pitch = ctypes.c_longlong()
         self._check(lib().gpe2p_field_ptr(self.h, FIELD[name], ctypes.byref(p), ctypes.byref(pitch)))
         return p.value, pitch.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gpe2p_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+FAULT_SKIP_BARRIER, FAULT_WAIT_LIMIT, FAULT_FORCE_PERSISTENT, FAULT_CLEAR = 1, 2, 3, 4
+
+
+class Batch:
+    """Many independent 2D problems advanced together (``gpe2p_create_batch``)."""
+
+    def __init__(self, prms, stream: int | None = None):
+        self.prms = [dict(p) for p in prms]
+        n = len(self.prms)
+        arr = (Params * n)(*[params(p) for p in self.prms])
+        self._arr = arr
+        h = ctypes.c_void_p()
+        rc = lib().gpe2p_create_batch(arr, n, ctypes.c_void_p(stream) if stream else None, ctypes.byref(h))
+        if rc != OK:
+            raise GPE2PError(rc, lib().gpe2p_last_error(None).decode())
+        self.h = h
+        self.shapes = [(int(p["ny"]), int(p["nx"])) for p in self.prms]
+
+    def _check(self, rc):
+        if rc != OK:
+            raise GPE2PError(rc, lib().gpe2p_last_error(self.h).decode())
+
+    def init_instance(self, k: int, f: dict):
+        a = {key: np.ascontiguousarray(f[key], dtype=np.float64) for key in ("phi", "u", "v", "p")}
+        for key, v in a.items():
+            if v.shape != self.shapes[k]:
+                raise ValueError(f"instance {k}: field {key} shape {v.shape} != {self.shapes[k]}")
+        self._check(lib().gpe2p_init_instance(self.h, int(k), _dptr(a["phi"]), _dptr(a["u"]), _dptr(a["v"]),
+                                              None, _dptr(a["p"])))
+
+    def read_instance(self, k: int) -> dict:
+        out = {key: np.empty(self.shapes[k]) for key in ("phi", "u", "v", "p", "mu")}
+        self._check(lib().gpe2p_read_instance(self.h, int(k), _dptr(out["phi"]), _dptr(out["u"]),
+                                              _dptr(out["v"]), None, _dptr(out["p"]), _dptr(out["mu"])))
+        return out
+
+    def step(self):
+        self._check(lib().gpe2p_step(self.h))
+
+    def advance(self, nsteps: int) -> dict:
+        d = Diag()
+        self._check(lib().gpe2p_advance(self.h, int(nsteps), ctypes.byref(d)))
+        return d.as_dict()
+
+    def diagnostics(self, k: int | None = None) -> dict:
+        d = Diag()
+        if k is None:
+            self._check(lib().gpe2p_diagnostics(self.h, ctypes.byref(d)))
+        else:
+            self._check(lib().gpe2p_diagnostics_instance(self.h, int(k), ctypes.byref(d)))
+        return d.as_dict()
+
+    def config(self) -> dict:
+        tx, ty, pers = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = ctypes.c_double()
+        self._check(lib().gpe2p_batch_config(self.h, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(pers),
+                                             ctypes.byref(ms)))
+        return {"tile": (tx.value, ty.value), "persistent": bool(pers.value), "tuned_ms_per_step": ms.value}
+
+    def fault(self, what: int, value: int = 0):
+        self._check(lib().gpe2p_set_fault_injection(self.h, int(what), int(value)))
 
     def close(self):
         if getattr(self, "h", None):

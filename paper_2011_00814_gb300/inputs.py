@@ -186,3 +186,50 @@ def random_fields(prm: dict, seed: int, amp_u: float = 0.05, amp_p: float = 0.01
             vel[tuple(sl)] = 0.0
         f[nm] = vel
     return f
+
+
+def batch_instances(n: int = 96, seed: int = 0, sides=(64, 128, 192, 256, 384, 512), precision: int = 32):
+    """The batched 2D workload: n drops and bubbles on periodic boxes.
+
+    Per instance (seeded): side from ``sides``; density ratio log-uniform in
+    [2, 100] (rho_L = 1); viscosity ratio log-uniform in [1, 50]
+    (eta_L = 0.1); radius uniform in [0.15, 0.3] x side, centred; sigma
+    uniform in [1e-3, 1e-2]; M uniform in [5e-3, 2e-2]; W = 4 cells.  Even
+    instances are drops (phi = +1 inside, g = 0), odd ones bubbles (phi = -1
+    inside, |g| uniform in [0, 1e-5] along -y, rho_ref the mean density of
+    the initial state, so that the periodic box does not accelerate).  The
+    sound speed is U_c / Ma with U_c = sigma / eta_L and Ma = 0.1; dt is the
+    acoustic CFL 0.3 step, reduced where needed to 0.4 of the explicit
+    viscous bound 2.5 dx^2 / (16 nu_max) and the CH bound 2 / (M lam (8a + kappa lam)),
+    lam = 16/3 dx^-2.  Returns (list of params, list of field dicts)."""
+    rng = np.random.default_rng(seed)
+    prms, fields = [], []
+    for k in range(n):
+        side = int(rng.choice(sides))
+        r_rho = float(np.exp(rng.uniform(np.log(2.0), np.log(100.0))))
+        r_eta = float(np.exp(rng.uniform(np.log(1.0), np.log(50.0))))
+        frac = float(rng.uniform(0.15, 0.3))
+        sigma = float(rng.uniform(1e-3, 1e-2))
+        M = float(rng.uniform(5e-3, 2e-2))
+        gmag = float(rng.uniform(0.0, 1e-5)) if k % 2 else 0.0
+        etaL, W, dx = 0.1, 4.0, 1.0
+        rhoL, rhoG, etaG = 1.0, 1.0 / r_rho, etaL / r_eta
+        cs = (sigma / etaL) / 0.1
+        nu_max = max(etaL / rhoL, etaG / rhoG)
+        lam = 16.0 / 3.0 / (dx * dx)
+        a, kappa = 3.0 / (4.0 * W), 3.0 * W / 8.0
+        dt = min(0.3 * dx / cs, 0.4 * 2.5 * dx * dx / (16.0 * nu_max), 0.4 * 2.0 / (M * lam * (8.0 * a + kappa * lam)))
+        prm = base_params(2, side, side, dx=dx, dt=dt, cs=cs, rhoL=rhoL, rhoG=rhoG, etaL=etaL, etaG=etaG,
+                          sigma=sigma, M=M, W=W, g=(0.0, -gmag, 0.0), bc=("periodic", "periodic", "periodic"),
+                          ch_scheme=2, iso=9)
+        prm["precision"] = precision
+        f = zero_fields(prm)
+        x, y = cell_centres(prm)
+        r = np.sqrt((x - side / 2.0) ** 2 + (y - side / 2.0) ** 2)
+        sign = 1.0 if k % 2 == 0 else -1.0
+        f["phi"] = sign * np.tanh(2.0 * (frac * side - r) / W)
+        rho0 = 0.5 * (rhoL * (1.0 + f["phi"]) + rhoG * (1.0 - f["phi"]))
+        prm["rho_ref"] = float(np.mean(rho0)) if gmag > 0 else 0.0
+        prms.append(prm)
+        fields.append(f)
+    return prms, fields
