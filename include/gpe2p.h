@@ -201,6 +201,47 @@ enum { GPE2P_FAULT_SKIP_BARRIER = 1, GPE2P_FAULT_WAIT_LIMIT = 2, GPE2P_FAULT_FOR
        GPE2P_FAULT_CLEAR = 4 };
 int gpe2p_set_fault_injection(gpe2p_handle h, int what, long long value);
 
+/* ---- the learned surrogate ------------------------------------------- */
+/* A convolutional U-Net on the periodic 2D grid (SURVEY rows a12-a13 of the
+ * project, spec pattern 4; the paper has no learned component): levels
+ * l = 0..L-1 with channels[l] (multiples of 16) at resolution H/2^l;
+ * encoder l: [2x2 average pooling if l > 0] conv3x3 + SiLU, conv3x3 + SiLU;
+ * decoder l = L-2..0: nearest 2x upsampling, conv3x3 + SiLU, concatenation
+ * with the encoder output of level l, conv3x3 + SiLU, conv3x3 + SiLU; a 1x1
+ * head to out_ch channels.  Convolutions pad circularly.  BF16 weights and
+ * activations, FP32 accumulation on the tensor cores, FP32 master weights,
+ * Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).  Tensors are FP32
+ * device arrays in NHWC order [batch][H][W][channels]. */
+typedef struct gpe2p_net *gpe2p_net_handle;
+
+/* Creates the network with seeded He-uniform weights (zero biases, a head
+ * scaled by 0.01).  in_ch, out_ch in [1, 16]; H, W multiples of
+ * 2^(levels-1); max_batch bounds the batch of every call. */
+int gpe2p_net_create(int levels, const int *channels, int in_ch, int out_ch, int H, int W, int max_batch,
+                     unsigned long long seed, void *stream, gpe2p_net_handle *out);
+/* Number of FP32 parameters (the layout: per convolution, in the order
+ * encoder 0..L-1 (a, b), then decoder L-2..0 (up, a, b): weights
+ * [cout][tap][cin] with tap = 3(dy+1) + (dx+1), then bias [cout]; then the
+ * head weights [out_ch][channels[0]] and bias [out_ch]). */
+long long gpe2p_net_num_params(gpe2p_net_handle n);
+int gpe2p_net_get_params(gpe2p_net_handle n, float *host, long long count);
+/* Sets the master weights (and resets the Adam moments). */
+int gpe2p_net_set_params(gpe2p_net_handle n, const float *host, long long count);
+/* y[batch][H][W][out_ch] = net(x[batch][H][W][in_ch]); device pointers; asynchronous. */
+int gpe2p_net_forward(gpe2p_net_handle n, const float *x, float *y, int batch);
+/* Loss = mean over all outputs of (net(x) - t)^2 and its gradient with
+ * respect to the master weights, copied to grad (host, num_params floats)
+ * if not NULL.  Synchronises. */
+int gpe2p_net_gradients(gpe2p_net_handle n, const float *x, const float *t, int batch, float *grad, float *loss);
+/* One training step: the loss above, its gradient and one Adam update with
+ * learning rate lr.  The loss is copied to *loss if not NULL (which
+ * synchronises).  */
+int gpe2p_net_train_step(gpe2p_net_handle n, const float *x, const float *t, int batch, float lr, float *loss);
+/* Multiply-add FLOPs (x2) of one forward pass of a batch. */
+double gpe2p_net_flops(gpe2p_net_handle n, int batch);
+const char *gpe2p_net_last_error(gpe2p_net_handle n);
+void gpe2p_net_destroy(gpe2p_net_handle n);
+
 /* Largest number of cells gpe2p_diagnostics_noalloc accepts. */
 #define GPE2P_NOALLOC_MAX_CELLS 67108864LL
 

@@ -1,0 +1,59 @@
+// nn.h -- launchers of the surrogate's kernels (nn.cu), used by net.cu.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace gpe2p {
+namespace nn {
+
+// one convolution (3x3 circular or 1x1) as implicit GEMMs; see nn.cu
+struct ConvArgs {
+  int B, H, W, npix;   // batch, height, width, B*H*W
+  int cin, cout, taps; // channels in/out (multiples of 16), taps 9 (3x3) or 1 (1x1)
+  // forward: y = act(z), z = conv(x) + bias
+  const __nv_bfloat16* x;
+  int ldx, xoff;       // x: row stride (channels per pixel) and channel offset
+  const __nv_bfloat16* wt;  // [cout][taps*cin]
+  const float* bias;
+  __nv_bfloat16* z;    // pre-activation [npix][cout] (or nullptr)
+  __nv_bfloat16* y;
+  int ldy, yoff, act;  // act: 1 SiLU, 0 identity
+  // dgrad: dx (+)= conv^T(dz)
+  const __nv_bfloat16* dz;  // [npix][cout]
+  int ldz;
+  const __nv_bfloat16* wd;  // [cin][taps*cout]
+  __nv_bfloat16* dx;
+  int lddx, dxoff, accumulate;
+  // wgrad: dw[co][tap*cin + ci] += sum over pixels (FP32, split over ksplit pixels per block)
+  float* dw;
+  int ksplit;
+};
+
+cudaError_t conv_forward(const ConvArgs& a, cudaStream_t s);
+cudaError_t conv_dgrad(const ConvArgs& a, cudaStream_t s);
+cudaError_t conv_wgrad(const ConvArgs& a, cudaStream_t s);
+cudaError_t dsilu(const __nv_bfloat16* dy, int ldy, int yoff, const __nv_bfloat16* z, __nv_bfloat16* dz,
+                  long long npix, int c, cudaStream_t s);
+cudaError_t bias_grad(const __nv_bfloat16* dz, long long npix, int c, float* db, cudaStream_t s);
+cudaError_t pool_fwd(const __nv_bfloat16* x, int ldx, int xoff, __nv_bfloat16* y, int B, int H, int W, int c,
+                     cudaStream_t s);
+cudaError_t pool_bwd(const __nv_bfloat16* dy, __nv_bfloat16* dx, int ldx, int xoff, int B, int H, int W, int c,
+                     int accumulate, cudaStream_t s);
+cudaError_t up_fwd(const __nv_bfloat16* x, __nv_bfloat16* y, int B, int H, int W, int c, cudaStream_t s);
+cudaError_t up_bwd(const __nv_bfloat16* dy, __nv_bfloat16* dx, int B, int H, int W, int c, cudaStream_t s);
+cudaError_t copy_ch(const __nv_bfloat16* src, int lds, int soff, __nv_bfloat16* dst, int ldd, int doff,
+                    long long npix, int c, int accumulate, cudaStream_t s);
+cudaError_t to_bf16(const float* x, int cin, __nv_bfloat16* y, int ldo, long long npix, cudaStream_t s);
+cudaError_t head_fwd(const __nv_bfloat16* x, int cin, const float* w, const float* b, float* y, int cout,
+                     long long npix, cudaStream_t s);
+cudaError_t head_bwd(const __nv_bfloat16* x, int cin, const float* w, const float* dy, int cout, __nv_bfloat16* dx,
+                     float* dw, float* db, long long npix, cudaStream_t s);
+cudaError_t mse(const float* y, const float* t, float* dy, long long n, float* loss, cudaStream_t s);
+cudaError_t adam(float* w, const float* g, float* m, float* v, long long n, float lr, float b1, float b2, float eps,
+                 float c1, float c2, cudaStream_t s);
+cudaError_t weights_bf16(const float* w, __nv_bfloat16* wt, __nv_bfloat16* wd, int cout, int cin, int taps,
+                         cudaStream_t s);
+
+}  // namespace nn
+}  // namespace gpe2p

@@ -90,6 +90,26 @@ def lib():
         for nm in ("gpe2p_create_batch", "gpe2p_init_instance", "gpe2p_read_instance",
                    "gpe2p_diagnostics_instance", "gpe2p_batch_config", "gpe2p_set_fault_injection"):
             getattr(L, nm).restype = ctypes.c_int
+        fp = ctypes.POINTER(ctypes.c_float)
+        L.gpe2p_net_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, vp,
+                                       ctypes.POINTER(vp)]
+        L.gpe2p_net_num_params.argtypes = [vp]
+        L.gpe2p_net_num_params.restype = ctypes.c_longlong
+        L.gpe2p_net_get_params.argtypes = [vp, fp, ctypes.c_longlong]
+        L.gpe2p_net_set_params.argtypes = [vp, fp, ctypes.c_longlong]
+        L.gpe2p_net_forward.argtypes = [vp, vp, vp, ctypes.c_int]
+        L.gpe2p_net_gradients.argtypes = [vp, vp, vp, ctypes.c_int, fp, fp]
+        L.gpe2p_net_train_step.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_float, fp]
+        L.gpe2p_net_flops.argtypes = [vp, ctypes.c_int]
+        L.gpe2p_net_flops.restype = ctypes.c_double
+        L.gpe2p_net_last_error.argtypes = [vp]
+        L.gpe2p_net_last_error.restype = ctypes.c_char_p
+        L.gpe2p_net_destroy.argtypes = [vp]
+        L.gpe2p_net_destroy.restype = None
+        for nm in ("gpe2p_net_create", "gpe2p_net_get_params", "gpe2p_net_set_params", "gpe2p_net_forward",
+                   "gpe2p_net_gradients", "gpe2p_net_train_step"):
+            getattr(L, nm).restype = ctypes.c_int
         L.gpe2p_last_error.argtypes = [vp]
         L.gpe2p_last_error.restype = ctypes.c_char_p
         L.gpe2p_destroy.argtypes = [vp]
@@ -304,6 +324,79 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             lib().gpe2p_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Net:
+    """The surrogate U-Net (``gpe2p_net_*``).  Tensors are torch CUDA float32
+    tensors (or raw device pointers) in NHWC order."""
+
+    def __init__(self, levels, channels, in_ch, out_ch, H, W, max_batch, seed=0, stream: int | None = None):
+        self.levels, self.channels = int(levels), [int(c) for c in channels]
+        self.in_ch, self.out_ch, self.H, self.W, self.max_batch = in_ch, out_ch, H, W, max_batch
+        ch = (ctypes.c_int * len(channels))(*channels)
+        h = ctypes.c_void_p()
+        rc = lib().gpe2p_net_create(levels, ch, in_ch, out_ch, H, W, max_batch, ctypes.c_ulonglong(seed),
+                                    ctypes.c_void_p(stream) if stream else None, ctypes.byref(h))
+        if rc != OK:
+            raise GPE2PError(rc, lib().gpe2p_net_last_error(None).decode())
+        self.h = h
+        self.nparam = int(lib().gpe2p_net_num_params(h))
+
+    def _check(self, rc):
+        if rc != OK:
+            raise GPE2PError(rc, lib().gpe2p_net_last_error(self.h).decode())
+
+    @staticmethod
+    def _ptr(t):
+        return ctypes.c_void_p(t if isinstance(t, int) else t.data_ptr())
+
+    def get_params(self) -> np.ndarray:
+        p = np.empty(self.nparam, dtype=np.float32)
+        self._check(lib().gpe2p_net_get_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                               self.nparam))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(lib().gpe2p_net_set_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                               self.nparam))
+
+    def forward(self, x, y, batch: int):
+        self._check(lib().gpe2p_net_forward(self.h, self._ptr(x), self._ptr(y), int(batch)))
+
+    def gradients(self, x, t, batch: int):
+        g = np.empty(self.nparam, dtype=np.float32)
+        loss = ctypes.c_float()
+        self._check(lib().gpe2p_net_gradients(self.h, self._ptr(x), self._ptr(t), int(batch),
+                                              g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                              ctypes.byref(loss)))
+        return float(loss.value), g
+
+    def train_step(self, x, t, batch: int, lr: float, want_loss: bool = True):
+        loss = ctypes.c_float()
+        self._check(lib().gpe2p_net_train_step(self.h, self._ptr(x), self._ptr(t), int(batch), float(lr),
+                                               ctypes.byref(loss) if want_loss else None))
+        return float(loss.value) if want_loss else None
+
+    def flops(self, batch: int) -> float:
+        return float(lib().gpe2p_net_flops(self.h, int(batch)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gpe2p_net_destroy(self.h)
             self.h = None
 
     def __enter__(self):
