@@ -202,8 +202,8 @@ enum { GPE2P_FAULT_SKIP_BARRIER = 1, GPE2P_FAULT_WAIT_LIMIT = 2, GPE2P_FAULT_FOR
 int gpe2p_set_fault_injection(gpe2p_handle h, int what, long long value);
 
 /* ---- the learned surrogate ------------------------------------------- */
-/* A convolutional U-Net on the periodic 2D grid (SURVEY rows a12-a13 of the
- * project, spec pattern 4; the paper has no learned component): levels
+/* A convolutional U-Net on the periodic 2D grid that learns to advance the
+ * state over many solver steps (the paper has no learned component): levels
  * l = 0..L-1 with channels[l] (multiples of 16) at resolution H/2^l;
  * encoder l: [2x2 average pooling if l > 0] conv3x3 + SiLU, conv3x3 + SiLU;
  * decoder l = L-2..0: nearest 2x upsampling, conv3x3 + SiLU, concatenation
@@ -227,9 +227,18 @@ long long gpe2p_net_num_params(gpe2p_net_handle n);
 int gpe2p_net_get_params(gpe2p_net_handle n, float *host, long long count);
 /* Sets the master weights (and resets the Adam moments). */
 int gpe2p_net_set_params(gpe2p_net_handle n, const float *host, long long count);
+/* Input normalisation and output map (host arrays of in_ch, in_ch and
+ * out_ch floats; NULL for 0, 1, 1): the network sees
+ * (x[c] - in_mean[c]) / in_scale[c] and returns
+ * y[c] = (residual ? x[c] : 0) + out_scale[c] * head[c], so that with
+ * residual = 1 it predicts the increment of its first out_ch input
+ * channels; the loss below is then taken on (y - t) / out_scale.  Defaults
+ * 0, 1, 1, residual 0.  residual needs out_ch <= in_ch. */
+int gpe2p_net_set_normalization(gpe2p_net_handle n, const float *in_mean, const float *in_scale,
+                                const float *out_scale, int residual);
 /* y[batch][H][W][out_ch] = net(x[batch][H][W][in_ch]); device pointers; asynchronous. */
 int gpe2p_net_forward(gpe2p_net_handle n, const float *x, float *y, int batch);
-/* Loss = mean over all outputs of (net(x) - t)^2 and its gradient with
+/* Loss = mean over all outputs of ((net(x) - t) / out_scale)^2 and its gradient with
  * respect to the master weights, copied to grad (host, num_params floats)
  * if not NULL.  Synchronises. */
 int gpe2p_net_gradients(gpe2p_net_handle n, const float *x, const float *t, int batch, float *grad, float *loss);
@@ -237,10 +246,45 @@ int gpe2p_net_gradients(gpe2p_net_handle n, const float *x, const float *t, int 
  * learning rate lr.  The loss is copied to *loss if not NULL (which
  * synchronises).  */
 int gpe2p_net_train_step(gpe2p_net_handle n, const float *x, const float *t, int batch, float lr, float *loss);
+/* Kernels of the 3x3 forward and data-gradient convolutions: 1 (default)
+ * tcgen05.mma with the accumulator in tensor memory, 0 the warp-level
+ * mma.sync kernels.  Both compute the same products (FP32 accumulation in a
+ * different order). */
+int gpe2p_net_set_backend(gpe2p_net_handle n, int tcgen05);
+/* Waits for the network's stream and reports GPE2P_ETIMEOUT if a tensor-core
+ * kernel gave up a bounded wait since the handle was created (the outputs of
+ * that call are then undefined).  gpe2p_net_gradients and
+ * gpe2p_net_train_step (with a loss pointer) report it too. */
+int gpe2p_net_sync(gpe2p_net_handle n);
 /* Multiply-add FLOPs (x2) of one forward pass of a batch. */
 double gpe2p_net_flops(gpe2p_net_handle n, int batch);
 const char *gpe2p_net_last_error(gpe2p_net_handle n);
 void gpe2p_net_destroy(gpe2p_net_handle n);
+
+/* ---- the state as a network tensor --------------------------------------
+ * The learned surrogate (a network that advances the state over many
+ * steps) reads and writes the state of a 2D problem as a
+ * device array tensor[ny][nx][nch] of floats, nch = 4 or 5, with the
+ * channels 0 phi, 1 u, 2 v, 3 p (the velocity components of the cell's low
+ * faces, p the stored deviation from rho_ref c_s^2) and, for nch = 5,
+ * 4 rho(phi)/rho_L (the density law of Sec. 2).  Element (j, i, c) holds
+ * (field_c at cell (i, j) - mean[c]) / scale[c]; mean and scale are host
+ * arrays of nch floats (scale nonzero), or NULL for 0 and 1.  inst is the
+ * instance of a batch handle and is ignored for a single problem.  The
+ * paper has no counterpart of these calls.  All are ordered on the
+ * handle's stream; only gpe2p_state_distance waits for it. */
+int gpe2p_pack_state(gpe2p_handle h, int inst, float *tensor, int nch, const float *mean, const float *scale);
+/* The inverse: sets phi, u, v, p to mean[c] + scale[c] * tensor (channel 4
+ * is not read; wall faces of the normal velocity stay zero) and recomputes
+ * mu from phi (the chemical-potential equation).  The step counter is kept. */
+int gpe2p_unpack_state(gpe2p_handle h, int inst, const float *tensor, int nch, const float *mean,
+                       const float *scale);
+/* FP64 sums over the cells, for c = 0..3 (phi, u, v, p):
+ * out[2c] = sum (field_c - (mean[c] + scale[c] tensor_c))^2 and
+ * out[2c+1] = sum field_c^2 (out: 8 doubles on the host).  A per-handle
+ * scratch of about 20 KB is allocated on the first call.  Deterministic. */
+int gpe2p_state_distance(gpe2p_handle h, int inst, const float *tensor, int nch, const float *mean,
+                         const float *scale, double *out);
 
 /* Largest number of cells gpe2p_diagnostics_noalloc accepts. */
 #define GPE2P_NOALLOC_MAX_CELLS 67108864LL

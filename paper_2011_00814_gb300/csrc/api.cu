@@ -56,6 +56,8 @@ struct gpe2p_ctx {
   bool have_graph = false;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   BatchCtx* batch = nullptr;    // set for a batch of 2D instances
+  double* d_dist = nullptr;     // state-distance scratch (allocated on first use)
+  double* h_dist = nullptr;
   std::string err;
 };
 
@@ -813,10 +815,14 @@ extern "C" void gpe2p_destroy(gpe2p_handle h) {
   if (!h) return;
   if (h->batch) {
     batch_destroy(h->batch);
+    if (h->d_dist) cudaFree(h->d_dist);
+    if (h->h_dist) cudaFreeHost(h->h_dist);
     delete h;
     return;
   }
   cudaSetDevice(h->dev);
+  if (h->d_dist) cudaFree(h->d_dist);
+  if (h->h_dist) cudaFreeHost(h->h_dist);
   for (int c = 0; c < 2; ++c)
     if (h->gexec[c]) cudaGraphExecDestroy(h->gexec[c]);
   if (h->stream) cudaStreamSynchronize(h->stream);
@@ -894,4 +900,97 @@ extern "C" int gpe2p_set_fault_injection(gpe2p_handle h, int what, long long val
   std::string why;
   const int rc = batch_fault(h->batch, what, value, why);
   return rc == GPE2P_OK ? rc : fail(h, rc, why);
+}
+
+// ---------------------------------------------------------------------------
+// the state of a 2D problem as a network tensor
+// ---------------------------------------------------------------------------
+
+// the fields (phi, u, v, p, mu) of the single problem or of batch instance inst
+template <typename real>
+static int state_of(gpe2p_ctx* h, int inst, KParams<real>* P, real* f[5], int* iso, int** err) {
+  if (h->batch) {
+    *err = batch_err(h->batch);
+    return batch_instance<real>(h->batch, inst, P, f, iso);
+  }
+  *P = kparams<real>(h->prm);
+  const int c = h->cur;
+  f[0] = (real*)h->phi;
+  f[1] = (real*)h->Q[c][1];
+  f[2] = (real*)h->Q[c][2];
+  f[3] = (real*)h->Q[c][0];
+  f[4] = (real*)h->mu;
+  *iso = h->prm.iso;
+  *err = h->d_err;
+  return GPE2P_OK;
+}
+
+enum PackOp { OP_PACK, OP_UNPACK, OP_DISTANCE };
+
+template <typename real>
+static cudaError_t pack_op(gpe2p_ctx* h, int inst, PackOp op, float* t, int nch, const float* mean,
+                           const float* scale, cudaStream_t s, int* rc) {
+  KParams<real> P;
+  real* f[5];
+  int iso = 9;
+  int* err = nullptr;
+  *rc = state_of<real>(h, inst, &P, f, &iso, &err);
+  if (*rc != GPE2P_OK) return cudaSuccess;
+  if (op == OP_PACK) return launch_pack<real>(P, f, t, nch, mean, scale, s);
+  if (op == OP_DISTANCE) return launch_distance<real>(P, f, t, nch, mean, scale, h->d_dist, h->d_dist + 8 * kDistanceBlocks, s);
+  cudaError_t e = launch_unpack<real>(P, f, t, nch, mean, scale, s);
+  if (e != cudaSuccess) return e;
+  return launch_mu<real, 2>(P, f[0], f[4], iso, 1, s, nullptr, err);
+}
+
+static int pack_any(gpe2p_handle h, int inst, PackOp op, float* t, int nch, const float* mean, const float* scale,
+                    double* dist) {
+  if (!h || !t) return fail(h, GPE2P_EINVAL, "NULL argument");
+  if (nch != 4 && nch != 5) return fail(h, GPE2P_EINVAL, "nch must be 4 or 5");
+  for (int c = 0; c < nch; ++c)
+    if ((scale && (!(scale[c] != 0.0f) || !std::isfinite(scale[c]))) || (mean && !std::isfinite(mean[c])))
+      return fail(h, GPE2P_EINVAL, "mean and scale must be finite, scale nonzero");
+  if (!h->batch && h->prm.dim != 2) return fail(h, GPE2P_EINVAL, "the tensor form is defined for 2D problems");
+  if (h->batch && (inst < 0 || inst >= batch_size(h->batch))) return fail(h, GPE2P_EINVAL, "instance index out of range");
+  if (!h->batch && !h->initialized && op != OP_UNPACK) return fail(h, GPE2P_ESTATE, "state used before gpe2p_init_fields");
+  const int dev = h->batch ? batch_dev(h->batch) : h->dev;
+  const int esize = h->batch ? batch_esize(h->batch) : h->esize;
+  cudaStream_t s = h->batch ? batch_stream(h->batch) : h->stream;
+  CK(h, cudaSetDevice(dev), "set device");
+  if (op == OP_DISTANCE && !h->d_dist) {
+    CK(h, cudaMalloc((void**)&h->d_dist, (8 * kDistanceBlocks + 8) * sizeof(double)), "distance scratch");
+    CK(h, cudaMallocHost((void**)&h->h_dist, 8 * sizeof(double)), "distance scratch");
+  }
+  int rc = GPE2P_OK;
+  cudaError_t e = esize == 4 ? pack_op<float>(h, inst, op, t, nch, mean, scale, s, &rc)
+                             : pack_op<double>(h, inst, op, t, nch, mean, scale, s, &rc);
+  if (rc != GPE2P_OK) return fail(h, rc, "instance index out of range");
+  if (e != cudaSuccess) return cuda_fail(h, e, op == OP_PACK ? "pack" : op == OP_UNPACK ? "unpack" : "distance");
+  if (op == OP_UNPACK) {
+    if (h->batch) batch_mark_initialized(h->batch);
+    else h->initialized = true;
+  }
+  if (op == OP_DISTANCE) {
+    CK(h, cudaMemcpyAsync(h->h_dist, h->d_dist + 8 * kDistanceBlocks, 8 * sizeof(double), cudaMemcpyDeviceToHost, s),
+       "distance");
+    CK(h, cudaStreamSynchronize(s), "distance");
+    std::memcpy(dist, h->h_dist, 8 * sizeof(double));
+  }
+  return GPE2P_OK;
+}
+
+extern "C" int gpe2p_pack_state(gpe2p_handle h, int inst, float* tensor, int nch, const float* mean,
+                                const float* scale) {
+  return pack_any(h, inst, OP_PACK, tensor, nch, mean, scale, nullptr);
+}
+
+extern "C" int gpe2p_unpack_state(gpe2p_handle h, int inst, const float* tensor, int nch, const float* mean,
+                                  const float* scale) {
+  return pack_any(h, inst, OP_UNPACK, const_cast<float*>(tensor), nch, mean, scale, nullptr);
+}
+
+extern "C" int gpe2p_state_distance(gpe2p_handle h, int inst, const float* tensor, int nch, const float* mean,
+                                    const float* scale, double* out) {
+  if (!out) return fail(h, GPE2P_EINVAL, "NULL argument");
+  return pack_any(h, inst, OP_DISTANCE, const_cast<float*>(tensor), nch, mean, scale, out);
 }

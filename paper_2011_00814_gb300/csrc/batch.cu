@@ -723,6 +723,30 @@ int batch_fault(BatchCtx* b, int what, long long value, std::string& why) {
   return GPE2P_OK;
 }
 
+template <typename real>
+int batch_instance(BatchCtx* b, int k, KParams<real>* P, real* f[5], int* iso) {
+  if (k < 0 || k >= b->n || (int)sizeof(real) != b->esize) return GPE2P_EINVAL;
+  const BInst<real>* I = reinterpret_cast<const BInst<real>*>(b->insts_host.data());
+  const int c = b->cur;
+  *P = I[k].P;
+  f[0] = I[k].phi;
+  f[1] = I[k].Q[c][1];
+  f[2] = I[k].Q[c][2];
+  f[3] = I[k].Q[c][0];
+  f[4] = I[k].mu;
+  *iso = b->prm[k].iso;
+  return GPE2P_OK;
+}
+template int batch_instance<float>(BatchCtx*, int, KParams<float>*, float* [5], int*);
+template int batch_instance<double>(BatchCtx*, int, KParams<double>*, double* [5], int*);
+
+void batch_mark_initialized(BatchCtx* b) { b->initialized = true; }
+int* batch_err(BatchCtx* b) { return b->err; }
+int batch_dev(const BatchCtx* b) { return b->dev; }
+int batch_esize(const BatchCtx* b) { return b->esize; }
+
+cudaStream_t batch_stream(const BatchCtx* b) { return b->stream; }
+
 long long batch_cells(const BatchCtx* b) {
   long long s = 0;
   for (long long c : b->ncell) s += c;

@@ -72,4 +72,17 @@ cudaError_t launch_from_double(const KParams<real>& P, const double* src, real* 
 template <typename real>
 cudaError_t launch_to_double(const KParams<real>& P, const real* src, double* dst, long long n, cudaStream_t s);
 
+// 2D state <-> network tensor [ny][nx][nch] (phi, u, v, p[, rho/rho_L]); see pack.cu
+constexpr int kDistanceBlocks = 304;
+template <typename real>
+cudaError_t launch_pack(const KParams<real>& P, const real* const f[4], float* out, int nch, const float* mean,
+                        const float* scale, cudaStream_t s);
+template <typename real>
+cudaError_t launch_unpack(const KParams<real>& P, real* const f[4], const float* in, int nch, const float* mean,
+                          const float* scale, cudaStream_t s);
+// part: kDistanceBlocks * 8 doubles; out: 8 doubles (device)
+template <typename real>
+cudaError_t launch_distance(const KParams<real>& P, const real* const f[4], const float* in, int nch, const float* mean,
+                            const float* scale, double* part, double* out, cudaStream_t s);
+
 }  // namespace gpe2p

@@ -50,6 +50,10 @@ struct gpe2p_net {
   long long nparam = 0, head_w = 0, head_b = 0;
   float *P = nullptr, *G = nullptr, *Am = nullptr, *Av = nullptr;
   long long adam_t = 0;
+  int use_tc = 1;                // 3x3 forward / data gradient on tcgen05
+  int* d_err = nullptr;          // device error word of the tcgen05 kernels
+  int* h_err = nullptr;          // pinned copy
+  Norm norm{};
   Act in16;
   std::vector<Act> ea, eb, pooled, upx, cat, da, db;
   __nv_bfloat16* dz = nullptr;   // scratch for one layer's dZ
@@ -123,6 +127,8 @@ static ConvArgs conv_args(const gpe2p_net* n, const ConvL& c, int B) {
   a.ldz = c.cout;
   a.dw = n->G + c.w;
   a.ksplit = 2048;
+  a.tc = n->use_tc;
+  a.err = n->d_err;
   return a;
 }
 
@@ -165,7 +171,7 @@ static cudaError_t bwd(gpe2p_net* n, const ConvL& c, int B, const __nv_bfloat16*
 
 static cudaError_t forward(gpe2p_net* n, const float* x, int B) {
   const int L = n->L;
-  cudaError_t e = to_bf16(x, n->in_ch, n->in16.v, 16, npix_at(n, 0, B), n->stream);
+  cudaError_t e = to_bf16(x, n->in_ch, n->in16.v, 16, npix_at(n, 0, B), n->norm, n->stream);
   if (e != cudaSuccess) return e;
   for (int l = 0; l < L; ++l) {
     const __nv_bfloat16* in = n->in16.v;
@@ -192,7 +198,8 @@ static cudaError_t forward(gpe2p_net* n, const float* x, int B) {
     if ((e = fwd(n, n->conv[n->dec_b[l]], B, n->da[l].v, c, 0, n->db[l].v, c, 0)) != cudaSuccess) return e;
     din = n->db[l].v;
   }
-  return head_fwd(din, n->ch[0], n->P + n->head_w, n->P + n->head_b, n->out, n->out_ch, npix_at(n, 0, B), n->stream);
+  return head_fwd(din, n->ch[0], n->P + n->head_w, n->P + n->head_b, n->out, n->out_ch, npix_at(n, 0, B), x,
+                  n->in_ch, n->norm, n->stream);
 }
 
 static cudaError_t backward(gpe2p_net* n, int B) {
@@ -262,6 +269,12 @@ extern "C" int gpe2p_net_create(int levels, const int* channels, int in_ch, int 
   n->H = H;
   n->W = W;
   n->maxB = max_batch;
+  for (int c = 0; c < 16; ++c) {
+    n->norm.mean[c] = 0.f;
+    n->norm.inv[c] = 1.f;
+    n->norm.oscale[c] = 1.f;
+  }
+  n->norm.residual = 0;
   cudaError_t e = cudaSuccess;
   if (stream) n->stream = (cudaStream_t)stream;
   else {
@@ -329,9 +342,12 @@ extern "C" int gpe2p_net_create(int levels, const int* channels, int in_ch, int 
     }
   }
   if ((e = nalloc(n, &n->dz, (size_t)zmax)) || (e = nalloc(n, &n->out, (size_t)npix_at(n, 0, B) * out_ch)) ||
-      (e = nalloc(n, &n->dout, (size_t)npix_at(n, 0, B) * out_ch)) || (e = nalloc(n, &n->loss, 1)))
+      (e = nalloc(n, &n->dout, (size_t)npix_at(n, 0, B) * out_ch)) || (e = nalloc(n, &n->loss, 1)) ||
+      (e = nalloc(n, &n->d_err, 1)))
     return fail_alloc(e);
   if ((e = cudaMallocHost((void**)&n->loss_h, sizeof(float)))) return fail_alloc(e);
+  if ((e = cudaMallocHost((void**)&n->h_err, sizeof(int)))) return fail_alloc(e);
+  if ((e = cudaMemset(n->d_err, 0, sizeof(int)))) return fail_alloc(e);
   // He-uniform initial weights (seeded), zero biases, a small head
   std::vector<float> p(n->nparam, 0.f);
   std::mt19937_64 rng(seed);
@@ -353,6 +369,47 @@ extern "C" int gpe2p_net_create(int levels, const int* channels, int in_ch, int 
     return net_fail(nullptr, GPE2P_ECUDA, std::string("net set-up: ") + cudaGetErrorString(e));
   }
   *out = n;
+  return GPE2P_OK;
+}
+
+extern "C" int gpe2p_net_set_normalization(gpe2p_net_handle n, const float* in_mean, const float* in_scale,
+                                           const float* out_scale, int residual) {
+  if (!n) return net_fail(n, GPE2P_EINVAL, "NULL handle");
+  if (residual != 0 && residual != 1) return net_fail(n, GPE2P_EINVAL, "residual must be 0 or 1");
+  if (residual && n->out_ch > n->in_ch) return net_fail(n, GPE2P_EINVAL, "residual needs out_ch <= in_ch");
+  Norm nm = n->norm;
+  for (int c = 0; c < n->in_ch; ++c) {
+    const float m = in_mean ? in_mean[c] : 0.f, s = in_scale ? in_scale[c] : 1.f;
+    if (!std::isfinite(m) || !std::isfinite(s) || !(s != 0.f)) return net_fail(n, GPE2P_EINVAL, "bad input normalisation");
+    nm.mean[c] = m;
+    nm.inv[c] = 1.0f / s;
+  }
+  for (int c = 0; c < n->out_ch; ++c) {
+    const float s = out_scale ? out_scale[c] : 1.f;
+    if (!std::isfinite(s) || !(s != 0.f)) return net_fail(n, GPE2P_EINVAL, "bad output scale");
+    nm.oscale[c] = s;
+  }
+  nm.residual = residual;
+  n->norm = nm;
+  return GPE2P_OK;
+}
+
+// after a synchronisation: GPE2P_ETIMEOUT if a tcgen05 kernel gave up a wait
+static int net_err_word(gpe2p_net* n) {
+  NK(n, cudaMemcpyAsync(n->h_err, n->d_err, sizeof(int), cudaMemcpyDeviceToHost, n->stream), "error word");
+  NK(n, cudaStreamSynchronize(n->stream), "error word");
+  if (*n->h_err) return net_fail(n, GPE2P_ETIMEOUT, "a tensor-core kernel timed out waiting for its MMAs");
+  return GPE2P_OK;
+}
+
+extern "C" int gpe2p_net_sync(gpe2p_net_handle n) {
+  if (!n) return net_fail(n, GPE2P_EINVAL, "NULL handle");
+  return net_err_word(n);
+}
+
+extern "C" int gpe2p_net_set_backend(gpe2p_net_handle n, int tcgen05) {
+  if (!n || (tcgen05 != 0 && tcgen05 != 1)) return net_fail(n, GPE2P_EINVAL, "bad arguments");
+  n->use_tc = tcgen05;
   return GPE2P_OK;
 }
 
@@ -389,7 +446,7 @@ static int loss_and_grads(gpe2p_net* n, const float* x, const float* t, int batc
   NK(n, cudaMemsetAsync(n->G, 0, n->nparam * sizeof(float), n->stream), "zero grads");
   NK(n, cudaMemsetAsync(n->loss, 0, sizeof(float), n->stream), "zero loss");
   NK(n, forward(n, x, batch), "forward");
-  NK(n, mse(n->out, t, n->dout, npix_at(n, 0, batch) * n->out_ch, n->loss, n->stream), "loss");
+  NK(n, mse(n->out, t, n->dout, npix_at(n, 0, batch) * n->out_ch, n->out_ch, n->norm, n->loss, n->stream), "loss");
   NK(n, backward(n, batch), "backward");
   return GPE2P_OK;
 }
@@ -403,7 +460,7 @@ extern "C" int gpe2p_net_gradients(gpe2p_net_handle n, const float* x, const flo
   NK(n, cudaMemcpyAsync(n->loss_h, n->loss, sizeof(float), cudaMemcpyDeviceToHost, n->stream), "loss");
   NK(n, cudaStreamSynchronize(n->stream), "gradients");
   if (loss) *loss = *n->loss_h;
-  return GPE2P_OK;
+  return net_err_word(n);
 }
 
 extern "C" int gpe2p_net_train_step(gpe2p_net_handle n, const float* x, const float* t, int batch, float lr,
@@ -421,6 +478,7 @@ extern "C" int gpe2p_net_train_step(gpe2p_net_handle n, const float* x, const fl
     NK(n, cudaMemcpyAsync(n->loss_h, n->loss, sizeof(float), cudaMemcpyDeviceToHost, n->stream), "loss");
     NK(n, cudaStreamSynchronize(n->stream), "train step");
     *loss = *n->loss_h;
+    return net_err_word(n);
   }
   return GPE2P_OK;
 }
@@ -440,6 +498,7 @@ extern "C" void gpe2p_net_destroy(gpe2p_net_handle n) {
   if (n->stream) cudaStreamSynchronize(n->stream);
   for (void* p : n->allocs) cudaFree(p);
   if (n->loss_h) cudaFreeHost(n->loss_h);
+  if (n->h_err) cudaFreeHost(n->h_err);
   if (n->own_stream && n->stream) cudaStreamDestroy(n->stream);
   delete n;
 }

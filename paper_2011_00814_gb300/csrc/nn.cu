@@ -337,24 +337,25 @@ __global__ void copy_ch_kernel(const __nv_bfloat16* src, int lds, int soff, __nv
   }
 }
 
-// FP32 NHWC (cin channels) -> BF16 NHWC padded to ldo channels with zeros
-__global__ void to_bf16_kernel(const float* x, int cin, __nv_bfloat16* y, int ldo, long long npix) {
+// FP32 NHWC (cin channels) -> normalised BF16 NHWC padded to ldo channels with zeros
+__global__ void to_bf16_kernel(const float* x, int cin, __nv_bfloat16* y, int ldo, long long npix, const Norm nm) {
   const long long n = npix * ldo;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const long long p = i / ldo;
     const int ch = (int)(i - p * ldo);
-    y[i] = __float2bfloat16_rn(ch < cin ? x[p * cin + ch] : 0.f);
+    y[i] = __float2bfloat16_rn(ch < cin ? (x[p * cin + ch] - nm.mean[ch]) * nm.inv[ch] : 0.f);
   }
 }
 
-// output layer: 1x1 convolution cin -> cout (small cout), FP32 out, no activation
+// output layer: 1x1 convolution cin -> cout (small cout), FP32 out, no activation, then the
+// output map (scale, optional residual from the raw FP32 input xin of in_ch channels)
 __global__ void head_fwd_kernel(const __nv_bfloat16* x, int cin, const float* w, const float* b, float* y, int cout,
-                                long long npix) {
+                                long long npix, const float* xin, int in_ch, const Norm nm) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix; p += (long long)gridDim.x * blockDim.x) {
     for (int o = 0; o < cout; ++o) {
       float s = b[o];
       for (int c = 0; c < cin; ++c) s += w[o * cin + c] * __bfloat162float(x[p * cin + c]);
-      y[p * cout + o] = s;
+      y[p * cout + o] = (nm.residual ? xin[p * in_ch + o] : 0.f) + nm.oscale[o] * s;
     }
   }
 }
@@ -383,13 +384,15 @@ __global__ void head_bwd_kernel(const __nv_bfloat16* x, int cin, const float* w,
   for (int q = threadIdx.x; q < cout; q += blockDim.x) atomicAdd(db + q, sred[cout * cin + q]);
 }
 
-// mean squared error and its gradient: loss += sum (y - t)^2 / n, dy = 2 (y - t) / n
-__global__ void mse_kernel(const float* y, const float* t, float* dy, long long n, float* loss) {
+// mean squared error of the scaled output error e = (y - t) / oscale and its gradient with
+// respect to the head's output: loss += sum e^2 / n, dy = 2 e / n
+__global__ void mse_kernel(const float* y, const float* t, float* dy, long long n, int cout, const Norm nm,
+                           float* loss) {
   __shared__ float red[256];
   float s = 0.f;
   const float inv = 1.0f / (float)n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float d = y[i] - t[i];
+    const float d = (y[i] - t[i]) / nm.oscale[i % cout];
     s += d * d;
     if (dy) dy[i] = 2.0f * d * inv;
   }
@@ -433,6 +436,7 @@ __global__ void weights_bf16_kernel(const float* w, __nv_bfloat16* wt, __nv_bflo
 // ---------------------------------------------------------------------------
 
 cudaError_t conv_forward(const ConvArgs& a, cudaStream_t s) {
+  if (a.tc && conv_tc_supported(a, 0)) return conv_forward_tc(a, s);
   dim3 grid((a.npix + BM - 1) / BM, (a.cout + 63) / 64);
   if (a.cout % 64 == 0) {
     igemm_kernel<0, 64><<<grid, NT, 0, s>>>(a);
@@ -444,6 +448,7 @@ cudaError_t conv_forward(const ConvArgs& a, cudaStream_t s) {
 }
 
 cudaError_t conv_dgrad(const ConvArgs& a, cudaStream_t s) {
+  if (a.tc && conv_tc_supported(a, 1)) return conv_dgrad_tc(a, s);
   dim3 grid((a.npix + BM - 1) / BM, (a.cin + 63) / 64);
   if (a.cin % 64 == 0) {
     igemm_kernel<1, 64><<<grid, NT, 0, s>>>(a);
@@ -503,14 +508,15 @@ cudaError_t copy_ch(const __nv_bfloat16* src, int lds, int soff, __nv_bfloat16* 
   return cudaGetLastError();
 }
 
-cudaError_t to_bf16(const float* x, int cin, __nv_bfloat16* y, int ldo, long long npix, cudaStream_t s) {
-  to_bf16_kernel<<<blocks_for(npix * ldo), 256, 0, s>>>(x, cin, y, ldo, npix);
+cudaError_t to_bf16(const float* x, int cin, __nv_bfloat16* y, int ldo, long long npix, const Norm& nm,
+                    cudaStream_t s) {
+  to_bf16_kernel<<<blocks_for(npix * ldo), 256, 0, s>>>(x, cin, y, ldo, npix, nm);
   return cudaGetLastError();
 }
 
 cudaError_t head_fwd(const __nv_bfloat16* x, int cin, const float* w, const float* b, float* y, int cout,
-                     long long npix, cudaStream_t s) {
-  head_fwd_kernel<<<blocks_for(npix), 256, 0, s>>>(x, cin, w, b, y, cout, npix);
+                     long long npix, const float* xin, int in_ch, const Norm& nm, cudaStream_t s) {
+  head_fwd_kernel<<<blocks_for(npix), 256, 0, s>>>(x, cin, w, b, y, cout, npix, xin, in_ch, nm);
   return cudaGetLastError();
 }
 
@@ -523,8 +529,9 @@ cudaError_t head_bwd(const __nv_bfloat16* x, int cin, const float* w, const floa
   return cudaGetLastError();
 }
 
-cudaError_t mse(const float* y, const float* t, float* dy, long long n, float* loss, cudaStream_t s) {
-  mse_kernel<<<blocks_for(n), 256, 0, s>>>(y, t, dy, n, loss);
+cudaError_t mse(const float* y, const float* t, float* dy, long long n, int cout, const Norm& nm, float* loss,
+                cudaStream_t s) {
+  mse_kernel<<<blocks_for(n), 256, 0, s>>>(y, t, dy, n, cout, nm, loss);
   return cudaGetLastError();
 }
 

@@ -99,6 +99,9 @@ def lib():
         L.gpe2p_net_get_params.argtypes = [vp, fp, ctypes.c_longlong]
         L.gpe2p_net_set_params.argtypes = [vp, fp, ctypes.c_longlong]
         L.gpe2p_net_forward.argtypes = [vp, vp, vp, ctypes.c_int]
+        L.gpe2p_net_set_normalization.argtypes = [vp, fp, fp, fp, ctypes.c_int]
+        L.gpe2p_net_set_backend.argtypes = [vp, ctypes.c_int]
+        L.gpe2p_net_sync.argtypes = [vp]
         L.gpe2p_net_gradients.argtypes = [vp, vp, vp, ctypes.c_int, fp, fp]
         L.gpe2p_net_train_step.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_float, fp]
         L.gpe2p_net_flops.argtypes = [vp, ctypes.c_int]
@@ -110,6 +113,12 @@ def lib():
         for nm in ("gpe2p_net_create", "gpe2p_net_get_params", "gpe2p_net_set_params", "gpe2p_net_forward",
                    "gpe2p_net_gradients", "gpe2p_net_train_step"):
             getattr(L, nm).restype = ctypes.c_int
+        for nm in ("gpe2p_pack_state", "gpe2p_unpack_state"):
+            getattr(L, nm).argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, fp, fp]
+            getattr(L, nm).restype = ctypes.c_int
+        L.gpe2p_state_distance.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, fp, fp,
+                                           ctypes.POINTER(ctypes.c_double)]
+        L.gpe2p_state_distance.restype = ctypes.c_int
         L.gpe2p_last_error.argtypes = [vp]
         L.gpe2p_last_error.restype = ctypes.c_char_p
         L.gpe2p_destroy.argtypes = [vp]
@@ -158,6 +167,29 @@ def stability_limits(prm: dict):
     if rc != OK:
         raise GPE2PError(rc, lib().gpe2p_last_error(None).decode())
     return tuple(out)
+
+
+def _tensor_call(obj, op, inst, tensor, mean, scale):
+    """Marshal one call of the state <-> tensor family; ``tensor`` is a
+    contiguous CUDA float32 tensor [ny, nx, nch] (or a raw device pointer
+    with ``nch`` taken from ``mean``)."""
+    if isinstance(tensor, int):
+        ptr, nch = tensor, len(mean) if mean is not None else 4
+    else:
+        if tensor.dtype != __import__("torch").float32 or not tensor.is_contiguous() or not tensor.is_cuda:
+            raise ValueError("tensor must be a contiguous CUDA float32 tensor")
+        ptr, nch = tensor.data_ptr(), int(tensor.shape[-1])
+    m = None if mean is None else (ctypes.c_float * nch)(*[float(x) for x in mean])
+    s = None if scale is None else (ctypes.c_float * nch)(*[float(x) for x in scale])
+    L = lib()
+    if op == "pack":
+        obj._check(L.gpe2p_pack_state(obj.h, int(inst), ctypes.c_void_p(ptr), nch, m, s))
+    elif op == "unpack":
+        obj._check(L.gpe2p_unpack_state(obj.h, int(inst), ctypes.c_void_p(ptr), nch, m, s))
+    else:
+        out = (ctypes.c_double * 8)()
+        obj._check(L.gpe2p_state_distance(obj.h, int(inst), ctypes.c_void_p(ptr), nch, m, s, out))
+        return list(out)
 
 
 class Solver:
@@ -233,6 +265,18 @@ class Solver:
         self._check(lib().gpe2p_profile_steps(self.h, int(nsteps), ms, 64, ctypes.byref(n), names, 2048))
         nm = names.value.decode().split(",")
         return [(nm[i], ms[i]) for i in range(n.value)]
+
+    def pack(self, tensor, mean=None, scale=None):
+        """State -> tensor [ny, nx, nch] (phi, u, v, p[, rho/rho_L]), normalised."""
+        _tensor_call(self, "pack", 0, tensor, mean, scale)
+
+    def unpack(self, tensor, mean=None, scale=None):
+        """Tensor -> state (mu recomputed)."""
+        _tensor_call(self, "unpack", 0, tensor, mean, scale)
+
+    def distance(self, tensor, mean=None, scale=None):
+        """[sum (f_c - t_c)^2, sum f_c^2] for c = phi, u, v, p (8 floats)."""
+        return _tensor_call(self, "distance", 0, tensor, mean, scale)
 
     def field_ptr(self, name: str):
         """(device pointer, row pitch in elements) of a field of the current state."""
@@ -311,6 +355,15 @@ class Batch:
             self._check(lib().gpe2p_diagnostics_instance(self.h, int(k), ctypes.byref(d)))
         return d.as_dict()
 
+    def pack(self, k: int, tensor, mean=None, scale=None):
+        _tensor_call(self, "pack", k, tensor, mean, scale)
+
+    def unpack(self, k: int, tensor, mean=None, scale=None):
+        _tensor_call(self, "unpack", k, tensor, mean, scale)
+
+    def distance(self, k: int, tensor, mean=None, scale=None):
+        return _tensor_call(self, "distance", k, tensor, mean, scale)
+
     def config(self) -> dict:
         tx, ty, pers = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         ms = ctypes.c_double()
@@ -373,6 +426,20 @@ class Net:
         p = np.ascontiguousarray(p, dtype=np.float32)
         self._check(lib().gpe2p_net_set_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                                self.nparam))
+
+    def set_normalization(self, in_mean=None, in_scale=None, out_scale=None, residual: bool = False):
+        """Input normalisation and output map (see gpe2p_net_set_normalization)."""
+        def arr(v, n):
+            return None if v is None else (ctypes.c_float * n)(*[float(a) for a in v])
+        self._check(lib().gpe2p_net_set_normalization(self.h, arr(in_mean, self.in_ch), arr(in_scale, self.in_ch),
+                                                      arr(out_scale, self.out_ch), int(bool(residual))))
+
+    def set_backend(self, tcgen05: bool):
+        """3x3 convolutions on tcgen05 (True, default) or on mma.sync (False)."""
+        self._check(lib().gpe2p_net_set_backend(self.h, int(bool(tcgen05))))
+
+    def sync(self):
+        self._check(lib().gpe2p_net_sync(self.h))
 
     def forward(self, x, y, batch: int):
         self._check(lib().gpe2p_net_forward(self.h, self._ptr(x), self._ptr(y), int(batch)))

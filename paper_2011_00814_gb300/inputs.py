@@ -233,3 +233,51 @@ def batch_instances(n: int = 96, seed: int = 0, sides=(64, 128, 192, 256, 384, 5
         prms.append(prm)
         fields.append(f)
     return prms, fields
+
+
+def two_drops(seed: int, n: int = 256, gap=(2.0, 8.0), precision: int = 32):
+    """Two drops on a periodic n x n box: the surrogate's training and test case.
+
+    Seeded draws: radii R1, R2 uniform in [20, 50] cells (scaled by n / 256
+    on other boxes); density ratio
+    log-uniform in [2, 20] (rho_L = 1) with the viscosity ratio equal to it
+    (eta_L = 0.1, so both phases have the kinematic viscosity 0.1); the
+    first centre uniform on the box, the second at the distance
+    R1 + R2 + gap in a uniform direction, gap uniform in ``gap`` cells, so
+    that the drops are separate but close enough to coalesce within a few
+    thousand steps.  phi is the larger of the two profiles
+    tanh(2 (R - d) / W), d the periodic distance to the centre.
+    sigma = 0.01, M = 0.02, W = 4, Mach 0.1 with U_c = sigma / eta_L
+    (c_s = 1) and acoustic CFL 0.3 (dt = 0.3; the viscous and CH bounds of
+    ``batch_instances`` are looser here).  u = v = p = 0.
+    Returns (params, fields)."""
+    rng = np.random.default_rng([seed, 20110814])
+    R1, R2 = (float(r) * n / 256.0 for r in rng.uniform(20.0, 50.0, size=2))
+    r_rho = float(np.exp(rng.uniform(np.log(2.0), np.log(20.0))))
+    c1 = rng.uniform(0.0, n, size=2)
+    ang = float(rng.uniform(0.0, 2.0 * math.pi))
+    dist = R1 + R2 + float(rng.uniform(*gap))
+    c2 = (c1 + dist * np.array([math.cos(ang), math.sin(ang)])) % n
+    etaL, sigma, M, W, dx = 0.1, 0.01, 0.02, 4.0, 1.0
+    rhoL, rhoG, etaG = 1.0, 1.0 / r_rho, etaL / r_rho
+    cs = (sigma / etaL) / 0.1
+    nu_max = max(etaL / rhoL, etaG / rhoG)
+    lam = 16.0 / 3.0 / (dx * dx)
+    a, kappa = 3.0 / (4.0 * W), 3.0 * W / 8.0
+    dt = min(0.3 * dx / cs, 0.4 * 2.5 * dx * dx / (16.0 * nu_max), 0.4 * 2.0 / (M * lam * (8.0 * a + kappa * lam)))
+    prm = base_params(2, n, n, dx=dx, dt=dt, cs=cs, rhoL=rhoL, rhoG=rhoG, etaL=etaL, etaG=etaG, sigma=sigma, M=M,
+                      W=W, bc=("periodic", "periodic", "periodic"), ch_scheme=2, iso=9)
+    prm["precision"] = precision
+    prm["r_rho"] = r_rho
+    f = zero_fields(prm)
+    x, y = cell_centres(prm)
+
+    def pdist(c):
+        dxp = np.abs(x - c[0])
+        dyp = np.abs(y - c[1])
+        dxp = np.minimum(dxp, n - dxp)
+        dyp = np.minimum(dyp, n - dyp)
+        return np.sqrt(dxp ** 2 + dyp ** 2)
+
+    f["phi"] = np.maximum(np.tanh(2.0 * (R1 - pdist(c1)) / W), np.tanh(2.0 * (R2 - pdist(c2)) / W))
+    return prm, f

@@ -1,0 +1,355 @@
+"""Learned surrogate of the 2D two-phase step, with the solver as judge and fallback.
+
+A convolutional U-Net (the library's ``gpe2p_net_*``) advances the state
+(phi, u, v, p) of a periodic 2D problem over K solver steps in one call.  Its
+input is the packed state plus the density channel rho(phi)/rho_L
+(``gpe2p_pack_state`` with 5 channels), normalised per channel; its output is
+the state K steps later, formed as the input plus a scaled learned increment
+(``residual`` output map), and written back with ``gpe2p_unpack_state``,
+which also recomputes mu from phi.  Every step of that path runs in the
+library's kernels; this module only sequences the calls.
+
+The controller keeps the solver as the judge: every ``check_every``-th call
+also runs the K solver steps from the same start and measures the relative
+phi L2 distance between the two results (``gpe2p_state_distance``).  The
+solver's result is kept.  If the distance exceeds ``tol``, the window of calls
+since the last check is discarded, the state at that check is restored and
+the window is recomputed by the solver, and the next ``cooldown`` windows run
+on the solver alone.  Training data are trajectories of the solver itself
+(the batched engine), and training runs on the library's forward, backward
+and Adam kernels.  The paper has no learned component; this is an extension
+around its method.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+
+import numpy as np
+
+from . import gpe2p, inputs
+
+NCH = 5                    # phi, u, v, p, rho(phi)/rho_L
+LEVELS = 4
+CHANNELS = (32, 64, 128, 256)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+# ---------------------------------------------------------------------------
+# the network with its normalisation
+# ---------------------------------------------------------------------------
+
+class Surrogate:
+    """The U-Net that maps the packed state to the state ``K`` steps later."""
+
+    def __init__(self, n: int = 256, K: int = 64, levels: int = LEVELS, channels=CHANNELS, max_batch: int = 8,
+                 seed: int = 0):
+        torch = _torch()
+        self.n, self.K, self.levels, self.channels = int(n), int(K), int(levels), tuple(int(c) for c in channels)
+        # one stream for the network, the minibatch copies and the solvers it works with
+        self.torch_stream = torch.cuda.Stream()
+        self.stream = self.torch_stream.cuda_stream
+        self.net = gpe2p.Net(levels, list(channels), NCH, NCH, n, n, max_batch, seed=seed, stream=self.stream)
+        self.in_mean = np.zeros(NCH, np.float32)
+        self.in_scale = np.ones(NCH, np.float32)
+        self.out_scale = np.ones(NCH, np.float32)
+        self._apply()
+
+    def _apply(self):
+        self.net.set_normalization(self.in_mean, self.in_scale, self.out_scale, residual=True)
+
+    def set_stats(self, in_mean, in_scale, out_scale):
+        self.in_mean = np.asarray(in_mean, np.float32)
+        self.in_scale = np.asarray(in_scale, np.float32)
+        self.out_scale = np.asarray(out_scale, np.float32)
+        self._apply()
+
+    def forward(self, x, y, batch: int = 1):
+        self.net.forward(x, y, batch)
+
+    def flops(self, batch: int = 1) -> float:
+        return self.net.flops(batch)
+
+    def save(self, path: str, meta: dict | None = None):
+        """FP32 weights and the normalisation in one ``.npz``."""
+        np.savez_compressed(path, params=self.net.get_params(), in_mean=self.in_mean, in_scale=self.in_scale,
+                            out_scale=self.out_scale,
+                            shape=np.array([self.n, self.K, self.levels, *self.channels], np.int64),
+                            meta=np.frombuffer(repr(meta or {}).encode(), np.uint8))
+
+    @classmethod
+    def load(cls, path: str, max_batch: int = 8) -> "Surrogate":
+        z = np.load(path)
+        n, K, levels, *ch = [int(v) for v in z["shape"]]
+        s = cls(n=n, K=K, levels=levels, channels=ch, max_batch=max_batch)
+        s.net.set_params(z["params"])
+        s.set_stats(z["in_mean"], z["in_scale"], z["out_scale"])
+        return s
+
+    def close(self):
+        self.net.close()
+
+
+# ---------------------------------------------------------------------------
+# training data: solver trajectories
+# ---------------------------------------------------------------------------
+
+def generate(cases, snapshots: int, K: int, group: int = 64):
+    """Trajectories of the batched solver: D[t, s] = packed state of case t
+    after s*K steps, s = 0..snapshots, as one CUDA float32 tensor
+    [T, snapshots + 1, n, n, 5] (raw values: mean 0, scale 1).  ``cases`` is
+    a list of (params, fields) of equal size.  Returns (D, seconds of solver
+    time)."""
+    torch = _torch()
+    T = len(cases)
+    n = int(cases[0][0]["nx"])
+    D = torch.empty((T, snapshots + 1, n, n, NCH), dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    for g0 in range(0, T, group):
+        part = cases[g0:g0 + group]
+        b = gpe2p.Batch([p for p, _ in part])
+        try:
+            for k, (_, f) in enumerate(part):
+                b.init_instance(k, f)
+            for s in range(snapshots + 1):
+                if s:
+                    b.advance(K)
+                for k in range(len(part)):
+                    b.pack(k, D[g0 + k, s])
+            torch.cuda.synchronize()
+        finally:
+            b.close()
+    return D, time.perf_counter() - t0
+
+
+def dataset_stats(D, sample: int = 64, seed: int = 0):
+    """Per-channel mean and standard deviation of the states and standard
+    deviation of the K-step increments, from a seeded sample of snapshot
+    pairs read back to the host (configuration of the network's
+    normalisation, not part of the stepped path)."""
+    T, S1 = D.shape[0], D.shape[1]
+    rng = np.random.default_rng(seed)
+    xs, ds = [], []
+    for _ in range(sample):
+        t, s = int(rng.integers(T)), int(rng.integers(S1 - 1))
+        a = D[t, s].cpu().numpy().astype(np.float64)
+        b = D[t, s + 1].cpu().numpy().astype(np.float64)
+        xs.append(a.reshape(-1, NCH))
+        ds.append((b - a).reshape(-1, NCH))
+    X = np.concatenate(xs)
+    dX = np.concatenate(ds)
+    mean = X.mean(axis=0)
+    scale = np.maximum(X.std(axis=0), 1e-6)
+    oscale = np.sqrt((dX ** 2).mean(axis=0))
+    oscale = np.maximum(oscale, 1e-3 * max(float(oscale.max()), 1e-12))
+    return mean.astype(np.float32), scale.astype(np.float32), oscale.astype(np.float32)
+
+
+def train(sur: Surrogate, D, steps: int, batch: int = 8, lr: float = 1e-3, lr_end: float = 5e-5, seed: int = 0,
+          log_every: int = 0):
+    """Adam on the mean squared scaled error of the K-step map over random
+    snapshot pairs of D, with a cosine learning-rate schedule.  Minibatches
+    are gathered by device-to-device copies.  Returns the loss history
+    (every ``log_every`` steps, or the last loss)."""
+    torch = _torch()
+    T, S1, n = D.shape[0], D.shape[1], D.shape[2]
+    x = torch.empty((batch, n, n, NCH), dtype=torch.float32, device="cuda")
+    t = torch.empty_like(x)
+    rng = np.random.default_rng(seed)
+    hist = []
+    torch.cuda.synchronize()
+    for it in range(steps):
+        with torch.cuda.stream(sur.torch_stream):
+            for b in range(batch):
+                ti, si = int(rng.integers(T)), int(rng.integers(S1 - 1))
+                x[b].copy_(D[ti, si])
+                t[b].copy_(D[ti, si + 1])
+        a = lr_end + 0.5 * (lr - lr_end) * (1.0 + math.cos(math.pi * it / max(steps - 1, 1)))
+        want = bool(log_every) and (it % log_every == 0 or it == steps - 1)
+        loss = sur.net.train_step(x, t, batch, a, want_loss=want or it == steps - 1)
+        if want or it == steps - 1:
+            hist.append((it, loss))
+    return hist
+
+
+def one_call_errors(sur: Surrogate, D, pairs):
+    """Relative phi L2 error of one network call and of the persistence map
+    (the state left unchanged) on the snapshot pairs (t, s) of D, computed
+    on the device through a scratch problem and ``gpe2p_state_distance``."""
+    torch = _torch()
+    n = D.shape[2]
+    y = torch.empty((1, n, n, NCH), dtype=torch.float32, device="cuda")
+    prm, _ = inputs.two_drops(0, n=n)
+    out = []
+    torch.cuda.synchronize()
+    with gpe2p.Solver(prm, stream=sur.stream) as s:
+        for t, k in pairs:
+            s.unpack(D[t, k + 1])                  # reference: the solver's state K steps later
+            sur.forward(D[t, k], y, 1)
+            dn = s.distance(y[0])
+            dp = s.distance(D[t, k])
+            out.append((math.sqrt(dn[0] / dn[1]), math.sqrt(dp[0] / dp[1])))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# the controller
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Stats:
+    calls: int = 0
+    net_calls: int = 0
+    solver_calls: int = 0          # K-step solver runs (checks, fallbacks, cooldown)
+    checks: int = 0
+    failures: int = 0
+    max_check_l2: float = 0.0
+    check_l2: list = dataclasses.field(default_factory=list)
+
+
+class Controller:
+    """Advances one 2D problem (a ``gpe2p.Solver`` of the surrogate's size) by
+    K steps per call, with the network and the solver's periodic check."""
+
+    def __init__(self, sur: Surrogate, solver: gpe2p.Solver, check_every: int = 4, tol: float = 2e-2,
+                 cooldown: int = 1, persistence: bool = False):
+        torch = _torch()
+        self.sur, self.s = sur, solver
+        # persistence: the baseline without the network (the state is left unchanged by a call)
+        self.persistence = bool(persistence)
+        self.check_every, self.tol, self.cooldown = int(check_every), float(tol), int(cooldown)
+        n = sur.n
+        self.x = torch.empty((1, n, n, NCH), dtype=torch.float32, device="cuda")
+        self.y = torch.empty_like(self.x)
+        self.ckpt = torch.empty_like(self.x)
+        self.stats = Stats()
+        self._window = 0           # calls since the last check
+        self._off = 0              # windows left on the solver alone
+
+    def _net_call(self):
+        if self.persistence:
+            self.s.pack(self.y[0])
+            return
+        self.s.pack(self.x[0])
+        self.sur.forward(self.x, self.y, 1)
+
+    def call(self):
+        st = self.stats
+        K = self.sur.K
+        st.calls += 1
+        if self._window == 0:
+            self.s.pack(self.ckpt[0])                        # the last verified state
+        self._window += 1
+        last = self._window == self.check_every
+        if self._off > 0:
+            self.s.advance(K)
+            st.solver_calls += 1
+            if last:
+                self._window = 0
+                self._off -= 1
+            return
+        self._net_call()
+        st.net_calls += 1
+        if not last:
+            self.s.unpack(self.y[0])
+            return
+        self._window = 0
+        self.s.advance(K)                                    # the judge, from the same start
+        st.solver_calls += 1
+        st.checks += 1
+        d = self.s.distance(self.y[0])
+        e = math.sqrt(d[0] / max(d[1], 1e-300))
+        st.check_l2.append(e)
+        st.max_check_l2 = max(st.max_check_l2, e)
+        if not (e <= self.tol):
+            st.failures += 1
+            self.s.unpack(self.ckpt[0])                      # back to the last verified state
+            self.s.advance(K * self.check_every)
+            st.solver_calls += self.check_every
+            self._off = self.cooldown
+
+    def run(self, calls: int):
+        for _ in range(calls):
+            self.call()
+        return self.stats
+
+
+# ---------------------------------------------------------------------------
+# evaluation measures (host side, on fields read back)
+# ---------------------------------------------------------------------------
+
+def phi_l2(phi, phi_ref) -> float:
+    """Relative L2 distance of two phase fields."""
+    return float(np.linalg.norm(phi - phi_ref) / max(np.linalg.norm(phi_ref), 1e-300))
+
+
+def interface_error(phi, phi_ref):
+    """Displacement of the phi = 0 interface, in cells: (mean, max).
+
+    With phi_ref of the equilibrium profile tanh(2d/W), the integral of
+    |phi - phi_ref| across an interface moved by delta is 2 delta and the
+    integral of |grad phi_ref| across it is 2, so their ratio over the box is
+    the mean normal displacement.  The max is the largest pointwise
+    |phi - phi_ref| / |grad phi_ref| over the cells with |phi_ref| < 0.5."""
+    gx = 0.5 * (np.roll(phi_ref, -1, 1) - np.roll(phi_ref, 1, 1))
+    gy = 0.5 * (np.roll(phi_ref, -1, 0) - np.roll(phi_ref, 1, 0))
+    g = np.sqrt(gx ** 2 + gy ** 2)
+    diff = np.abs(phi - phi_ref)
+    mean = float(diff.sum() / max(g.sum(), 1e-300))
+    band = np.abs(phi_ref) < 0.5
+    mx = float((diff[band] / np.maximum(g[band], 1e-12)).max()) if band.any() else 0.0
+    return mean, mx
+
+
+def compare_to_solver(sur: Surrogate, prm, fields, calls: int, check_every: int = 4, tol: float = 2e-2,
+                      repeats: int = 1, persistence: bool = False):
+    """Time-to-solution of the controller against the plain solver over
+    ``calls`` * K steps from the same initial state, and the final errors.
+    Both run on the surrogate's stream; times are CUDA-event times of the
+    whole run on that stream (best of ``repeats``), host waits included."""
+    torch = _torch()
+    stream = sur.torch_stream
+    K = sur.K
+    res = {}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), out
+
+    with gpe2p.Solver(prm, stream=sur.stream) as ref:
+        ref.init_fields(fields)
+        ref.advance(1)                                       # graphs built outside the timing
+        best = float("inf")
+        for _ in range(repeats):
+            ref.init_fields(fields)
+            ms, _ = timed(lambda: ref.advance(calls * K))
+            best = min(best, ms)
+        res["solver_ms"] = best
+        phi_ref = ref.read_fields()["phi"]
+    with gpe2p.Solver(prm, stream=sur.stream) as s:
+        s.init_fields(fields)
+        s.advance(1)
+        best, stats = float("inf"), None
+        for _ in range(repeats):
+            s.init_fields(fields)
+            c = Controller(sur, s, check_every=check_every, tol=tol, persistence=persistence)
+            ms, st = timed(lambda: c.run(calls))
+            if ms < best:
+                best, stats = ms, st
+        phi = s.read_fields()["phi"]
+    res["controller_ms"] = best
+    res["speedup"] = res["solver_ms"] / best
+    res["phi_l2"] = phi_l2(phi, phi_ref)
+    res["interface_mean"], res["interface_max"] = interface_error(phi, phi_ref)
+    res["stats"] = dataclasses.asdict(stats)
+    return res
