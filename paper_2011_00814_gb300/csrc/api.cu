@@ -405,15 +405,15 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// a field as a 3D tensor (x, y, z) with padded rows; box = one staged plane
-static bool encode_map(gpe2p_ctx* h, CUtensorMap* m, void* base) {
+// a field as a 3D tensor (x, y, z) with padded rows; box = one staged plane of `rows` rows
+static bool encode_map(gpe2p_ctx* h, CUtensorMap* m, void* base, int rows = SY) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return false;
   const int es = h->esize;
   cuuint64_t dims[3] = {(cuuint64_t)h->prm.nx, (cuuint64_t)h->prm.ny, (cuuint64_t)h->prm.nz};
   cuuint64_t strides[2] = {(cuuint64_t)(h->pitch * es), (cuuint64_t)(h->pitch * h->prm.ny * es)};
   const int bx = es == 4 ? RingGeom<float>::BX : RingGeom<double>::BX;
-  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)SY, 1};
+  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(m, es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base, dims,
                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -424,9 +424,9 @@ static bool encode_map(gpe2p_ctx* h, CUtensorMap* m, void* base) {
 static int build_maps(gpe2p_ctx* h) {
   bool ok = true;
   for (int s = 0; s < 3; ++s) {
-    for (int f = 0; f < 4; ++f) ok = ok && encode_map(h, &h->flow_maps[s].m[f], h->Q[s][f]);
-    ok = ok && encode_map(h, &h->flow_maps[s].m[4], h->phi);
-    ok = ok && encode_map(h, &h->flow_maps[s].m[5], h->mu);
+    for (int f = 0; f < 4; ++f) ok = ok && encode_map(h, &h->flow_maps[s].m[f], h->Q[s][f], FLOW3_SY);
+    ok = ok && encode_map(h, &h->flow_maps[s].m[4], h->phi, FLOW3_SY);
+    ok = ok && encode_map(h, &h->flow_maps[s].m[5], h->mu, FLOW3_SY);
   }
   void* phis[3] = {h->phi, h->phis[0], h->phis[1]};
   void* mus[3] = {h->mu, h->mus, h->mus};

@@ -59,7 +59,7 @@ __device__ __forceinline__ bool ring_acquire(Ring<real, NRAW, RING>& R, const KP
     for (int q = tid; q < ncell; q += NTHR) {
       int lx, ly;
       if (full) { ly = q / SX; lx = q - ly * SX; }
-      else perim_cell(q, lx, ly);
+      else perim_cell<SY>(q, lx, ly);
       const int gi = R.i0 - 1 + lx, gj = R.j0 - 1 + ly;
       if (ghost_plane || gi < 0 || gi >= P.n[0] || gj < 0 || gj >= P.n[1]) {
         const int ci = clampi(gi, -1, P.n[0]), cj = clampi(gj, -1, P.n[1]);

@@ -1,22 +1,31 @@
 // conv_tc.cu -- the surrogate's 3x3 circular convolutions (forward and data
 // gradient) as implicit GEMMs on the 5th-generation tensor cores.
 //
-// One CTA computes a tile of 128 output pixels (16 rows x 8 columns of one
-// image: GEMM rows M = 128) for BN output channels (GEMM columns N).  The K
-// dimension (tap, input channel) is walked in chunks of 16 channels.  For a
-// chunk the CTA stages, with cp.async:
+// A work item is a tile of 128 output pixels (16 rows x 8 columns of one
+// image: GEMM rows M = 128) for a block of BN output channels (GEMM columns
+// N).  Its K dimension (tap, input channel) is walked in chunks of 16
+// channels.  For a chunk the CTA stages, with cp.async:
 //   A: the 18 x 10 input window of the tile (the 1-pixel halo wrapped
 //      periodically), 16 channels, as no-swizzle K-major core matrices
 //      [8-channel half][window row][window column][8 channels];
-//   B: the weights of the 9 taps for those channels, [tap][half][n][8].
+//   B: the weights of the 9 taps for those channels, [tap][half][n][8],
+//      unless the CTA holds all its weights resident in shared memory.
 // The A operand of tap (dy, dx) is the same window read from a start address
 // shifted by (dy, dx) pixels: with 8-pixel tile rows, consecutive 8-row core
 // matrices of M sit one window row (160 bytes) apart for every tap.  One
 // thread issues the 9 tcgen05.mma (kind::f16, BF16 in, FP32 accumulator in
-// tensor memory) of a chunk and commits them to the chunk's mbarrier; the
-// stage is refilled only after that barrier completes.  The epilogue reads
-// the accumulator with tcgen05.ld (one pixel row per thread), adds the bias,
-// applies SiLU and stores BF16 NHWC.
+// tensor memory) of a chunk and commits them to the chunk's mbarrier; a
+// stage is refilled only after that barrier completes.
+//
+// The CTAs are persistent: CTA (x, y) takes the output-channel block y and
+// the tiles x, x + gridDim.x, ...; the chunks of its tiles form one
+// pipelined stream.  The accumulator is double-buffered in tensor memory, so
+// the epilogue of a tile (tcgen05.ld, bias, SiLU, BF16 NHWC stores) runs
+// while the tensor cores work on the next one.
+//
+// The forward input may be read as the nearest 2x upsampling of a tensor of
+// half the resolution (a.up), which fuses the decoder's upsampling into the
+// convolution that follows it.
 //
 // Every wait is bounded (about 2 s of SM clock); on a timeout the CTA records
 // an error in a.err, stops issuing work, waits (bounded) for its MMAs and
@@ -36,21 +45,23 @@ constexpr int TH = 16, TW = 8;              // output tile (M = 128 pixels)
 constexpr int WH = TH + 2, WW = TW + 2;     // input window with the halo
 constexpr int KC = 16;                      // channels per K chunk
 constexpr int NTHR = 128;
+constexpr int S = 4;                        // pipeline stages
+constexpr int PD = 2;                       // chunks loaded ahead
 constexpr int A_BYTES = 2 * WH * WW * 16;   // 5760
-// Room past the staged operands so that every address the descriptors can
-// form stays inside the CTA's shared memory for either reading of the
-// descriptor's two byte-offset fields.
-constexpr int SLACK = 48 * 1024;
+constexpr int HEAD = 1024;                  // barriers and the tensor-memory slot
+constexpr int SMEM_MAX = 200 * 1024;
 
 template <int BN>
 struct Cfg {
-  static constexpr int S = BN >= 128 ? 3 : 4;      // stages
-  static constexpr int PD = S - 2;                 // chunks loaded ahead
-  static constexpr int B_BYTES = 9 * 2 * BN * 16;
-  static constexpr int STAGE = A_BYTES + B_BYTES;
-  static constexpr int SMEM = 1024 + 1024 + S * STAGE + SLACK;   // alignment + barriers + stages + slack
-  static constexpr int TCOLS = BN < 32 ? 32 : BN;  // tensor-memory columns (power of two >= 32)
+  static constexpr int BCHUNK = 9 * 2 * BN * 16;   // weights of one chunk
+  static constexpr int TCOLS = 2 * BN < 32 ? 32 : 2 * BN;   // two accumulators
 };
+
+// shared memory of a launch: streaming B per stage, or resident weights of all chunks
+__host__ __device__ __forceinline__ int smem_bytes(int bn, int nchunks, bool resident) {
+  const int bchunk = 9 * 2 * bn * 16;
+  return 1024 + HEAD + S * (A_BYTES + (resident ? 0 : bchunk)) + (resident ? nchunks * bchunk : 0);
+}
 
 __device__ __forceinline__ int wrapm(int v, int n) {
   int r = v % n;
@@ -80,7 +91,7 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
   return d;                // base offset 0, absolute lbo mode 0, layout 0 (no swizzle)
 }
 
-// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major, M = 128
 template <int N>
 __device__ __forceinline__ uint32_t idesc_bf16() {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
@@ -105,41 +116,55 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t v[8]) {
                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
                : "r"(taddr)
                : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+
+struct TileGeom {
+  int b, y0, x0;
+};
+
+__device__ __forceinline__ TileGeom tile_of(int t, int tiles_x, int tiles_y) {
+  TileGeom g;
+  const int tx = t % tiles_x;
+  t /= tiles_x;
+  g.y0 = (t % tiles_y) * TH;
+  g.b = t / tiles_y;
+  g.x0 = tx * TW;
+  return g;
 }
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + expf(-z)); }
-
-// MODE 0: forward  y = act(conv(x) + bias) (and z = conv(x) + bias);
+// MODE 0: forward  y = act(conv(x) + bias) (and z = conv(x) + bias if a.z);
 // MODE 1: data gradient  dx (+)= conv^T(dz)
 template <int MODE, int BN>
-__global__ void __launch_bounds__(NTHR, 1) conv3_tc_kernel(const ConvArgs a, int tiles_x, int tiles_y) {
+__global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, int tiles_x, int tiles_y, int ntiles,
+                                                         int resident) {
   using C = Cfg<BN>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 512);
-  unsigned char* stages = sm + 1024;
+  unsigned char* stages = sm + HEAD;
+  const int stage_bytes = A_BYTES + (resident ? 0 : C::BCHUNK);
+  unsigned char* wres = stages + S * stage_bytes;   // resident weights [chunk][tap][half][n][8]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  int t = blockIdx.x;
-  const int tx = t % tiles_x;
-  t /= tiles_x;
-  const int ty = t % tiles_y;
-  const int b = t / tiles_y;
-  const int y0 = ty * TH, x0 = tx * TW;
   const int n0 = blockIdx.y * BN;
   const int H = a.H, W = a.W;
-  const int Cin = MODE == 0 ? a.cin : a.cout;     // channels of the K dimension
+  const int Hs = a.up ? H >> 1 : H, Ws = a.up ? W >> 1 : W;   // stored size of the source
+  const int Cin = MODE == 0 ? a.cin : a.cout;                  // channels of the K dimension
   const __nv_bfloat16* src = MODE == 0 ? a.x : a.dz;
   const int lds = MODE == 0 ? a.ldx : a.ldz;
   const int soff = MODE == 0 ? a.xoff : 0;
   const __nv_bfloat16* wsrc = MODE == 0 ? a.wt : a.wd;
-  const int Kw = 9 * Cin;                          // row length of the weight matrix
+  const int Kw = 9 * Cin;                                      // row length of the weight matrix
   const int nchunks = Cin / KC;
+  const int nitems = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int G = nitems * nchunks;                              // chunks of this CTA
 
   if (tid == 0) {
-    for (int s = 0; s < C::S; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
     fence_mbar_init();
     fence_proxy_async_smem();
   }
@@ -154,126 +179,150 @@ __global__ void __launch_bounds__(NTHR, 1) conv3_tc_kernel(const ConvArgs a, int
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  auto load_chunk = [&](int k, int s) {
-    unsigned char* A = stages + s * C::STAGE;
-    unsigned char* B = A + A_BYTES;
-    const int c0 = k * KC;
-    for (int q = tid; q < 2 * WH * WW; q += NTHR) {
-      const int h = q & 1, r = q >> 1;
-      const int wy = r / WW, wx = r - wy * WW;
-      const int yy = wrapm(y0 + wy - 1, H), xx = wrapm(x0 + wx - 1, W);
-      const __nv_bfloat16* g = src + ((size_t)(b * H + yy) * W + xx) * lds + soff + c0 + 8 * h;
-      cp_async16(A + ((h * WH + wy) * WW + wx) * 16, g);
-    }
+  auto load_weights = [&](unsigned char* B, int c0) {
     for (int q = tid; q < 9 * 2 * BN; q += NTHR) {
       const int h = q & 1, r = q >> 1;
       const int tap = r / BN, n = r - tap * BN;
       cp_async16(B + ((tap * 2 + h) * BN + n) * 16, wsrc + (size_t)(n0 + n) * Kw + tap * Cin + c0 + 8 * h);
     }
   };
+  auto load_chunk = [&](int g) {
+    const int item = g / nchunks, k = g - item * nchunks;
+    const TileGeom tg = tile_of(blockIdx.x + item * gridDim.x, tiles_x, tiles_y);
+    unsigned char* A = stages + (g % S) * stage_bytes;
+    const int c0 = k * KC;
+    for (int q = tid; q < 2 * WH * WW; q += NTHR) {
+      const int h = q & 1, r = q >> 1;
+      const int wy = r / WW, wx = r - wy * WW;
+      int yy = wrapm(tg.y0 + wy - 1, H), xx = wrapm(tg.x0 + wx - 1, W);
+      if (a.up) { yy >>= 1; xx >>= 1; }
+      const __nv_bfloat16* gp = src + ((size_t)(tg.b * Hs + yy) * Ws + xx) * lds + soff + c0 + 8 * h;
+      cp_async16(A + ((h * WH + wy) * WW + wx) * 16, gp);
+    }
+    if (!resident) load_weights(A + A_BYTES, c0);
+  };
 
-  for (int k = 0; k < C::PD && k < nchunks; ++k) {
-    load_chunk(k, k % C::S);
+  auto epilogue = [&](int item) {
+    const TileGeom tg = tile_of(blockIdx.x + item * gridDim.x, tiles_x, tiles_y);
+    const uint32_t acc = tmem + (uint32_t)((item & 1) * BN);
+    const int m = warp * 32 + lane;
+    const int y = tg.y0 + m / TW, x = tg.x0 + m % TW;
+    const bool valid = y < H && x < W;
+    const size_t p = ((size_t)tg.b * H + (valid ? y : 0)) * W + (valid ? x : 0);
+#pragma unroll 1
+    for (int j = 0; j < BN; j += 16) {
+      uint32_t v[16];
+      const uint32_t ta = acc + ((uint32_t)(warp * 32) << 16) + (uint32_t)j;
+      tmem_ld8(ta, v);
+      tmem_ld8(ta + 8, v + 8);
+      tmem_wait_ld();
+      if (!valid) continue;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int n = n0 + j + 8 * hh;
+        float f[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) f[e] = __uint_as_float(v[8 * hh + e]);
+        if (MODE == 0) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) f[e] += a.bias[n + e];
+          if (a.z) {
+            uint4 zz;
+            __nv_bfloat162* zp = reinterpret_cast<__nv_bfloat162*>(&zz);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) zp[e] = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
+            *reinterpret_cast<uint4*>(a.z + p * a.cout + n) = zz;
+          }
+          uint4 yv;
+          __nv_bfloat162* yp = reinterpret_cast<__nv_bfloat162*>(&yv);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float u0 = a.act ? silu_f(f[2 * e]) : f[2 * e];
+            const float u1 = a.act ? silu_f(f[2 * e + 1]) : f[2 * e + 1];
+            yp[e] = __floats2bfloat162_rn(u0, u1);
+          }
+          *reinterpret_cast<uint4*>(a.y + p * a.ldy + a.yoff + n) = yv;
+        } else {
+          __nv_bfloat16* dst = a.dx + p * a.lddx + a.dxoff + n;
+          if (a.accumulate) {
+            const uint4 old = *reinterpret_cast<const uint4*>(dst);
+            const __nv_bfloat162* op = reinterpret_cast<const __nv_bfloat162*>(&old);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float2 o = __bfloat1622float2(op[e]);
+              f[2 * e] += o.x;
+              f[2 * e + 1] += o.y;
+            }
+          }
+          uint4 dd;
+          __nv_bfloat162* dp = reinterpret_cast<__nv_bfloat162*>(&dd);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) dp[e] = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
+          *reinterpret_cast<uint4*>(dst) = dd;
+        }
+      }
+    }
+  };
+
+  // prologue: the resident weights join the first group
+  if (resident && G > 0)
+    for (int k = 0; k < nchunks; ++k) load_weights(wres + k * C::BCHUNK, k * KC);
+  for (int g = 0; g < PD; ++g) {
+    if (g < G) load_chunk(g);
     cp_async_commit();
   }
-  for (int k = nchunks; k < C::PD; ++k) cp_async_commit();
 
   bool bad = false;
-  for (int k = 0; k < nchunks; ++k) {
-    const int kn = k + C::PD;
-    if (kn < nchunks) {
-      const int sn = kn % C::S;
+  for (int g = 0; g < G; ++g) {
+    const int gn = g + PD;
+    if (gn < G) {
       bool to = false;
-      if (kn >= C::S) to = !mbar_wait_bounded(&bar[sn], (uint32_t)(((kn - C::S) / C::S) & 1), WAIT_CYCLES);
+      if (gn >= S) to = !mbar_wait_bounded(&bar[gn % S], (uint32_t)(((gn - S) / S) & 1), WAIT_CYCLES);
       if (__syncthreads_or(to)) { bad = true; break; }
-      load_chunk(kn, sn);
+      load_chunk(gn);
     }
     cp_async_commit();
-    cp_async_wait<C::PD>();
+    cp_async_wait<PD>();
     fence_proxy_async_smem();
     __syncthreads();
+    const int item = g / nchunks, k = g - item * nchunks;
     if (tid == 0) {
       tc_fence_after();
-      const int s = k % C::S;
-      const uint32_t Aa = smem_u32(stages + s * C::STAGE);
-      const uint32_t Ba = Aa + A_BYTES;
+      const int s = g % S;
+      const uint32_t Aa = smem_u32(stages + s * stage_bytes);
+      const uint32_t Ba = resident ? smem_u32(wres + k * C::BCHUNK) : Aa + A_BYTES;
+      const uint32_t acc = tmem + (uint32_t)((item & 1) * BN);
 #pragma unroll
       for (int tap = 0; tap < 9; ++tap) {
         int dy = tap / 3 - 1, dx = tap % 3 - 1;
         if (MODE == 1) { dy = -dy; dx = -dx; }
         const uint64_t ad = sdesc(Aa + (uint32_t)(((dy + 1) * WW + (dx + 1)) * 16), WH * WW * 16, WW * 16);
         const uint64_t bd = sdesc(Ba + (uint32_t)(tap * 2 * BN * 16), BN * 16, 128);
-        mma_tc(tmem, ad, bd, idesc_bf16<BN>(), (k > 0 || tap > 0) ? 1u : 0u);
+        mma_tc(acc, ad, bd, idesc_bf16<BN>(), (k > 0 || tap > 0) ? 1u : 0u);
       }
       mma_commit(&bar[s]);
+    }
+    if (k == 0 && item > 0) {
+      // the previous tile is fully issued: its epilogue overlaps this tile's MMAs
+      const bool ok = mbar_wait_bounded(&bar[(g - 1) % S], (uint32_t)(((g - 1) / S) & 1), WAIT_CYCLES);
+      if (__syncthreads_or(!ok)) { bad = true; break; }
+      tc_fence_after();
+      epilogue(item - 1);
+      tc_fence_before();
     }
   }
   cp_async_wait<0>();
 
-  // the last committed chunk covers every MMA issued before it
-  bool done = false;
-  if (nchunks > 0) {
-    const int kl = bad ? -1 : nchunks - 1;
-    if (kl >= 0) done = mbar_wait_bounded(&bar[kl % C::S], (uint32_t)((kl / C::S) & 1), WAIT_CYCLES);
-  }
+  bool done = G == 0;
+  if (!bad && G > 0) done = mbar_wait_bounded(&bar[(G - 1) % S], (uint32_t)(((G - 1) / S) & 1), WAIT_CYCLES);
   if (__syncthreads_or(!done)) {
     if (tid == 0 && a.err) atomicExch(a.err, 1);
-    // drain: give the MMAs issued so far a bounded time to finish before the memory is freed
+    // give the MMAs issued so far a bounded time to finish before the memory is freed
     const long long t0 = clock64();
     while (clock64() - t0 < 1000000) {}
-  } else {
+  } else if (G > 0) {
     tc_fence_after();
-    const int m = warp * 32 + lane;
-    const int y = y0 + m / TW, x = x0 + m % TW;
-    const bool valid = y < H && x < W;
-    const size_t p = ((size_t)b * H + (valid ? y : 0)) * W + (valid ? x : 0);
-#pragma unroll 1
-    for (int j = 0; j < BN; j += 8) {
-      uint32_t v[8];
-      tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j, v);
-      if (!valid) continue;
-      const int n = n0 + j;
-      float f[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) f[e] = __uint_as_float(v[e]);
-      if (MODE == 0) {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) f[e] += a.bias[n + e];
-        if (a.z) {
-          uint4 zz;
-          __nv_bfloat162* zp = reinterpret_cast<__nv_bfloat162*>(&zz);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) zp[e] = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
-          *reinterpret_cast<uint4*>(a.z + p * a.cout + n) = zz;
-        }
-        uint4 yy;
-        __nv_bfloat162* yp = reinterpret_cast<__nv_bfloat162*>(&yy);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float u0 = a.act ? silu_f(f[2 * e]) : f[2 * e];
-          const float u1 = a.act ? silu_f(f[2 * e + 1]) : f[2 * e + 1];
-          yp[e] = __floats2bfloat162_rn(u0, u1);
-        }
-        *reinterpret_cast<uint4*>(a.y + p * a.ldy + a.yoff + n) = yy;
-      } else {
-        __nv_bfloat16* dst = a.dx + p * a.lddx + a.dxoff + n;
-        if (a.accumulate) {
-          const uint4 old = *reinterpret_cast<const uint4*>(dst);
-          const __nv_bfloat162* op = reinterpret_cast<const __nv_bfloat162*>(&old);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float2 o = __bfloat1622float2(op[e]);
-            f[2 * e] += o.x;
-            f[2 * e + 1] += o.y;
-          }
-        }
-        uint4 dd;
-        __nv_bfloat162* dp = reinterpret_cast<__nv_bfloat162*>(&dd);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) dp[e] = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
-        *reinterpret_cast<uint4*>(dst) = dd;
-      }
-    }
+    epilogue(nitems - 1);
   }
   tc_fence_before();
   __syncthreads();
@@ -283,16 +332,35 @@ __global__ void __launch_bounds__(NTHR, 1) conv3_tc_kernel(const ConvArgs a, int
 }
 
 template <int MODE, int BN>
-cudaError_t launch_tc(const ConvArgs& a, int tiles_x, int tiles_y, long long tiles, int nout, cudaStream_t s) {
-  static bool attr = false;
+cudaError_t launch_tc(const ConvArgs& a, int tiles_x, int tiles_y, int ntiles, int nout, cudaStream_t s) {
+  static int attr_set = 0;
+  static int occ_res = 0, occ_str = 0;
   auto k = conv3_tc_kernel<MODE, BN>;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<BN>::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
+  cudaError_t e;
+  if (!attr_set) {
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_MAX)) != cudaSuccess) return e;
+    attr_set = 1;
   }
-  dim3 grid((unsigned)tiles, (unsigned)(nout / BN));
-  k<<<grid, NTHR, Cfg<BN>::SMEM, s>>>(a, tiles_x, tiles_y);
+  const int nch = (MODE == 0 ? a.cin : a.cout) / KC;
+  const bool resident = smem_bytes(BN, nch, true) <= SMEM_MAX;
+  const int smem = smem_bytes(BN, nch, resident);
+  int occ = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, NTHR, smem)) != cudaSuccess) return e;
+  (void)occ_res;
+  (void)occ_str;
+  if (occ < 1) occ = 1;
+  // tensor memory: at most 512 columns per SM
+  const int tc_occ = 512 / Cfg<BN>::TCOLS;
+  if (occ > tc_occ) occ = tc_occ;
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int nblk_n = nout / BN;
+  long long gx = ((long long)occ * nsm + nblk_n - 1) / nblk_n;
+  if (gx > ntiles) gx = ntiles;
+  if (gx < 1) gx = 1;
+  dim3 grid((unsigned)gx, (unsigned)nblk_n);
+  k<<<grid, NTHR, smem, s>>>(a, tiles_x, tiles_y, ntiles, resident ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -301,14 +369,15 @@ cudaError_t conv3_tc(const ConvArgs& a, cudaStream_t s) {
   const int nout = MODE == 0 ? a.cout : a.cin;
   const int tiles_x = (a.W + TW - 1) / TW, tiles_y = (a.H + TH - 1) / TH;
   const long long tiles = (long long)a.B * tiles_x * tiles_y;
+  if (tiles > (1LL << 30)) return cudaErrorInvalidValue;
   int bn = 128;
   while (bn > 16 && nout % bn) bn >>= 1;
   while (bn > 32 && tiles * (nout / bn) < 2 * 152) bn >>= 1;
   switch (bn) {
-    case 128: return launch_tc<MODE, 128>(a, tiles_x, tiles_y, tiles, nout, s);
-    case 64: return launch_tc<MODE, 64>(a, tiles_x, tiles_y, tiles, nout, s);
-    case 32: return launch_tc<MODE, 32>(a, tiles_x, tiles_y, tiles, nout, s);
-    default: return launch_tc<MODE, 16>(a, tiles_x, tiles_y, tiles, nout, s);
+    case 128: return launch_tc<MODE, 128>(a, tiles_x, tiles_y, (int)tiles, nout, s);
+    case 64: return launch_tc<MODE, 64>(a, tiles_x, tiles_y, (int)tiles, nout, s);
+    case 32: return launch_tc<MODE, 32>(a, tiles_x, tiles_y, (int)tiles, nout, s);
+    default: return launch_tc<MODE, 16>(a, tiles_x, tiles_y, (int)tiles, nout, s);
   }
 }
 
@@ -317,8 +386,11 @@ cudaError_t conv3_tc(const ConvArgs& a, cudaStream_t s) {
 bool conv_tc_supported(const ConvArgs& a, int mode) {
   const int kin = mode == 0 ? a.cin : a.cout, nout = mode == 0 ? a.cout : a.cin;
   if (a.taps != 9 || kin % KC || nout % 16 || a.H < 1 || a.W < 1) return false;
+  if (mode == 0 && a.up && (a.H % 2 || a.W % 2)) return false;
+  if (mode == 1 && a.up) return false;
   const int ld = mode == 0 ? a.ldx : a.ldz, off = mode == 0 ? a.xoff : 0;
   const int ldo = mode == 0 ? a.ldy : a.lddx, offo = mode == 0 ? a.yoff : a.dxoff;
+  if (smem_bytes(16, kin / KC, false) > SMEM_MAX) return false;
   return ld % 8 == 0 && off % 8 == 0 && ldo % 8 == 0 && offo % 8 == 0;
 }
 

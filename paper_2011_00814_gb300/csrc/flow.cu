@@ -8,18 +8,11 @@
 // One thread per cell computes the pressure rate at the cell centre and the
 // rate of each velocity component on the cell's low faces (the operators are
 // in flow_ops.cuh).  2D blocks stage one tile with its halo; 3D blocks march
-// along z fed by the TMA plane ring of ring3d.cuh.
+// along z fed by the TMA plane ring of ring3d.cuh, two cells per thread.
 #include "flow_ops.cuh"
 #include "gpe2p_dev.cuh"
 #include "gpe2p_launch.h"
 #include "ring3d.cuh"
-
-// Whether the 3D flow stage precomputes the divergence and the edge
-// viscosities per staged cell (fewer instructions per cell, but four more
-// shared-memory planes per derived slot, which costs occupancy).
-#ifndef GPE2P_FLOW_PRECOMPUTE
-#define GPE2P_FLOW_PRECOMPUTE 0
-#endif
 
 namespace gpe2p {
 
@@ -34,150 +27,124 @@ __global__ void __launch_bounds__(NTHR) flow2d_kernel(const KParams<real> P, con
 // 3D: the same stage fed by the TMA plane ring of ring3d.cuh
 // ---------------------------------------------------------------------------
 
-// raw (copied) fields of the ring and the derived planes rho, eta, nu, the
-// divergence and the three edge viscosities
+// fields staged per plane; rho, eta and nu are formed from phi where they are read
 enum { R_P = 0, R_U = 1, R_V = 2, R_W = 3, R_PHI = 4, R_MU = 5, NRAW_FLOW = 6 };
-enum { D_RHO = 0, D_ETA = 1, D_NU = 2, D_DIV = 3, D_EXY = 4, D_EXZ = 5, D_EYZ = 6 };
-constexpr int NDER_FLOW = GPE2P_FLOW_PRECOMPUTE ? 7 : 3;
 
 template <typename real, int PAVG_>
 struct RingTile {
   static constexpr int PAVG = PAVG_;
-  using G = RingGeom<real>;
-  const real* sm;  // the block's shared memory
-  int r[3];        // index of the thread's cell in raw field 0 of planes k-1, k, k+1
-  int d[3];        // index of the thread's cell in derived field 0 of planes k-1, k, k+1
+  using G = RingGeom<real, FLOW3_SY>;
+  const real* sm;           // the block's shared memory
+  const KParams<real>* P;
+  int r[3];                 // index of the thread's cell in raw field 0 of planes k-1, k, k+1
+  __device__ __forceinline__ real raw(int f, int o, int dz) const { return sm[r[dz + 1] + f * G::PE + o]; }
   __device__ __forceinline__ real operator()(int f, int dx, int dy, int dz) const {
     const int o = dy * G::BX + dx;
     switch (f) {
-      case F_P: return sm[r[dz + 1] + R_P * G::PE + o];
-      case F_U: return sm[r[dz + 1] + R_U * G::PE + o];
-      case F_V: return sm[r[dz + 1] + R_V * G::PE + o];
-      case F_W: return sm[r[dz + 1] + R_W * G::PE + o];
-      case F_PHI: return sm[r[dz + 1] + R_PHI * G::PE + o];
-      case F_MU: return sm[r[dz + 1] + R_MU * G::PE + o];
-      case F_RHO: return sm[d[dz + 1] + D_RHO * G::PE + o];
-      case F_ETA: return sm[d[dz + 1] + D_ETA * G::PE + o];
-      case F_NU: return sm[d[dz + 1] + D_NU * G::PE + o];
-      case F_DIV: return sm[d[dz + 1] + D_DIV * G::PE + o];
-      case F_EXY: return sm[d[dz + 1] + D_EXY * G::PE + o];
-      case F_EXZ: return sm[d[dz + 1] + D_EXZ * G::PE + o];
-      default: return sm[d[dz + 1] + D_EYZ * G::PE + o];
+      case F_P: return raw(R_P, o, dz);
+      case F_U: return raw(R_U, o, dz);
+      case F_V: return raw(R_V, o, dz);
+      case F_W: return raw(R_W, o, dz);
+      case F_PHI: return raw(R_PHI, o, dz);
+      case F_MU: return raw(R_MU, o, dz);
+      case F_RHO: return rho_of(*P, raw(R_PHI, o, dz));
+      case F_ETA: return eta_of(*P, raw(R_PHI, o, dz));
+      default: {  // F_NU
+        const real phi = raw(R_PHI, o, dz);
+        return fdiv(eta_of(*P, phi), rho_of(*P, phi));
+      }
     }
   }
 };
-template <typename real, int PAVG_>
-struct HasPre<RingTile<real, PAVG_>> {
-  static constexpr bool value = GPE2P_FLOW_PRECOMPUTE != 0;
-};
 
+// One block: a TX x FLOW3_TY column of cells over the planes [kbeg, kend);
+// thread (tx, ty) computes the cells (i0 + tx, j0 + 2 ty + r), r = 0, 1.  The
+// two cells share most of their stencil, so the loads and sub-expressions
+// they have in common are formed once.
 template <typename real, int MODE, int RING, int PAVG>
 __global__ void __launch_bounds__(NTHR, 2) flow3d_kernel(const __grid_constant__ Maps<NRAW_FLOW> maps,
-                                                      const KParams<real> P, const FlowArgs<real> A,
-                                                      const int kchunk, int* err) {
-  using G = RingGeom<real>;
+                                                      const __grid_constant__ KParams<real> P,
+                                                      const FlowArgs<real> A, const int kchunk, int* err) {
+  constexpr int SYv = FLOW3_SY;
+  using G = RingGeom<real, SYv>;
   extern __shared__ __align__(128) unsigned char smraw[];
-  Ring<real, NRAW_FLOW, RING> R;
+  Ring<real, NRAW_FLOW, RING, SYv> R;
   unsigned char* sbase = smem_base128(smraw);
   R.bar = reinterpret_cast<uint64_t*>(sbase);
   R.raw = reinterpret_cast<real*>(sbase + 128);
-  real* der = R.raw + (size_t)RING * NRAW_FLOW * G::PE;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * FLOW3_TY;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(kbeg + kchunk, P.n[2]);
   const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
-  const bool edge_tile = i0 == 0 || i0 + TX + 1 > nx || j0 == 0 || j0 + TY + 1 > ny;
-  const int i = i0 + tx, j = j0 + ty;
-  const bool active = i < nx && j < ny;
-  auto dplane = [&](int kk) { return der + (size_t)((unsigned)(kk + 4) & 3u) * NDER_FLOW * G::PE; };
+  const bool edge_tile = i0 == 0 || i0 + TX + 1 > nx || j0 == 0 || j0 + FLOW3_TY + 1 > ny;
+  const bool ragged = i0 + TX > nx || j0 + FLOW3_TY > ny;
+  const int i = i0 + tx, ja = j0 + 2 * ty;
+  const bool act[2] = {i < nx && ja < ny, i < nx && ja + 1 < ny};
 
   R.start(P, maps.m, kbeg, kend, i0, j0);
 
-  // wait for plane kk; overwrite its out-of-domain cells; derive rho, eta, nu
-  // of plane kk, then the divergence of plane kk - 1 and the edge viscosities
-  // of plane kk
+  // wait for plane kk and overwrite its out-of-domain cells (all cells of a
+  // ghost plane or of a tile overhanging the domain end, else the perimeter
+  // of a tile on the boundary)
   auto acquire = [&](int kk, bool refill) -> bool {
     if (!R.wait(kk)) return false;
     if (refill && tid == 0) R.refill(P, maps.m, kk);
     const bool ghost_plane = kk < 0 || kk >= nz;
+    if (!ghost_plane && !edge_tile) return true;
     real* pl[NRAW_FLOW];
 #pragma unroll
     for (int f = 0; f < NRAW_FLOW; ++f) pl[f] = R.plane(kk, f);
-    real* dk = dplane(kk);
-    for (int idx = tid; idx < SX * SY; idx += NTHR) {
-      const int ly = idx / SX, lx = idx - ly * SX;
-      const int e = G::at(lx, ly);
-      if (ghost_plane || edge_tile) {
-        const int gi = i0 - 1 + lx, gj = j0 - 1 + ly;
-        if (ghost_plane || gi < 0 || gi >= nx || gj < 0 || gj >= ny) {
-          const int ci = clampi(gi, -1, nx), cj = clampi(gj, -1, ny);
-          pl[R_P][e] = ld_cen(A.q[0], P, ci, cj, kk);
-          pl[R_U][e] = ld_face<0>(A.q[1], P, ci, cj, kk);
-          pl[R_V][e] = ld_face<1>(A.q[2], P, ci, cj, kk);
-          pl[R_W][e] = ld_face<2>(A.q[3], P, ci, cj, kk);
-          pl[R_PHI][e] = ld_cen(A.phi, P, ci, cj, kk);
-          pl[R_MU][e] = ld_cen(A.mu, P, ci, cj, kk);
-        }
-      }
-      const real phi = pl[R_PHI][e];
-      const real rho = rho_of(P, phi), eta = eta_of(P, phi);
-      dk[D_RHO * G::PE + e] = rho;
-      dk[D_ETA * G::PE + e] = eta;
-      dk[D_NU * G::PE + e] = fdiv(eta, rho);
-    }
-    if (ghost_plane || edge_tile) fence_proxy_async_smem();
-    if (!GPE2P_FLOW_PRECOMPUTE) return true;
-    __syncthreads();
-    const bool have_prev = kk > R.first;
-    const real* um = R.plane(kk - 1, R_U);
-    const real* vm = R.plane(kk - 1, R_V);
-    const real* wm = R.plane(kk - 1, R_W);
-    const real* wk = pl[R_W];
-    real* dm = dplane(kk - 1);
-    const real* em = dplane(kk - 1) + D_ETA * G::PE;
-    const real* ek = dk + D_ETA * G::PE;
-    for (int idx = tid; idx < SX * SY; idx += NTHR) {
-      const int ly = idx / SX, lx = idx - ly * SX;
-      const int e = G::at(lx, ly);
-      if (have_prev && lx < SX - 1 && ly < SY - 1)
-        dm[D_DIV * G::PE + e] =
-            ((um[e + 1] - um[e]) + (vm[e + G::BX] - vm[e]) + (wk[e] - wm[e])) * P.inv_dx;
-      if (lx > 0 && ly > 0) {
-        dk[D_EXY * G::PE + e] = ((ek[e] + ek[e - 1]) + (ek[e - G::BX] + ek[e - 1 - G::BX])) * real(0.25);
-        if (have_prev) {
-          dk[D_EXZ * G::PE + e] = ((ek[e] + ek[e - 1]) + (em[e] + em[e - 1])) * real(0.25);
-          dk[D_EYZ * G::PE + e] = ((ek[e] + ek[e - G::BX]) + (em[e] + em[e - G::BX])) * real(0.25);
-        }
+    const bool full = ghost_plane || ragged;
+    const int ncell = full ? SX * SYv : perim<SYv>();
+    for (int q = tid; q < ncell; q += NTHR) {
+      int lx, ly;
+      if (full) { ly = q / SX; lx = q - ly * SX; }
+      else perim_cell<SYv>(q, lx, ly);
+      const int gi = i0 - 1 + lx, gj = j0 - 1 + ly;
+      if (ghost_plane || gi < 0 || gi >= nx || gj < 0 || gj >= ny) {
+        const int e = G::at(lx, ly);
+        const int ci = clampi(gi, -1, nx), cj = clampi(gj, -1, ny);
+        pl[R_P][e] = ld_cen(A.q[0], P, ci, cj, kk);
+        pl[R_U][e] = ld_face<0>(A.q[1], P, ci, cj, kk);
+        pl[R_V][e] = ld_face<1>(A.q[2], P, ci, cj, kk);
+        pl[R_W][e] = ld_face<2>(A.q[3], P, ci, cj, kk);
+        pl[R_PHI][e] = ld_cen(A.phi, P, ci, cj, kk);
+        pl[R_MU][e] = ld_cen(A.mu, P, ci, cj, kk);
       }
     }
+    fence_proxy_async_smem();
     return true;
   };
 
   if (!acquire(kbeg - 1, false)) { R.fail(err, kbeg - 1); return; }
   if (!acquire(kbeg, false)) { R.fail(err, kbeg); return; }
   const real* smr = reinterpret_cast<const real*>(smraw);
-  const int raw0 = (int)(R.raw - smr), der0 = (int)(der - smr);
-  const int cell = G::at(tx + 1, ty + 1);
-  long long id = lin(P, i, j, kbeg);
+  const int raw0 = (int)(R.raw - smr);
+  const int cell0 = G::at(tx + 1, 2 * ty + 1);
+  long long id = lin(P, i, ja, kbeg);
   for (int k = kbeg; k < kend; ++k, id += P.sz) {
-    real q0v[4];
-    if (MODE == 2 && active) {
+    real q0v[2][4];
+    if (MODE == 2) {
 #pragma unroll
-      for (int f = 0; f < 4; ++f) q0v[f] = A.q0[f][id];
+      for (int r = 0; r < 2; ++r)
+        if (act[r]) {
+#pragma unroll
+          for (int f = 0; f < 4; ++f) q0v[r][f] = A.q0[f][id + r * P.sy];
+        }
     }
     if (!acquire(k + 1, true)) { R.fail(err, k + 1); return; }
     __syncthreads();
-    if (active) {
+    using Ops = FlowOps<real, 3, RingTile<real, PAVG>>;
+    real out[2][4];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
       RingTile<real, PAVG> S;
       S.sm = smr;
+      S.P = &P;
 #pragma unroll
-      for (int dz = -1; dz <= 1; ++dz) {
-        S.r[dz + 1] = raw0 + R.slot(k + dz) * NRAW_FLOW * G::PE + cell;
-        S.d[dz + 1] = der0 + (int)((unsigned)(k + dz + 4) & 3u) * NDER_FLOW * G::PE + cell;
-      }
-      using Ops = FlowOps<real, 3, RingTile<real, PAVG>>;
-      const real D0 = Ops::div(S, P, 0, 0, 0);
+      for (int dz = -1; dz <= 1; ++dz) S.r[dz + 1] = raw0 + R.slot(k + dz) * NRAW_FLOW * G::PE + cell0 + r * G::BX;
+      const real D0 = Ops::divsum(S, 0, 0, 0);
       real L[4];
       L[0] = Ops::rate_p(S, P, D0);
       L[1] = Ops::template rate_vel<0>(S, P, D0);
@@ -185,22 +152,27 @@ __global__ void __launch_bounds__(NTHR, 2) flow3d_kernel(const __grid_constant__
       L[3] = Ops::template rate_vel<2>(S, P, D0);
       // faces on a wall are never updated
       if (P.bc[0] != BC_PERIODIC && i == 0) L[1] = real(0);
-      if (P.bc[1] != BC_PERIODIC && j == 0) L[2] = real(0);
+      if (P.bc[1] != BC_PERIODIC && ja + r == 0) L[2] = real(0);
       if (P.bc[2] != BC_PERIODIC && k == 0) L[3] = real(0);
       const int F[4] = {F_P, F_U, F_V, F_W};
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
-        real o;
         if (MODE == 0) {
-          o = L[f];
+          out[r][f] = L[f];
         } else {
           const real q = S(F[f], 0, 0, 0);
-          if (MODE == 1) o = q + P.dt * L[f];
-          else o = A.a * q0v[f] + A.b * (q + P.dt * L[f]);
+          if (MODE == 1) out[r][f] = q + P.dt * L[f];
+          else out[r][f] = A.a * q0v[r][f] + A.b * (q + P.dt * L[f]);
         }
-        A.out[f][id] = o;
       }
     }
+    // stores after both cells, so that nothing separates their shared loads
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+      if (act[r]) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) A.out[f][id + r * P.sy] = out[r][f];
+      }
   }
 }
 
@@ -223,7 +195,8 @@ cudaError_t launch_flow_stage(const KParams<real>& P, const FlowArgs<real>& A, i
   cudaError_t e;
   if constexpr (DIM == 3) {
     constexpr int RING = flow_ring<real>();
-    const size_t sm = ring_smem_bytes<real, NRAW_FLOW, NDER_FLOW, RING>();
+    const size_t sm = ring_smem_bytes<real, NRAW_FLOW, 0, RING, FLOW3_SY>();
+    grd.y = (P.n[1] + FLOW3_TY - 1) / FLOW3_TY;
 #define GPE2P_FLOW3_CASE(M)                                                                                 \
   if (P.pavg) {                                                                                             \
     e = cudaFuncSetAttribute(flow3d_kernel<real, M, RING, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \

@@ -15,132 +15,109 @@
 namespace gpe2p {
 
 enum { F_P = 0, F_U = 1, F_V = 2, F_W = 3, F_PHI = 4, F_RHO = 5, F_ETA = 6, F_NU = 7, F_MU = 8, F_N = 9 };
-// precomputed per-cell quantities offered by the 3D ring accessor: the
-// divergence of the cell and the viscosity of the cell's low edge in each
-// coordinate plane (mean of eta over the four cells around the edge)
-enum { F_DIV = 9, F_EXY = 10, F_EXZ = 11, F_EYZ = 12 };
 
-// accessors that stage only the raw fields (the 2D plane kernel)
-template <typename T>
-struct HasPre {
-  static constexpr bool value = false;
-};
-
+// The rates below gather every term with its grid factor applied once:
+// sums of the four edge viscosities, face velocities and transverse
+// pressures are formed unnormalised and scaled together at the end.
 template <typename real, int DIM, typename T>
 struct FlowOps {
-  static constexpr bool PRE = HasPre<T>::value;
-
-  // velocity divergence of the cell at offset (ox,oy,oz), Eq. div-v-discretization
-  __device__ __forceinline__ static real div(const T& S, const KParams<real>& P, int ox, int oy, int oz) {
-    if constexpr (PRE) {
-      return S(F_DIV, ox, oy, oz);
-    } else {
-      real d = (S(F_U, ox + 1, oy, oz) - S(F_U, ox, oy, oz)) + (S(F_V, ox, oy + 1, oz) - S(F_V, ox, oy, oz));
-      if (DIM == 3) d += S(F_W, ox, oy, oz + 1) - S(F_W, ox, oy, oz);
-      return d * P.inv_dx;
-    }
+  // velocity divergence of the cell at offset (ox,oy,oz) times dx, Eq. div-v-discretization
+  __device__ __forceinline__ static real divsum(const T& S, int ox, int oy, int oz) {
+    real d = (S(F_U, ox + 1, oy, oz) - S(F_U, ox, oy, oz)) + (S(F_V, ox, oy + 1, oz) - S(F_V, ox, oy, oz));
+    if (DIM == 3) d += S(F_W, ox, oy, oz + 1) - S(F_W, ox, oy, oz);
+    return d;
   }
 
-  // eta averaged over the four cells around the edge shared by the faces of
-  // components C and t (Eq. u-stress-discretization, eta bar at i, j+-1/2):
-  // the edge on the +t side (etp) or on the -t side (etm) of the C face
+  // 4 x (eta averaged over the four cells around the edge shared by the faces
+  // of components C and t), Eq. u-stress-discretization (eta bar at i, j+-1/2):
+  // the edge on the +t side (e4p) and on the -t side (e4m) of the C face
   template <int C>
-  __device__ __forceinline__ static void edge_eta(const T& S, int t, real& etp, real& etm) {
+  __device__ __forceinline__ static void edge_eta4(const T& S, int t, real& e4p, real& e4m) {
     const int cx = C == 0, cy = C == 1, cz = C == 2;
     const int tx = t == 0, ty = t == 1, tz = t == 2;
-    if constexpr (PRE) {
-      const int a = C < t ? C : t, b = C < t ? t : C;
-      const int FE = (a == 0 && b == 1) ? F_EXY : ((a == 0 && b == 2) ? F_EXZ : F_EYZ);
-      etp = S(FE, tx, ty, tz);
-      etm = S(FE, 0, 0, 0);
-    } else {
-      etp = (S(F_ETA, 0, 0, 0) + S(F_ETA, tx, ty, tz) + S(F_ETA, -cx, -cy, -cz) +
-             S(F_ETA, tx - cx, ty - cy, tz - cz)) *
-            real(0.25);
-      etm = (S(F_ETA, 0, 0, 0) + S(F_ETA, -tx, -ty, -tz) + S(F_ETA, -cx, -cy, -cz) +
-             S(F_ETA, -tx - cx, -ty - cy, -tz - cz)) *
-            real(0.25);
-    }
+    e4p = (S(F_ETA, 0, 0, 0) + S(F_ETA, tx, ty, tz)) + (S(F_ETA, -cx, -cy, -cz) + S(F_ETA, tx - cx, ty - cy, tz - cz));
+    e4m = (S(F_ETA, 0, 0, 0) + S(F_ETA, -tx, -ty, -tz)) +
+          (S(F_ETA, -cx, -cy, -cz) + S(F_ETA, -tx - cx, -ty - cy, -tz - cz));
   }
 
-  // averaged pressure of the cell at offset o for the gradient along C
-  // (Eq. gradp-u-discretization in 2D, Eq. gradp-u-p-ave-3d in 3D)
+  // whether the pressure gradient averages transversally (Eq. gradp-u-p-ave-3d)
+  __device__ __forceinline__ static bool averaged(const KParams<real>& P) {
+    if constexpr (T::PAVG == 0) return false;
+    else if constexpr (T::PAVG > 0) return true;
+    else return P.pavg != 0;
+  }
+
+  // the averaged pressure of the cell at offset o for the gradient along C,
+  // unnormalised: 6 pbar in 2D (Eq. gradp-u-discretization), 36 pbar in 3D
   template <int C>
-  __device__ __forceinline__ static real pbar(const T& S, const KParams<real>& P, int ox, int oy, int oz) {
-    if constexpr (T::PAVG == 0) {
-      return S(F_P, ox, oy, oz);
-    } else if constexpr (T::PAVG < 0) {
-      if (!P.pavg) return S(F_P, ox, oy, oz);
-    }
+  __device__ __forceinline__ static real psum(const T& S, int ox, int oy, int oz) {
     if (DIM == 2) {
       constexpr int tx = C == 1, ty = C == 0;
-      return (real(4) * S(F_P, ox, oy, oz) + S(F_P, ox + tx, oy + ty, oz) + S(F_P, ox - tx, oy - ty, oz)) *
-             real(1.0 / 6.0);
+      return real(4) * S(F_P, ox, oy, oz) + (S(F_P, ox + tx, oy + ty, oz) + S(F_P, ox - tx, oy - ty, oz));
     } else {
       constexpr int T1 = (C + 1) % 3, T2 = (C + 2) % 3;
       constexpr int ax = T1 == 0, ay = T1 == 1, az = T1 == 2;  // unit vector t1
       constexpr int bx = T2 == 0, by = T2 == 1, bz = T2 == 2;  // unit vector t2
-      const real s4 = S(F_P, ox + ax, oy + ay, oz + az) + S(F_P, ox - ax, oy - ay, oz - az) +
-                      S(F_P, ox + bx, oy + by, oz + bz) + S(F_P, ox - bx, oy - by, oz - bz);
-      const real s1 = S(F_P, ox + ax + bx, oy + ay + by, oz + az + bz) +
-                      S(F_P, ox - ax - bx, oy - ay - by, oz - az - bz) +
-                      S(F_P, ox - ax + bx, oy - ay + by, oz - az + bz) +
-                      S(F_P, ox + ax - bx, oy + ay - by, oz + az - bz);
-      return (real(16) * S(F_P, ox, oy, oz) + real(4) * s4 + s1) * real(1.0 / 36.0);
+      const real s4 = (S(F_P, ox + ax, oy + ay, oz + az) + S(F_P, ox - ax, oy - ay, oz - az)) +
+                      (S(F_P, ox + bx, oy + by, oz + bz) + S(F_P, ox - bx, oy - by, oz - bz));
+      const real s1 = (S(F_P, ox + ax + bx, oy + ay + by, oz + az + bz) +
+                       S(F_P, ox - ax - bx, oy - ay - by, oz - az - bz)) +
+                      (S(F_P, ox - ax + bx, oy - ay + by, oz - az + bz) +
+                       S(F_P, ox + ax - bx, oy + ay - by, oz + az - bz));
+      return real(16) * S(F_P, ox, oy, oz) + (real(4) * s4 + s1);
     }
   }
 
-  // pressure rate at the cell centre: -rho c_s^2 div u + div(nu grad p)
-  __device__ __forceinline__ static real rate_p(const T& S, const KParams<real>& P, real D0) {
+  // pressure rate at the cell centre: -rho c_s^2 div u + div(nu grad p); d0 = dx div u
+  __device__ __forceinline__ static real rate_p(const T& S, const KParams<real>& P, real d0) {
     real diff = real(0);
+    const real nu0 = S(F_NU, 0, 0, 0), p0 = S(F_P, 0, 0, 0);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       const int ex = a == 0, ey = a == 1, ez = a == 2;
-      const real nup = real(0.5) * (S(F_NU, 0, 0, 0) + S(F_NU, ex, ey, ez));
-      const real num = real(0.5) * (S(F_NU, 0, 0, 0) + S(F_NU, -ex, -ey, -ez));
-      diff += (nup * (S(F_P, ex, ey, ez) - S(F_P, 0, 0, 0)) - num * (S(F_P, 0, 0, 0) - S(F_P, -ex, -ey, -ez))) *
-              P.inv_dx2;
+      diff += (nu0 + S(F_NU, ex, ey, ez)) * (S(F_P, ex, ey, ez) - p0) -
+              (nu0 + S(F_NU, -ex, -ey, -ez)) * (p0 - S(F_P, -ex, -ey, -ez));
     }
-    return -S(F_RHO, 0, 0, 0) * P.cs2 * D0 + diff;
+    return -S(F_RHO, 0, 0, 0) * P.cs2 * (d0 * P.inv_dx) + diff * (real(0.5) * P.inv_dx2);
   }
 
-  // rate of velocity component C on the cell's low face along C
+  // rate of velocity component C on the cell's low face along C; d0 = dx div u of the cell
   template <int C>
-  __device__ __forceinline__ static real rate_vel(const T& S, const KParams<real>& P, real D0) {
+  __device__ __forceinline__ static real rate_vel(const T& S, const KParams<real>& P, real d0) {
     constexpr int cx = C == 0, cy = C == 1, cz = C == 2;
     const int FC = F_U + C;
-    const real rb = real(0.5) * (S(F_RHO, -cx, -cy, -cz) + S(F_RHO, 0, 0, 0));
-    const real gradp = (pbar<C>(S, P, 0, 0, 0) - pbar<C>(S, P, -cx, -cy, -cz)) * P.inv_dx;
+    const real rb2 = S(F_RHO, -cx, -cy, -cz) + S(F_RHO, 0, 0, 0);   // 2 rho on the face
+    real gradp;
+    if (averaged(P))
+      gradp = (psum<C>(S, 0, 0, 0) - psum<C>(S, -cx, -cy, -cz)) *
+              (P.inv_dx * real(DIM == 2 ? 1.0 / 6.0 : 1.0 / 36.0));
+    else
+      gradp = (S(F_P, 0, 0, 0) - S(F_P, -cx, -cy, -cz)) * P.inv_dx;
     const real uc0 = S(FC, 0, 0, 0);
-    const real t_cc = (S(F_ETA, 0, 0, 0) * (S(FC, cx, cy, cz) - uc0) -
-                       S(F_ETA, -cx, -cy, -cz) * (uc0 - S(FC, -cx, -cy, -cz))) *
-                      P.inv_dx2;
-    real t_tr = real(0), conv_tr = real(0);
+    const real tcc = S(F_ETA, 0, 0, 0) * (S(FC, cx, cy, cz) - uc0) -
+                     S(F_ETA, -cx, -cy, -cz) * (uc0 - S(FC, -cx, -cy, -cz));
+    real edge = real(0), conv4 = real(0);
 #pragma unroll
     for (int t = 0; t < DIM; ++t) {
       if (t == C) continue;
       const int tx = t == 0, ty = t == 1, tz = t == 2;
       const int FT = F_U + t;
-      real etp, etm;
-      edge_eta<C>(S, t, etp, etm);
-      const real t_tt = (etp * (S(FC, tx, ty, tz) - uc0) - etm * (uc0 - S(FC, -tx, -ty, -tz))) * P.inv_dx2;
-      const real t_tc = (etp * (S(FT, tx, ty, tz) - S(FT, tx - cx, ty - cy, tz - cz)) -
-                         etm * (S(FT, 0, 0, 0) - S(FT, -cx, -cy, -cz))) *
-                        P.inv_dx2;
-      t_tr += t_tt + t_tc;
-      const real ubar = (S(FT, 0, 0, 0) + S(FT, -cx, -cy, -cz) + S(FT, tx, ty, tz) +
-                         S(FT, tx - cx, ty - cy, tz - cz)) *
-                        real(0.25);
-      conv_tr += ubar * (S(FC, tx, ty, tz) - S(FC, -tx, -ty, -tz)) * P.inv_2dx;
+      real e4p, e4m;
+      edge_eta4<C>(S, t, e4p, e4m);
+      const real ucp = S(FC, tx, ty, tz), ucm = S(FC, -tx, -ty, -tz);
+      const real ut0 = S(FT, 0, 0, 0), utc = S(FT, -cx, -cy, -cz);
+      const real utp = S(FT, tx, ty, tz), utpc = S(FT, tx - cx, ty - cy, tz - cz);
+      edge += e4p * ((ucp - uc0) + (utp - utpc)) - e4m * ((uc0 - ucm) + (ut0 - utc));
+      conv4 += ((ut0 + utc) + (utp + utpc)) * (ucp - ucm);
     }
-    real t_b = real(0);
-    if (P.bulk) t_b = (S(F_ETA, 0, 0, 0) * D0 - S(F_ETA, -cx, -cy, -cz) * div(S, P, -cx, -cy, -cz)) * P.inv_dx;
+    real visc = real(2) * tcc + real(0.25) * edge;
+    if (P.bulk) visc += S(F_ETA, 0, 0, 0) * d0 - S(F_ETA, -cx, -cy, -cz) * divsum(S, -cx, -cy, -cz);
     const real st = -P.sigma * (S(F_PHI, 0, 0, 0) + S(F_PHI, -cx, -cy, -cz)) *
                     (S(F_MU, 0, 0, 0) - S(F_MU, -cx, -cy, -cz)) * P.inv_2dx;
-    const real grav = (rb - P.rho_ref) * P.g[C];
-    const real force = -gradp + real(2) * t_cc + t_tr + t_b + st + grav;
-    const real conv = uc0 * (S(FC, cx, cy, cz) - S(FC, -cx, -cy, -cz)) * P.inv_2dx + conv_tr;
-    return fdiv(force, rb) - conv;
+    const real grav = (real(0.5) * rb2 - P.rho_ref) * P.g[C];
+    const real force = -gradp + visc * P.inv_dx2 + st + grav;
+    const real conv = (uc0 * (S(FC, cx, cy, cz) - S(FC, -cx, -cy, -cz)) + real(0.25) * conv4) * P.inv_2dx;
+    return fdiv(real(2) * force, rb2) - conv;
   }
 };
 
@@ -189,7 +166,7 @@ __device__ __forceinline__ void flow2d_tile(const KParams<real>& P, const FlowAr
     S.sm = sm;
     S.c = (ty + 1) * SXv + (tx + 1);
     using Ops = FlowOps<real, 2, Tile2<real, SXv, PLv>>;
-    const real D0 = Ops::div(S, P, 0, 0, 0);
+    const real D0 = Ops::divsum(S, 0, 0, 0);
     real L[3];
     L[0] = Ops::rate_p(S, P, D0);
     L[1] = (P.bc[0] != BC_PERIODIC && i == 0) ? real(0) : Ops::template rate_vel<0>(S, P, D0);

@@ -9,6 +9,11 @@
 
 namespace gpe2p {
 
+// 3D flow stage: each thread computes two cells adjacent in y, so a block's
+// tile has 2 TY rows and its staged planes FLOW3_SY rows
+constexpr int FLOW3_TY = 2 * TY;
+constexpr int FLOW3_SY = FLOW3_TY + 2;
+
 // one flow stage: out = a q0 + b (q + dt L(q))   (Eq. tvd-rk3)
 template <typename real>
 struct FlowArgs {

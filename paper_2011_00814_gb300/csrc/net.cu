@@ -132,34 +132,39 @@ static ConvArgs conv_args(const gpe2p_net* n, const ConvL& c, int B) {
   return a;
 }
 
-// forward of layer c from (x, ldx, xoff) into (y, ldy, yoff), storing the pre-activation
+// forward of layer c from (x, ldx, xoff) into (y, ldy, yoff); the pre-activation is stored
+// for training; up: x is stored at half resolution and read upsampled
 static cudaError_t fwd(gpe2p_net* n, const ConvL& c, int B, const __nv_bfloat16* x, int ldx, int xoff,
-                       __nv_bfloat16* y, int ldy, int yoff) {
+                       __nv_bfloat16* y, int ldy, int yoff, bool train, int up = 0) {
   ConvArgs a = conv_args(n, c, B);
   a.x = x;
   a.ldx = ldx;
   a.xoff = xoff;
+  a.up = up;
   a.y = y;
   a.ldy = ldy;
   a.yoff = yoff;
+  if (!train) a.z = nullptr;
   return conv_forward(a, n->stream);
 }
 
-// backward of layer c: dY (gy, ldgy, gyoff) -> dZ -> dW, db and (if gx) dX into (gx, ldgx, gxoff)
+// backward of layer c: dY (gy, ldgy, gyoff) -> dZ -> dW, db and (if gx) dX into (gx, ldgx, gxoff);
+// up: the layer's input x is stored at half resolution (gx is then at full resolution)
 static cudaError_t bwd(gpe2p_net* n, const ConvL& c, int B, const __nv_bfloat16* x, int ldx, int xoff,
                        const __nv_bfloat16* gy, int ldgy, int gyoff, __nv_bfloat16* gx, int ldgx, int gxoff,
-                       int accumulate) {
+                       int accumulate, int up = 0) {
   const long long np = npix_at(n, c.level, B);
-  cudaError_t e = dsilu(gy, ldgy, gyoff, c.z, n->dz, np, c.cout, n->stream);
+  cudaError_t e = dsilu_bias(gy, ldgy, gyoff, c.z, n->dz, np, c.cout, n->G + c.b, n->stream);
   if (e != cudaSuccess) return e;
   ConvArgs a = conv_args(n, c, B);
   a.x = x;
   a.ldx = ldx;
   a.xoff = xoff;
+  a.up = up;
   a.dz = n->dz;
   if ((e = conv_wgrad(a, n->stream)) != cudaSuccess) return e;
-  if ((e = bias_grad(n->dz, np, c.cout, n->G + c.b, n->stream)) != cudaSuccess) return e;
   if (gx) {
+    a.up = 0;
     a.dx = gx;
     a.lddx = ldgx;
     a.dxoff = gxoff;
@@ -169,7 +174,11 @@ static cudaError_t bwd(gpe2p_net* n, const ConvL& c, int B, const __nv_bfloat16*
   return cudaSuccess;
 }
 
-static cudaError_t forward(gpe2p_net* n, const float* x, int B) {
+// The encoder output of level l < L-1 is written straight into the second
+// half of the decoder's concatenation buffer cat[l] (channels c..2c), where
+// the decoder reads it and the pooling of level l+1 takes it from; the
+// decoder's upsampling is read inside the convolution that follows it.
+static cudaError_t forward(gpe2p_net* n, const float* x, int B, bool train) {
   const int L = n->L;
   cudaError_t e = to_bf16(x, n->in_ch, n->in16.v, 16, npix_at(n, 0, B), n->norm, n->stream);
   if (e != cudaSuccess) return e;
@@ -177,25 +186,27 @@ static cudaError_t forward(gpe2p_net* n, const float* x, int B) {
     const __nv_bfloat16* in = n->in16.v;
     int ldin = 16;
     if (l > 0) {
-      if ((e = pool_fwd(n->eb[l - 1].v, n->ch[l - 1], 0, n->pooled[l - 1].v, B, n->H >> (l - 1), n->W >> (l - 1),
-                        n->ch[l - 1], n->stream)) != cudaSuccess)
+      const int cp = n->ch[l - 1];
+      if ((e = pool_fwd(n->cat[l - 1].v, 2 * cp, cp, n->pooled[l - 1].v, B, n->H >> (l - 1), n->W >> (l - 1), cp,
+                        n->stream)) != cudaSuccess)
         return e;
       in = n->pooled[l - 1].v;
-      ldin = n->ch[l - 1];
+      ldin = cp;
     }
-    if ((e = fwd(n, n->conv[n->enc_a[l]], B, in, ldin, 0, n->ea[l].v, n->ch[l], 0)) != cudaSuccess) return e;
-    if ((e = fwd(n, n->conv[n->enc_b[l]], B, n->ea[l].v, n->ch[l], 0, n->eb[l].v, n->ch[l], 0)) != cudaSuccess)
+    if ((e = fwd(n, n->conv[n->enc_a[l]], B, in, ldin, 0, n->ea[l].v, n->ch[l], 0, train)) != cudaSuccess) return e;
+    const bool last = l == L - 1;
+    __nv_bfloat16* out = last ? n->eb[l].v : n->cat[l].v;
+    if ((e = fwd(n, n->conv[n->enc_b[l]], B, n->ea[l].v, n->ch[l], 0, out, last ? n->ch[l] : 2 * n->ch[l],
+                 last ? 0 : n->ch[l], train)) != cudaSuccess)
       return e;
   }
   const __nv_bfloat16* din = n->eb[L - 1].v;
   for (int l = L - 2; l >= 0; --l) {
     const int c = n->ch[l], cu = n->ch[l + 1];
-    if ((e = up_fwd(din, n->upx[l].v, B, n->H >> l, n->W >> l, cu, n->stream)) != cudaSuccess) return e;
-    if ((e = fwd(n, n->conv[n->up[l]], B, n->upx[l].v, cu, 0, n->cat[l].v, 2 * c, 0)) != cudaSuccess) return e;
-    if ((e = copy_ch(n->eb[l].v, c, 0, n->cat[l].v, 2 * c, c, npix_at(n, l, B), c, 0, n->stream)) != cudaSuccess)
+    if ((e = fwd(n, n->conv[n->up[l]], B, din, cu, 0, n->cat[l].v, 2 * c, 0, train, 1)) != cudaSuccess) return e;
+    if ((e = fwd(n, n->conv[n->dec_a[l]], B, n->cat[l].v, 2 * c, 0, n->da[l].v, c, 0, train)) != cudaSuccess)
       return e;
-    if ((e = fwd(n, n->conv[n->dec_a[l]], B, n->cat[l].v, 2 * c, 0, n->da[l].v, c, 0)) != cudaSuccess) return e;
-    if ((e = fwd(n, n->conv[n->dec_b[l]], B, n->da[l].v, c, 0, n->db[l].v, c, 0)) != cudaSuccess) return e;
+    if ((e = fwd(n, n->conv[n->dec_b[l]], B, n->da[l].v, c, 0, n->db[l].v, c, 0, train)) != cudaSuccess) return e;
     din = n->db[l].v;
   }
   return head_fwd(din, n->ch[0], n->P + n->head_w, n->P + n->head_b, n->out, n->out_ch, npix_at(n, 0, B), x,
@@ -219,7 +230,8 @@ static cudaError_t backward(gpe2p_net* n, int B) {
       return e;
     if ((e = copy_ch(n->cat[l].g, 2 * c, c, n->eb[l].g, c, 0, npix_at(n, l, B), c, 0, n->stream)) != cudaSuccess)
       return e;
-    if ((e = bwd(n, n->conv[n->up[l]], B, n->upx[l].v, cu, 0, n->cat[l].g, 2 * c, 0, n->upx[l].g, cu, 0, 0)) !=
+    const __nv_bfloat16* dlow = l + 1 <= L - 2 ? n->db[l + 1].v : n->eb[L - 1].v;
+    if ((e = bwd(n, n->conv[n->up[l]], B, dlow, cu, 0, n->cat[l].g, 2 * c, 0, n->upx[l].g, cu, 0, 0, 1)) !=
         cudaSuccess)
       return e;
     __nv_bfloat16* gnext = l + 1 <= L - 2 ? n->db[l + 1].g : n->eb[L - 1].g;
@@ -435,7 +447,7 @@ extern "C" int gpe2p_net_set_params(gpe2p_net_handle n, const float* host, long 
 
 extern "C" int gpe2p_net_forward(gpe2p_net_handle n, const float* x, float* y, int batch) {
   if (!n || !x || !y || batch < 1 || batch > n->maxB) return net_fail(n, GPE2P_EINVAL, "bad arguments");
-  NK(n, forward(n, x, batch), "forward");
+  NK(n, forward(n, x, batch, false), "forward");
   NK(n, cudaMemcpyAsync(y, n->out, (size_t)npix_at(n, 0, batch) * n->out_ch * sizeof(float), cudaMemcpyDeviceToDevice,
                         n->stream),
      "forward copy");
@@ -445,7 +457,7 @@ extern "C" int gpe2p_net_forward(gpe2p_net_handle n, const float* x, float* y, i
 static int loss_and_grads(gpe2p_net* n, const float* x, const float* t, int batch) {
   NK(n, cudaMemsetAsync(n->G, 0, n->nparam * sizeof(float), n->stream), "zero grads");
   NK(n, cudaMemsetAsync(n->loss, 0, sizeof(float), n->stream), "zero loss");
-  NK(n, forward(n, x, batch), "forward");
+  NK(n, forward(n, x, batch, true), "forward");
   NK(n, mse(n->out, t, n->dout, npix_at(n, 0, batch) * n->out_ch, n->out_ch, n->norm, n->loss, n->stream), "loss");
   NK(n, backward(n, batch), "backward");
   return GPE2P_OK;

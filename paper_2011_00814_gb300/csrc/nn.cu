@@ -99,11 +99,13 @@ __global__ void __launch_bounds__(NT) igemm_kernel(const ConvArgs a) {
           int dy = 0, dx = 0;
           if (ks == 9) { dy = tap / 3 - 1; dx = tap % 3 - 1; }
           if (MODE == 1) { dy = -dy; dx = -dx; }
-          const int yy = wrapi(y + dy, a.H), xx = wrapi(x + dx, a.W);
+          int yy = wrapi(y + dy, a.H), xx = wrapi(x + dx, a.W);
           const __nv_bfloat16* src = MODE == 0 ? a.x : a.dz;
           const int ld = MODE == 0 ? a.ldx : a.ldz;
           const int off = MODE == 0 ? a.xoff : 0;
-          const uint4* s = reinterpret_cast<const uint4*>(src + ((size_t)(b * a.H + yy) * a.W + xx) * ld + off + c);
+          int Hs = a.H, Ws = a.W;
+          if (MODE == 0 && a.up) { yy >>= 1; xx >>= 1; Hs >>= 1; Ws >>= 1; }
+          const uint4* s = reinterpret_cast<const uint4*>(src + ((size_t)(b * Hs + yy) * Ws + xx) * ld + off + c);
           v0 = s[0];
           v1 = s[1];
         }
@@ -149,8 +151,10 @@ __global__ void __launch_bounds__(NT) igemm_kernel(const ConvArgs a) {
           pix(p, a.H, a.W, b, y, x);
           int dy = 0, dx = 0;
           if (ks == 9) { dy = tap / 3 - 1; dx = tap % 3 - 1; }
-          const int yy = wrapi(y + dy, a.H), xx = wrapi(x + dx, a.W);
-          v = *reinterpret_cast<const uint4*>(a.x + ((size_t)(b * a.H + yy) * a.W + xx) * a.ldx + a.xoff + ci);
+          int yy = wrapi(y + dy, a.H), xx = wrapi(x + dx, a.W);
+          int Hs = a.H, Ws = a.W;
+          if (a.up) { yy >>= 1; xx >>= 1; Hs >>= 1; Ws >>= 1; }
+          v = *reinterpret_cast<const uint4*>(a.x + ((size_t)(b * Hs + yy) * Ws + xx) * a.ldx + a.xoff + ci);
         }
         const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v);
 #pragma unroll
@@ -233,107 +237,145 @@ static unsigned blocks_for(long long n, int per = 256) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
-// dZ = dY * silu'(z) (dY read with row stride ldy and channel offset yoff)
-__global__ void dsilu_kernel(const __nv_bfloat16* dy, int ldy, int yoff, const __nv_bfloat16* z, __nv_bfloat16* dz,
-                             long long npix, int c) {
-  const long long n = npix * c;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i / c;
-    const int ch = (int)(i - p * c);
-    const float g = __bfloat162float(dy[p * ldy + yoff + ch]);
-    dz[i] = __float2bfloat16_rn(g * dsilu(__bfloat162float(z[i])));
+// eight BF16 channels <-> floats
+__device__ __forceinline__ void unpack8(const uint4& v, float f[8]) {
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float2 t = __bfloat1622float2(h[e]);
+    f[2 * e] = t.x;
+    f[2 * e + 1] = t.y;
   }
 }
+__device__ __forceinline__ uint4 pack8(const float f[8]) {
+  uint4 v;
+  __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&v);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
+  return v;
+}
+__device__ __forceinline__ uint4 ld8(const __nv_bfloat16* p) { return *reinterpret_cast<const uint4*>(p); }
+__device__ __forceinline__ void st8(__nv_bfloat16* p, const uint4& v) { *reinterpret_cast<uint4*>(p) = v; }
 
-// db[c] += sum_p dZ[p, c]
-__global__ void bias_grad_kernel(const __nv_bfloat16* dz, long long npix, int c, float* db) {
-  extern __shared__ float red[];
-  for (int ch = threadIdx.x; ch < c; ch += blockDim.x) red[ch] = 0.f;
+// dZ = dY * silu'(z) (dY read with row stride ldy and channel offset yoff) and
+// db[c] += sum over pixels of the stored dZ; a thread takes 8 channels of a pixel
+__global__ void dsilu_bias_kernel(const __nv_bfloat16* dy, int ldy, int yoff, const __nv_bfloat16* z,
+                                  __nv_bfloat16* dz, long long npix, int c, float* db) {
+  extern __shared__ float red[];  // c
+  const int G = c >> 3, lanes = blockDim.x / G;
+  const int g = threadIdx.x % G, pl = threadIdx.x / G;
+  for (int q = threadIdx.x; q < c; q += blockDim.x) red[q] = 0.f;
   __syncthreads();
-  for (long long p = blockIdx.x; p < npix; p += gridDim.x)
-    for (int ch = threadIdx.x; ch < c; ch += blockDim.x) red[ch] += __bfloat162float(dz[p * c + ch]);
+  float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (long long p = blockIdx.x * (long long)lanes + pl; p < npix; p += (long long)gridDim.x * lanes) {
+    float gy[8], zz[8], d[8];
+    unpack8(ld8(dy + p * ldy + yoff + 8 * g), gy);
+    unpack8(ld8(z + p * c + 8 * g), zz);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) d[e] = gy[e] * dsilu(zz[e]);
+    const uint4 o = pack8(d);
+    st8(dz + p * c + 8 * g, o);
+    float r[8];
+    unpack8(o, r);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) s[e] += r[e];
+  }
+#pragma unroll
+  for (int e = 0; e < 8; ++e) atomicAdd(&red[8 * g + e], s[e]);
   __syncthreads();
-  for (int ch = threadIdx.x; ch < c; ch += blockDim.x) atomicAdd(db + ch, red[ch]);
+  for (int q = threadIdx.x; q < c; q += blockDim.x) atomicAdd(db + q, red[q]);
 }
 
-// 2x2 average pooling (forward) and its adjoint
+// 2x2 average pooling (forward) and its adjoint; a thread takes 8 channels
 __global__ void pool_fwd_kernel(const __nv_bfloat16* x, int ldx, int xoff, __nv_bfloat16* y, int B, int H, int W,
                                 int c) {
-  const int Ho = H / 2, Wo = W / 2;
-  const long long n = (long long)B * Ho * Wo * c;
+  const int Ho = H / 2, Wo = W / 2, G = c >> 3;
+  const long long n = (long long)B * Ho * Wo * G;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int ch = (int)(i % c);
-    long long q = i / c;
+    const int g = (int)(i % G);
+    long long q = i / G;
     const int xo = (int)(q % Wo);
-    q /= Wo;
-    const int yo = (int)(q % Ho);
-    const int b = (int)(q / Ho);
-    float s = 0.f;
+    const long long r = q / Wo;
+    const int yo = (int)(r % Ho);
+    const int b = (int)(r / Ho);
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, f[8];
     for (int dy = 0; dy < 2; ++dy)
-      for (int dx = 0; dx < 2; ++dx)
-        s += __bfloat162float(x[((size_t)(b * H + 2 * yo + dy) * W + 2 * xo + dx) * ldx + xoff + ch]);
-    y[i] = __float2bfloat16_rn(0.25f * s);
+      for (int dx = 0; dx < 2; ++dx) {
+        unpack8(ld8(x + ((size_t)(b * H + 2 * yo + dy) * W + 2 * xo + dx) * ldx + xoff + 8 * g), f);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc[e] += f[e];
+      }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) acc[e] *= 0.25f;
+    st8(y + q * c + 8 * g, pack8(acc));
   }
 }
 
 // dX (row stride ldx, offset xoff) = 1/4 dY spread; accumulate adds to dX
 __global__ void pool_bwd_kernel(const __nv_bfloat16* dy, __nv_bfloat16* dx, int ldx, int xoff, int B, int H, int W,
                                 int c, int accumulate) {
-  const long long n = (long long)B * H * W * c;
+  const int G = c >> 3;
+  const long long n = (long long)B * H * W * G;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int ch = (int)(i % c);
-    long long q = i / c;
+    const int g = (int)(i % G);
+    const long long q = i / G;
     const int x = (int)(q % W);
-    q /= W;
-    const int y = (int)(q % H);
-    const int b = (int)(q / H);
-    const float g = 0.25f * __bfloat162float(dy[((size_t)(b * (H / 2) + y / 2) * (W / 2) + x / 2) * c + ch]);
-    __nv_bfloat16* d = dx + ((size_t)(b * H + y) * W + x) * ldx + xoff + ch;
-    *d = __float2bfloat16_rn(accumulate ? g + __bfloat162float(*d) : g);
+    const long long r = q / W;
+    const int y = (int)(r % H);
+    const int b = (int)(r / H);
+    float f[8];
+    unpack8(ld8(dy + ((size_t)(b * (H / 2) + y / 2) * (W / 2) + x / 2) * c + 8 * g), f);
+    __nv_bfloat16* d = dx + q * ldx + xoff + 8 * g;
+    float o[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (accumulate) unpack8(ld8(d), o);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) o[e] += 0.25f * f[e];
+    st8(d, pack8(o));
   }
 }
 
-// nearest-neighbour 2x upsampling and its adjoint (sum of the four children)
-__global__ void up_fwd_kernel(const __nv_bfloat16* x, __nv_bfloat16* y, int B, int H, int W, int c) {
-  const long long n = (long long)B * H * W * c;  // H, W of the output
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int ch = (int)(i % c);
-    long long q = i / c;
-    const int xx = (int)(q % W);
-    q /= W;
-    const int yy = (int)(q % H);
-    const int b = (int)(q / H);
-    y[i] = x[((size_t)(b * (H / 2) + yy / 2) * (W / 2) + xx / 2) * c + ch];
-  }
-}
-
+// adjoint of the nearest 2x upsampling: the sum of the four children
 __global__ void up_bwd_kernel(const __nv_bfloat16* dy, __nv_bfloat16* dx, int B, int H, int W, int c) {
-  const int Hi = H / 2, Wi = W / 2;  // H, W of dY
-  const long long n = (long long)B * Hi * Wi * c;
+  const int Hi = H / 2, Wi = W / 2, G = c >> 3;  // H, W of dY
+  const long long n = (long long)B * Hi * Wi * G;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const int ch = (int)(i % c);
-    long long q = i / c;
+    const int g = (int)(i % G);
+    const long long q = i / G;
     const int xo = (int)(q % Wi);
-    q /= Wi;
-    const int yo = (int)(q % Hi);
-    const int b = (int)(q / Hi);
-    float s = 0.f;
+    const long long r = q / Wi;
+    const int yo = (int)(r % Hi);
+    const int b = (int)(r / Hi);
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, f[8];
     for (int dy2 = 0; dy2 < 2; ++dy2)
-      for (int dx2 = 0; dx2 < 2; ++dx2) s += __bfloat162float(dy[((size_t)(b * H + 2 * yo + dy2) * W + 2 * xo + dx2) * c + ch]);
-    dx[i] = __float2bfloat16_rn(s);
+      for (int dx2 = 0; dx2 < 2; ++dx2) {
+        unpack8(ld8(dy + ((size_t)(b * H + 2 * yo + dy2) * W + 2 * xo + dx2) * c + 8 * g), f);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc[e] += f[e];
+      }
+    st8(dx + q * c + 8 * g, pack8(acc));
   }
 }
 
 // copy c channels from (src, lds, soff) to (dst, ldd, doff); accumulate adds
 __global__ void copy_ch_kernel(const __nv_bfloat16* src, int lds, int soff, __nv_bfloat16* dst, int ldd, int doff,
                                long long npix, int c, int accumulate) {
-  const long long n = npix * c;
+  const int G = c >> 3;
+  const long long n = npix * G;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i / c;
-    const int ch = (int)(i - p * c);
-    const float v = __bfloat162float(src[p * lds + soff + ch]);
-    __nv_bfloat16* d = dst + p * ldd + doff + ch;
-    *d = __float2bfloat16_rn(accumulate ? v + __bfloat162float(*d) : v);
+    const long long p = i / G;
+    const int g = (int)(i - p * G);
+    const uint4 v = ld8(src + p * lds + soff + 8 * g);
+    __nv_bfloat16* d = dst + p * ldd + doff + 8 * g;
+    if (accumulate) {
+      float a[8], b[8];
+      unpack8(v, a);
+      unpack8(ld8(d), b);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) a[e] += b[e];
+      st8(d, pack8(a));
+    } else {
+      st8(d, v);
+    }
   }
 }
 
@@ -347,41 +389,84 @@ __global__ void to_bf16_kernel(const float* x, int cin, __nv_bfloat16* y, int ld
   }
 }
 
-// output layer: 1x1 convolution cin -> cout (small cout), FP32 out, no activation, then the
-// output map (scale, optional residual from the raw FP32 input xin of in_ch channels)
+// output layer: 1x1 convolution cin -> cout (cout <= 16), FP32 out, no activation, then the
+// output map (scale, optional residual from the raw FP32 input xin of in_ch channels);
+// a thread takes one pixel, weights in shared memory
 __global__ void head_fwd_kernel(const __nv_bfloat16* x, int cin, const float* w, const float* b, float* y, int cout,
                                 long long npix, const float* xin, int in_ch, const Norm nm) {
+  extern __shared__ __align__(16) float sw[];  // [cout][cin], bias[cout]
+  for (int q = threadIdx.x; q < cout * cin + cout; q += blockDim.x) sw[q] = q < cout * cin ? w[q] : b[q - cout * cin];
+  __syncthreads();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix; p += (long long)gridDim.x * blockDim.x) {
-    for (int o = 0; o < cout; ++o) {
-      float s = b[o];
-      for (int c = 0; c < cin; ++c) s += w[o * cin + c] * __bfloat162float(x[p * cin + c]);
-      y[p * cout + o] = (nm.residual ? xin[p * in_ch + o] : 0.f) + nm.oscale[o] * s;
+    float acc[16];
+#pragma unroll
+    for (int o = 0; o < 16; ++o) acc[o] = o < cout ? sw[cout * cin + o] : 0.f;
+    for (int c0 = 0; c0 < cin; c0 += 8) {
+      float f[8];
+      unpack8(ld8(x + p * cin + c0), f);
+#pragma unroll
+      for (int o = 0; o < 16; ++o) {
+        if (o < cout) {
+          const float* wr = sw + o * cin + c0;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) acc[o] += wr[e] * f[e];
+        }
+      }
     }
+#pragma unroll
+    for (int o = 0; o < 16; ++o)
+      if (o < cout) y[p * cout + o] = (nm.residual ? xin[p * in_ch + o] : 0.f) + nm.oscale[o] * acc[o];
   }
 }
 
-// its adjoint: dX = dY W (bf16), dW += sum_p dY x^T, db += sum_p dY
+// its adjoint: dX = dY W (bf16), dW += sum_p dY x^T, db += sum_p dY.  A block stages a tile
+// of TP pixels; thread t computes dX of pixel t, and each (o, c) pair of dW, db is
+// accumulated by one thread in shared memory.
 __global__ void head_bwd_kernel(const __nv_bfloat16* x, int cin, const float* w, const float* dy, int cout,
-                                __nv_bfloat16* dx, float* dw, float* db, long long npix) {
-  extern __shared__ float sred[];  // cout*cin + cout
-  const int nr = cout * cin + cout;
-  for (int q = threadIdx.x; q < nr; q += blockDim.x) sred[q] = 0.f;
-  __syncthreads();
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix; p += (long long)gridDim.x * blockDim.x) {
-    for (int c = 0; c < cin; ++c) {
-      float s = 0.f;
-      for (int o = 0; o < cout; ++o) s += dy[p * cout + o] * w[o * cin + c];
-      dx[p * cin + c] = __float2bfloat16_rn(s);
+                                __nv_bfloat16* dx, float* dw, float* db, long long npix, int TP) {
+  extern __shared__ __align__(16) float sh[];
+  const int npair = cout * cin + cout;
+  float* sacc = sh;                         // npair
+  float* sw = sacc + npair;                 // cout * cin
+  float* sdy = sw + cout * cin;             // TP * cout
+  // the staged activations start on a 16-byte boundary (they are moved 8 channels at a time)
+  const int nf = (npair + cout * cin + TP * cout + 3) & ~3;
+  __nv_bfloat16* sx = reinterpret_cast<__nv_bfloat16*>(sh + nf);   // TP * cin
+  for (int q = threadIdx.x; q < npair; q += blockDim.x) sacc[q] = 0.f;
+  for (int q = threadIdx.x; q < cout * cin; q += blockDim.x) sw[q] = w[q];
+  for (long long p0 = (long long)blockIdx.x * TP; p0 < npix; p0 += (long long)gridDim.x * TP) {
+    const int np = (int)(npix - p0 < TP ? npix - p0 : TP);
+    __syncthreads();
+    for (int q = threadIdx.x; q < np * cout; q += blockDim.x) sdy[q] = dy[p0 * cout + q];
+    for (int q = threadIdx.x; q < np * (cin >> 3); q += blockDim.x)
+      st8(sx + q * 8, ld8(x + p0 * cin + (long long)q * 8));
+    __syncthreads();
+    for (int t = threadIdx.x; t < np; t += blockDim.x) {
+      for (int c0 = 0; c0 < cin; c0 += 8) {
+        float d[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int o = 0; o < cout; ++o) {
+          const float g = sdy[t * cout + o];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) d[e] += g * sw[o * cin + c0 + e];
+        }
+        st8(dx + (p0 + t) * cin + c0, pack8(d));
+      }
     }
-    for (int o = 0; o < cout; ++o) {
-      const float g = dy[p * cout + o];
-      atomicAdd(&sred[cout * cin + o], g);
-      for (int c = 0; c < cin; ++c) atomicAdd(&sred[o * cin + c], g * __bfloat162float(x[p * cin + c]));
+    for (int q = threadIdx.x; q < npair; q += blockDim.x) {
+      float acc = 0.f;
+      if (q < cout * cin) {
+        const int o = q / cin, c = q - o * cin;
+        for (int t = 0; t < np; ++t) acc += sdy[t * cout + o] * __bfloat162float(sx[t * cin + c]);
+      } else {
+        const int o = q - cout * cin;
+        for (int t = 0; t < np; ++t) acc += sdy[t * cout + o];
+      }
+      sacc[q] += acc;
     }
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < cout * cin; q += blockDim.x) atomicAdd(dw + q, sred[q]);
-  for (int q = threadIdx.x; q < cout; q += blockDim.x) atomicAdd(db + q, sred[cout * cin + q]);
+  for (int q = threadIdx.x; q < cout * cin; q += blockDim.x) atomicAdd(dw + q, sacc[q]);
+  for (int q = threadIdx.x; q < cout; q += blockDim.x) atomicAdd(db + q, sacc[cout * cin + q]);
 }
 
 // mean squared error of the scaled output error e = (y - t) / oscale and its gradient with
@@ -466,45 +551,36 @@ cudaError_t conv_wgrad(const ConvArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t dsilu(const __nv_bfloat16* dy, int ldy, int yoff, const __nv_bfloat16* z, __nv_bfloat16* dz,
-                  long long npix, int c, cudaStream_t s) {
-  dsilu_kernel<<<blocks_for(npix * c), 256, 0, s>>>(dy, ldy, yoff, z, dz, npix, c);
-  return cudaGetLastError();
-}
-
-cudaError_t bias_grad(const __nv_bfloat16* dz, long long npix, int c, float* db, cudaStream_t s) {
-  long long nb = npix / 256;
-  if (nb < 1) nb = 1;
-  if (nb > 152 * 4) nb = 152 * 4;
-  bias_grad_kernel<<<(unsigned)nb, 128, c * sizeof(float), s>>>(dz, npix, c, db);
+cudaError_t dsilu_bias(const __nv_bfloat16* dy, int ldy, int yoff, const __nv_bfloat16* z, __nv_bfloat16* dz,
+                       long long npix, int c, float* db, cudaStream_t s) {
+  const int G = c / 8;
+  const int lanes = G >= 256 ? 1 : 256 / G;
+  long long nb = (npix + lanes - 1) / lanes;
+  if (nb > 152 * 8) nb = 152 * 8;
+  dsilu_bias_kernel<<<(unsigned)nb, G * lanes, c * sizeof(float), s>>>(dy, ldy, yoff, z, dz, npix, c, db);
   return cudaGetLastError();
 }
 
 cudaError_t pool_fwd(const __nv_bfloat16* x, int ldx, int xoff, __nv_bfloat16* y, int B, int H, int W, int c,
                      cudaStream_t s) {
-  pool_fwd_kernel<<<blocks_for((long long)B * H * W * c / 4), 256, 0, s>>>(x, ldx, xoff, y, B, H, W, c);
+  pool_fwd_kernel<<<blocks_for((long long)B * H * W * c / 32), 256, 0, s>>>(x, ldx, xoff, y, B, H, W, c);
   return cudaGetLastError();
 }
 
 cudaError_t pool_bwd(const __nv_bfloat16* dy, __nv_bfloat16* dx, int ldx, int xoff, int B, int H, int W, int c,
                      int accumulate, cudaStream_t s) {
-  pool_bwd_kernel<<<blocks_for((long long)B * H * W * c), 256, 0, s>>>(dy, dx, ldx, xoff, B, H, W, c, accumulate);
-  return cudaGetLastError();
-}
-
-cudaError_t up_fwd(const __nv_bfloat16* x, __nv_bfloat16* y, int B, int H, int W, int c, cudaStream_t s) {
-  up_fwd_kernel<<<blocks_for((long long)B * H * W * c), 256, 0, s>>>(x, y, B, H, W, c);
+  pool_bwd_kernel<<<blocks_for((long long)B * H * W * c / 8), 256, 0, s>>>(dy, dx, ldx, xoff, B, H, W, c, accumulate);
   return cudaGetLastError();
 }
 
 cudaError_t up_bwd(const __nv_bfloat16* dy, __nv_bfloat16* dx, int B, int H, int W, int c, cudaStream_t s) {
-  up_bwd_kernel<<<blocks_for((long long)B * H * W * c / 4), 256, 0, s>>>(dy, dx, B, H, W, c);
+  up_bwd_kernel<<<blocks_for((long long)B * H * W * c / 32), 256, 0, s>>>(dy, dx, B, H, W, c);
   return cudaGetLastError();
 }
 
 cudaError_t copy_ch(const __nv_bfloat16* src, int lds, int soff, __nv_bfloat16* dst, int ldd, int doff, long long npix,
                     int c, int accumulate, cudaStream_t s) {
-  copy_ch_kernel<<<blocks_for(npix * c), 256, 0, s>>>(src, lds, soff, dst, ldd, doff, npix, c, accumulate);
+  copy_ch_kernel<<<blocks_for(npix * c / 8), 256, 0, s>>>(src, lds, soff, dst, ldd, doff, npix, c, accumulate);
   return cudaGetLastError();
 }
 
@@ -516,16 +592,25 @@ cudaError_t to_bf16(const float* x, int cin, __nv_bfloat16* y, int ldo, long lon
 
 cudaError_t head_fwd(const __nv_bfloat16* x, int cin, const float* w, const float* b, float* y, int cout,
                      long long npix, const float* xin, int in_ch, const Norm& nm, cudaStream_t s) {
-  head_fwd_kernel<<<blocks_for(npix), 256, 0, s>>>(x, cin, w, b, y, cout, npix, xin, in_ch, nm);
+  head_fwd_kernel<<<blocks_for(npix), 256, (cout * cin + cout) * sizeof(float), s>>>(x, cin, w, b, y, cout, npix,
+                                                                                      xin, in_ch, nm);
   return cudaGetLastError();
 }
 
 cudaError_t head_bwd(const __nv_bfloat16* x, int cin, const float* w, const float* dy, int cout, __nv_bfloat16* dx,
                      float* dw, float* db, long long npix, cudaStream_t s) {
-  long long nb = (npix + 255) / 256;
+  int TP = 8192 / cin;
+  if (TP > 256) TP = 256;
+  if (TP < 8) TP = 8;
+  const size_t nf = (size_t)((cout * cin + cout + cout * cin + TP * cout + 3) & ~3);
+  const size_t smem = nf * sizeof(float) + (size_t)TP * cin * 2;
+  long long nb = (npix + TP - 1) / TP;
   if (nb > 152 * 4) nb = 152 * 4;
-  head_bwd_kernel<<<(unsigned)nb, 256, (cout * cin + cout) * sizeof(float), s>>>(x, cin, w, dy, cout, dx, dw, db,
-                                                                                  npix);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(head_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  head_bwd_kernel<<<(unsigned)nb, 256, smem, s>>>(x, cin, w, dy, cout, dx, dw, db, npix, TP);
   return cudaGetLastError();
 }
 

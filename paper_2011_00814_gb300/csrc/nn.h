@@ -23,6 +23,7 @@ struct ConvArgs {
   // forward: y = act(z), z = conv(x) + bias
   const __nv_bfloat16* x;
   int ldx, xoff;       // x: row stride (channels per pixel) and channel offset
+  int up;              // 1: x is stored at (H/2, W/2) and read as its nearest 2x upsampling
   const __nv_bfloat16* wt;  // [cout][taps*cin]
   const float* bias;
   __nv_bfloat16* z;    // pre-activation [npix][cout] (or nullptr)
@@ -48,14 +49,13 @@ cudaError_t conv_forward_tc(const ConvArgs& a, cudaStream_t s);
 cudaError_t conv_dgrad_tc(const ConvArgs& a, cudaStream_t s);
 cudaError_t conv_dgrad(const ConvArgs& a, cudaStream_t s);
 cudaError_t conv_wgrad(const ConvArgs& a, cudaStream_t s);
-cudaError_t dsilu(const __nv_bfloat16* dy, int ldy, int yoff, const __nv_bfloat16* z, __nv_bfloat16* dz,
-                  long long npix, int c, cudaStream_t s);
-cudaError_t bias_grad(const __nv_bfloat16* dz, long long npix, int c, float* db, cudaStream_t s);
+// dZ = dY silu'(z) and db += sum over pixels of dZ
+cudaError_t dsilu_bias(const __nv_bfloat16* dy, int ldy, int yoff, const __nv_bfloat16* z, __nv_bfloat16* dz,
+                       long long npix, int c, float* db, cudaStream_t s);
 cudaError_t pool_fwd(const __nv_bfloat16* x, int ldx, int xoff, __nv_bfloat16* y, int B, int H, int W, int c,
                      cudaStream_t s);
 cudaError_t pool_bwd(const __nv_bfloat16* dy, __nv_bfloat16* dx, int ldx, int xoff, int B, int H, int W, int c,
                      int accumulate, cudaStream_t s);
-cudaError_t up_fwd(const __nv_bfloat16* x, __nv_bfloat16* y, int B, int H, int W, int c, cudaStream_t s);
 cudaError_t up_bwd(const __nv_bfloat16* dy, __nv_bfloat16* dx, int B, int H, int W, int c, cudaStream_t s);
 cudaError_t copy_ch(const __nv_bfloat16* src, int lds, int soff, __nv_bfloat16* dst, int ldd, int doff,
                     long long npix, int c, int accumulate, cudaStream_t s);

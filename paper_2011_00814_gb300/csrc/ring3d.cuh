@@ -33,13 +33,15 @@ __device__ __forceinline__ real ld_kind(int kind, const real* __restrict__ f, co
   }
 }
 
-template <typename real>
+// SYv: rows of a staged plane (the tile's rows plus the two halo rows)
+template <typename real, int SYv = SY>
 struct RingGeom {
   static constexpr int A = 16 / (int)sizeof(real);     // alignment of the box start, elements
   static constexpr int BX = TX + 2 * A;                // box width
-  static constexpr int PE = ((BX * SY * (int)sizeof(real) + 127) / 128) * 128 / (int)sizeof(real);
-  static constexpr uint32_t BOX_BYTES = BX * SY * sizeof(real);
-  // element (lx, ly) of the staged region (lx, ly in [0, SX) x [0, SY)): global
+  static constexpr int ROWS = SYv;
+  static constexpr int PE = ((BX * SYv * (int)sizeof(real) + 127) / 128) * 128 / (int)sizeof(real);
+  static constexpr uint32_t BOX_BYTES = BX * SYv * sizeof(real);
+  // element (lx, ly) of the staged region (lx, ly in [0, SX) x [0, SYv)): global
   // cell (i0 - 1 + lx, j0 - 1 + ly)
   __device__ __forceinline__ static int at(int lx, int ly) { return ly * BX + lx + A - 1; }
 };
@@ -51,11 +53,11 @@ struct Maps {
 
 // The pipeline state of one block.  NRAW fields are staged per plane; RING is
 // a power of two so that slots and phases are masks and shifts.
-template <typename real, int NRAW, int RING>
+template <typename real, int NRAW, int RING, int SYv = SY>
 struct Ring {
   static_assert((RING & (RING - 1)) == 0 && RING >= 4, "RING must be a power of two >= 4");
   static constexpr int LOG2 = RING == 4 ? 2 : (RING == 8 ? 3 : 4);
-  using G = RingGeom<real>;
+  using G = RingGeom<real, SYv>;
   uint64_t* bar;  // RING barriers
   real* raw;      // RING x NRAW x PE
   int first, last;  // planes kbeg-1 .. kend (inclusive)
@@ -120,21 +122,24 @@ struct Ring {
 };
 
 // the staged cells of a plane that can lie outside the domain: all of them on
-// a ghost plane, else the one-cell perimeter of the staged region
-constexpr int PERIM = 2 * SX + 2 * (SY - 2);
+// a ghost plane, else the one-cell perimeter of the staged region (SYv rows)
+template <int SYv = SY>
+constexpr int perim() { return 2 * SX + 2 * (SYv - 2); }
+constexpr int PERIM = perim<SY>();
+template <int SYv = SY>
 __device__ __forceinline__ void perim_cell(int q, int& lx, int& ly) {
   if (q < SX) { lx = q; ly = 0; }
-  else if (q < 2 * SX) { lx = q - SX; ly = SY - 1; }
-  else if (q < 2 * SX + SY - 2) { lx = 0; ly = q - 2 * SX + 1; }
-  else { lx = SX - 1; ly = q - 2 * SX - (SY - 2) + 1; }
+  else if (q < 2 * SX) { lx = q - SX; ly = SYv - 1; }
+  else if (q < 2 * SX + SYv - 2) { lx = 0; ly = q - 2 * SX + 1; }
+  else { lx = SX - 1; ly = q - 2 * SX - (SYv - 2) + 1; }
 }
 
 // shared-memory bytes of a kernel with NRAW staged and NDER derived fields
 // (derived fields keep four planes, indexed by the plane number mod 4):
 // 128 bytes of slack to align the base, 128 for the barriers, then the planes
-template <typename real, int NRAW, int NDER, int RING>
+template <typename real, int NRAW, int NDER, int RING, int SYv = SY>
 constexpr size_t ring_smem_bytes() {
-  return 256 + sizeof(real) * (size_t)RingGeom<real>::PE * (RING * NRAW + 4 * NDER);
+  return 256 + sizeof(real) * (size_t)RingGeom<real, SYv>::PE * (RING * NRAW + 4 * NDER);
 }
 
 // the 128-byte aligned start of the dynamic shared memory

@@ -350,6 +350,10 @@ def compare_to_solver(sur: Surrogate, prm, fields, calls: int, check_every: int 
     res["controller_ms"] = best
     res["speedup"] = res["solver_ms"] / best
     res["phi_l2"] = phi_l2(phi, phi_ref)
+    # the same error relative to how far the solver moved phi over the run: 1 for a
+    # method that leaves phi where it started, 0 for the solver itself
+    res["phi_l2_of_change"] = float(np.linalg.norm(phi - phi_ref) /
+                                    max(np.linalg.norm(phi_ref - fields["phi"]), 1e-300))
     res["interface_mean"], res["interface_max"] = interface_error(phi, phi_ref)
     res["stats"] = dataclasses.asdict(stats)
     return res
