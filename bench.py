@@ -208,6 +208,68 @@ def measure_batch2d(stream, steps=20, warmup=3, n=96):
     return out
 
 
+SURROGATE_WEIGHTS = os.path.join(ROOT, "paper_2011_00814_gb300", "data", "unet_two_drops_256.npz")
+
+
+def measure_surrogate(cases=(0, 1), calls=64):
+    """The learned surrogate on held-out two-drop problems (256 x 256, K = 64
+    steps per call, 64 calls = 4096 steps): time to solution of the
+    controller (network calls with a solver check every 4th call) against the
+    plain FP32 solver on the same stream, the final phase errors against the
+    solver, the same with the network replaced by persistence (the method
+    without the network), and the network's forward throughput against the
+    BF16 tensor peak."""
+    import torch
+    from paper_2011_00814_gb300 import surrogate as S
+    if not os.path.exists(SURROGATE_WEIGHTS):
+        return {"unavailable": "no trained weights file"}
+    sur = S.Surrogate.load(SURROGATE_WEIGHTS, max_batch=8)
+    out = {"workload": "two drops, periodic 256x256, FP32, K=64 steps per call, 64 calls (4096 steps), "
+                       "check every 4th call at phi L2 <= 2e-2",
+           "cases": []}
+    for c in cases:
+        prm, f = inputs.two_drops(50000 + c)
+        row = {"case": c, "r_rho": prm["r_rho"]}
+        for pers in (False, True):
+            r = S.compare_to_solver(sur, prm, f, calls=calls, repeats=2, persistence=pers)
+            r["stats"].pop("check_l2", None)
+            row["persistence" if pers else "network"] = r
+        out["cases"].append(row)
+    net = [row["network"] for row in out["cases"]]
+    out["speedup"] = statistics.mean(r["speedup"] for r in net)
+    out["phi_l2_max"] = max(r["phi_l2"] for r in net)
+    out["interface_max_cells"] = max(r["interface_max"] for r in net)
+    out["phi_l2_of_change"] = statistics.mean(r["phi_l2_of_change"] for r in net)
+    out["persistence_phi_l2_of_change"] = statistics.mean(row["persistence"]["phi_l2_of_change"]
+                                                          for row in out["cases"])
+    # network forward, batch 8, inference (BF16 tensor cores)
+    B = 8
+    x = torch.randn(B, sur.n, sur.n, S.NCH, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        sur.forward(x, y, B)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 20
+    e0.record(sur.torch_stream)
+    for _ in range(n):
+        sur.forward(x, y, B)
+    e1.record(sur.torch_stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    tf = sur.flops(B) / (ms / 1e3) / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak, kind = float(json.load(fh)["bf16_tflops"]), "measured"
+    except Exception:
+        peak, kind = 1900.0, "fallback"
+    out["forward"] = {"batch": B, "ms": ms, "gflop": sur.flops(B) / 1e9,
+                      "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                                   "frac": tf / peak, "peak_kind": kind}}
+    sur.close()
+    return out
+
+
 def dist_setup(n_gpus):
     if n_gpus <= 1 and "WORLD_SIZE" not in os.environ:
         return 0, 1, None
@@ -266,6 +328,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 2D measurement")
     ap.add_argument("--profile-steps", type=int, default=3)
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -379,6 +442,8 @@ def main():
     }
     if not args.no_batch:
         line["batch2d"] = measure_batch2d(stream)
+    if not args.no_surrogate and world == 1:
+        line["surrogate"] = measure_surrogate()
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)

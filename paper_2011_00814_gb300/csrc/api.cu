@@ -406,7 +406,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // a field as a 3D tensor (x, y, z) with padded rows; box = one staged plane of `rows` rows
-static bool encode_map(gpe2p_ctx* h, CUtensorMap* m, void* base, int rows = SY) {
+static bool encode_map(gpe2p_ctx* h, CUtensorMap* m, void* base, int rows) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return false;
   const int es = h->esize;
@@ -424,17 +424,17 @@ static bool encode_map(gpe2p_ctx* h, CUtensorMap* m, void* base, int rows = SY) 
 static int build_maps(gpe2p_ctx* h) {
   bool ok = true;
   for (int s = 0; s < 3; ++s) {
-    for (int f = 0; f < 4; ++f) ok = ok && encode_map(h, &h->flow_maps[s].m[f], h->Q[s][f], FLOW3_SY);
-    ok = ok && encode_map(h, &h->flow_maps[s].m[4], h->phi, FLOW3_SY);
-    ok = ok && encode_map(h, &h->flow_maps[s].m[5], h->mu, FLOW3_SY);
+    for (int f = 0; f < 4; ++f) ok = ok && encode_map(h, &h->flow_maps[s].m[f], h->Q[s][f], K3_SY);
+    ok = ok && encode_map(h, &h->flow_maps[s].m[4], h->phi, K3_SY);
+    ok = ok && encode_map(h, &h->flow_maps[s].m[5], h->mu, K3_SY);
   }
   void* phis[3] = {h->phi, h->phis[0], h->phis[1]};
   void* mus[3] = {h->mu, h->mus, h->mus};
   for (int c = 0; c < 3; ++c) {
-    ok = ok && encode_map(h, &h->ch_maps[c].m[0], phis[c]);
-    ok = ok && encode_map(h, &h->ch_maps[c].m[1], mus[c]);
-    for (int a = 0; a < 3; ++a) ok = ok && encode_map(h, &h->ch_maps[c].m[2 + a], h->uh[a]);
-    ok = ok && encode_map(h, &h->mu_maps[c].m[0], phis[c]);
+    ok = ok && encode_map(h, &h->ch_maps[c].m[0], phis[c], K3_SY);
+    ok = ok && encode_map(h, &h->ch_maps[c].m[1], mus[c], K3_SY);
+    for (int a = 0; a < 3; ++a) ok = ok && encode_map(h, &h->ch_maps[c].m[2 + a], h->uh[a], K3_SY);
+    ok = ok && encode_map(h, &h->mu_maps[c].m[0], phis[c], K3_SY);
   }
   if (!ok) return fail(h, GPE2P_ECUDA, "cuTensorMapEncodeTiled failed or is unavailable");
   return GPE2P_OK;
@@ -527,7 +527,7 @@ extern "C" int gpe2p_create(const gpe2p_params* p, void* stream, gpe2p_handle* o
   }
   // z-chunk of the marching kernels: enough blocks to fill the GPU a few times
   if (h->prm.dim == 3) {
-    const long long bxy = (long long)((h->prm.nx + TX - 1) / TX) * ((h->prm.ny + TY - 1) / TY);
+    const long long bxy = (long long)((h->prm.nx + TX - 1) / TX) * ((h->prm.ny + K3_TY - 1) / K3_TY);
     long long zch = (152LL * 6 + bxy - 1) / bxy;
     long long kc = (h->prm.nz + zch - 1) / zch;
     if (kc < 4) kc = 4;

@@ -105,17 +105,13 @@ __device__ __forceinline__ void ch_point_load(const KParams<real>& P, const CHAr
   if (A.scheme == 4 && A.stage >= 2) c.acc = A.acc[id];
 }
 
-// one cell of a CH stage: the rate -uhat.grad(phi_s) + M lap(mu_s) (or its
-// conservative form) and the RK combination of the stage
+// the CH rate of one cell: -uhat.grad(phi_s) + M lap(mu_s), or its conservative form
 template <typename real, int DIM, int ISO, typename T>
-__device__ __forceinline__ void ch_cell(const T& S, const KParams<real>& P, const CHArgs<real>& A, int i, int j,
-                                        int k, const CHPoint<real>& c) {
-  const long long id = lin(P, i, j, k);
+__device__ __forceinline__ real ch_rate(const T& S, const KParams<real>& P, const CHArgs<real>& A,
+                                       const CHPoint<real>& c) {
   const real lapmu = lap_iso<real, DIM, ISO>(S, P, C_MU);
   real adv = real(0);
   if (!A.conservative) {
-    if (A.compute_uh && A.stage != 0)
-      for (int a = 0; a < DIM; ++a) A.uh[a][id] = c.uh[a];
     real g[3];
     grad_iso<real, DIM, ISO>(S, P, C_PHI, g);
 #pragma unroll
@@ -142,13 +138,22 @@ __device__ __forceinline__ void ch_cell(const T& S, const KParams<real>& P, cons
 #pragma unroll
     for (int a = 0; a < DIM; ++a) adv += P.grad_c * s[a];
   }
-  const real L = -adv + P.M * lapmu;
+  return -adv + P.M * lapmu;
+}
+
+// the RK combination of a CH stage for one cell with rate L (phis0 = phi_s
+// at the cell) and its stores; also stores the stage-1 cell velocity
+template <typename real, int DIM>
+__device__ __forceinline__ void ch_finish(const KParams<real>& P, const CHArgs<real>& A, long long id,
+                                          const CHPoint<real>& c, real L, real phis0) {
+  if (!A.conservative && A.compute_uh && A.stage != 0)
+    for (int a = 0; a < DIM; ++a) A.uh[a][id] = c.uh[a];
   real o;
   if (A.stage == 0) {
     o = L;
   } else if (A.scheme == 2) {
     if (A.stage == 1) o = c.pn + P.dt * L;
-    else o = real(0.5) * c.pn + real(0.5) * (S(C_PHI, 0, 0, 0) + P.dt * L);
+    else o = real(0.5) * c.pn + real(0.5) * (phis0 + P.dt * L);
   } else {
     const real d = P.dt * L;
     const real pn = c.pn;
@@ -158,6 +163,13 @@ __device__ __forceinline__ void ch_cell(const T& S, const KParams<real>& P, cons
     else { o = pn + (c.acc + d) / real(6); }
   }
   A.out[id] = o;
+}
+
+// one cell of a CH stage: rate and RK combination
+template <typename real, int DIM, int ISO, typename T>
+__device__ __forceinline__ void ch_cell(const T& S, const KParams<real>& P, const CHArgs<real>& A, int i, int j,
+                                        int k, const CHPoint<real>& c) {
+  ch_finish<real, DIM>(P, A, lin(P, i, j, k), c, ch_rate<real, DIM, ISO>(S, P, A, c), S(C_PHI, 0, 0, 0));
 }
 
 // One 2D CH stage on the tile of TXv x TYv cells at (i0, j0), by a block of

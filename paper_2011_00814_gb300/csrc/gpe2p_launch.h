@@ -9,10 +9,11 @@
 
 namespace gpe2p {
 
-// 3D flow stage: each thread computes two cells adjacent in y, so a block's
-// tile has 2 TY rows and its staged planes FLOW3_SY rows
-constexpr int FLOW3_TY = 2 * TY;
-constexpr int FLOW3_SY = FLOW3_TY + 2;
+// 3D ring kernels (flow stage, CH stage, mu): each thread computes two cells
+// adjacent in y, so a block's tile has K3_TY = 2 TY rows and its staged
+// planes K3_SY rows
+constexpr int K3_TY = 2 * TY;
+constexpr int K3_SY = K3_TY + 2;
 
 // one flow stage: out = a q0 + b (q + dt L(q))   (Eq. tvd-rk3)
 template <typename real>

@@ -75,9 +75,36 @@ class Surrogate:
     def flops(self, batch: int = 1) -> float:
         return self.net.flops(batch)
 
+    def conv_weight_mask(self) -> np.ndarray:
+        """True for the entries of the flat parameters that the kernels read in
+        BF16: the 3x3 convolution weights (the layout of gpe2p_net_num_params:
+        per convolution, encoder 0..L-1 (a, b) then decoder L-2..0 (up, a, b),
+        weights [cout][9][cin] then bias [cout]; then the head)."""
+        L, ch = self.levels, self.channels
+        convs = []
+        for l in range(L):
+            convs += [(16 if l == 0 else ch[l - 1], ch[l]), (ch[l], ch[l])]
+        for l in range(L - 2, -1, -1):
+            convs += [(ch[l + 1], ch[l]), (2 * ch[l], ch[l]), (ch[l], ch[l])]
+        parts = []
+        for cin, cout in convs:
+            parts += [np.ones(cout * 9 * cin, bool), np.zeros(cout, bool)]
+        parts.append(np.zeros(NCH * ch[0] + NCH, bool))
+        m = np.concatenate(parts)
+        assert m.size == self.net.nparam
+        return m
+
     def save(self, path: str, meta: dict | None = None):
-        """FP32 weights and the normalisation in one ``.npz``."""
-        np.savez_compressed(path, params=self.net.get_params(), in_mean=self.in_mean, in_scale=self.in_scale,
+        """Weights and the normalisation in one ``.npz``.  The convolution
+        weights are stored rounded to BF16, the precision the kernels read them
+        in (so inference from the file is unchanged); biases and the head stay
+        FP32."""
+        p = self.net.get_params()
+        m = self.conv_weight_mask()
+        u = p[m].view(np.uint32).astype(np.uint64)
+        u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+        p[m] = u.astype(np.uint32).view(np.float32)
+        np.savez_compressed(path, params=p, in_mean=self.in_mean, in_scale=self.in_scale,
                             out_scale=self.out_scale,
                             shape=np.array([self.n, self.K, self.levels, *self.channels], np.int64),
                             meta=np.frombuffer(repr(meta or {}).encode(), np.uint8))
@@ -288,6 +315,44 @@ def phi_l2(phi, phi_ref) -> float:
     return float(np.linalg.norm(phi - phi_ref) / max(np.linalg.norm(phi_ref), 1e-300))
 
 
+def zero_crossings(phi, refine: int = 4):
+    """Points of the phi = 0 contour: phi is interpolated bilinearly
+    (periodically) onto a grid ``refine`` times finer, and on every x- and
+    y-edge of that grid where it changes sign the linear interpolation of the
+    crossing is taken; coordinates in cells of the original grid."""
+    from scipy.ndimage import zoom
+    ny0, nx0 = phi.shape
+    if refine > 1:
+        phi = zoom(phi, refine, order=1, mode="grid-wrap", grid_mode=True)
+    ny, nx = phi.shape
+    pts = []
+    for axis in (0, 1):
+        nb = np.roll(phi, -1, axis=axis)
+        m = (phi > 0) != (nb > 0)
+        jj, ii = np.nonzero(m)
+        a, b = phi[m], nb[m]
+        t = a / (a - b)
+        x = ii + 0.5 + (t if axis == 1 else 0.0)
+        y = jj + 0.5 + (t if axis == 0 else 0.0)
+        pts.append(np.stack([(x % nx) * (nx0 / nx), (y % ny) * (ny0 / ny)], axis=1))
+    return np.concatenate(pts)
+
+
+def interface_hausdorff(phi, phi_ref):
+    """Hausdorff distance, in cells, between the phi = 0 contours of two
+    periodic phase fields (the largest distance from a point of either
+    contour to the other contour)."""
+    from scipy.spatial import cKDTree
+    ny, nx = phi.shape
+    a, b = zero_crossings(phi), zero_crossings(phi_ref)
+    if len(a) == 0 or len(b) == 0:
+        return 0.0 if len(a) == len(b) else float("inf")
+    box = [nx, ny]
+    da = cKDTree(b, boxsize=box).query(a)[0]
+    db = cKDTree(a, boxsize=box).query(b)[0]
+    return float(max(da.max(), db.max()))
+
+
 def interface_error(phi, phi_ref):
     """Displacement of the phi = 0 interface, in cells: (mean, max).
 
@@ -354,6 +419,7 @@ def compare_to_solver(sur: Surrogate, prm, fields, calls: int, check_every: int 
     # method that leaves phi where it started, 0 for the solver itself
     res["phi_l2_of_change"] = float(np.linalg.norm(phi - phi_ref) /
                                     max(np.linalg.norm(phi_ref - fields["phi"]), 1e-300))
-    res["interface_mean"], res["interface_max"] = interface_error(phi, phi_ref)
+    res["interface_mean"], res["interface_max_local"] = interface_error(phi, phi_ref)
+    res["interface_max"] = interface_hausdorff(phi, phi_ref)
     res["stats"] = dataclasses.asdict(stats)
     return res

@@ -47,8 +47,8 @@ def main(argv=None):
 
     train_cases = [inputs.two_drops(a.seed * 100000 + s, n=a.n) for s in range(a.train)]
     test_cases = [inputs.two_drops(a.seed * 100000 + 50000 + s, n=a.n) for s in range(a.test)]
-    D, t_gen = S.generate(train_cases, a.snapshots, a.K)
-    Dt, t_gen_t = S.generate(test_cases, a.snapshots, a.K)
+    D, t_gen = S.generate(train_cases, a.snapshots, a.K, group=256)
+    Dt, t_gen_t = S.generate(test_cases, a.snapshots, a.K, group=256)
     steps_gen = (a.train + a.test) * a.snapshots * a.K
     summary["generate"] = {"seconds": t_gen + t_gen_t, "instance_steps": steps_gen,
                            "cell_updates_per_s": steps_gen * a.n * a.n / (t_gen + t_gen_t),
@@ -84,6 +84,7 @@ def main(argv=None):
 
     runs = []
     for c in range(min(a.compare, a.test)):
+        torch.cuda.synchronize()
         prm, f = test_cases[c]
         for pers in (False, True):
             r = S.compare_to_solver(sur, prm, f, calls=a.calls, repeats=2, persistence=pers)
