@@ -61,8 +61,15 @@ struct RingTile {
 // thread (tx, ty) computes the cells (i0 + tx, j0 + 2 ty + r), r = 0, 1.  The
 // two cells share most of their stencil, so the loads and sub-expressions
 // they have in common are formed once.
+// resident blocks per SM the 3D flow stage is compiled for (2: up to 128
+// registers, no spills; 3 caps them at 80 with spills and measured slower,
+// 5.61 against 4.88 ms per step of the 256x256x512 bubble)
+#ifndef GPE2P_FLOW_MINB
+#define GPE2P_FLOW_MINB 2
+#endif
+
 template <typename real, int MODE, int RING, int PAVG>
-__global__ void __launch_bounds__(NTHR, 2) flow3d_kernel(const __grid_constant__ Maps<NRAW_FLOW> maps,
+__global__ void __launch_bounds__(NTHR, GPE2P_FLOW_MINB) flow3d_kernel(const __grid_constant__ Maps<NRAW_FLOW> maps,
                                                       const __grid_constant__ KParams<real> P,
                                                       const FlowArgs<real> A, const int kchunk, int* err) {
   constexpr int SYv = K3_SY;
