@@ -201,6 +201,29 @@ enum { GPE2P_FAULT_SKIP_BARRIER = 1, GPE2P_FAULT_WAIT_LIMIT = 2, GPE2P_FAULT_FOR
        GPE2P_FAULT_CLEAR = 4 };
 int gpe2p_set_fault_injection(gpe2p_handle h, int what, long long value);
 
+/* ---- precision policy of the phi accumulation --------------------------
+ * FP32 problems store phi^{n+1/2} in FP32.  The Cahn-Hilliard update
+ * conserves the phi integral exactly in exact arithmetic with the
+ * conservative advection form (and with the diffusion part of Eq. che in
+ * either form); FP32 rounding of phi + dt L makes the integral drift.  With
+ * the compensated accumulation on, phi is held as an FP32 high/low pair and
+ * the final RK stage of each step forms phi^{n+3/2} in FP64 (about 48
+ * significant bits), while the stencils keep reading the FP32 high part.
+ * Modes: GPE2P_PHI_ACC_FP32 (off), GPE2P_PHI_ACC_COMPENSATED (on),
+ * GPE2P_PHI_ACC_AUTO (the default: switched on for the rest of the run at
+ * the first diagnostics -- gpe2p_diagnostics, the end of gpe2p_advance and
+ * every diag_every steps inside it -- at which the relative drift
+ * |int phi - int phi_0| / int |phi_0| exceeds threshold, 1e-10 by default).
+ * The drift is measured from the state set by gpe2p_init_fields.  The low
+ * part is included in gpe2p_read_fields and in the diagnostics.  FP64
+ * problems and batches ignore the policy.  The paper has no counterpart. */
+enum { GPE2P_PHI_ACC_FP32 = 0, GPE2P_PHI_ACC_COMPENSATED = 1, GPE2P_PHI_ACC_AUTO = 2 };
+int gpe2p_set_phi_accumulation(gpe2p_handle h, int mode, double threshold);
+/* The mode, whether the compensated accumulation is active, the last
+ * measured relative drift and the step at which it was switched on (-1:
+ * not switched since gpe2p_init_fields).  Any pointer may be NULL. */
+int gpe2p_phi_accumulation(gpe2p_handle h, int *mode, int *active, double *drift, long long *switched_at);
+
 /* ---- the learned surrogate ------------------------------------------- */
 /* A convolutional U-Net on the periodic 2D grid that learns to advance the
  * state over many solver steps (the paper has no learned component): levels

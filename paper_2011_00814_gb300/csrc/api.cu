@@ -58,6 +58,14 @@ struct gpe2p_ctx {
   BatchCtx* batch = nullptr;    // set for a batch of 2D instances
   double* d_dist = nullptr;     // state-distance scratch (allocated on first use)
   double* h_dist = nullptr;
+  // precision policy of the phi accumulation (FP32 problems): low part of phi
+  // when the compensated (FP64) accumulation is on; the mode; the drift
+  // threshold of the automatic switch and its reference values
+  void* phi_lo = nullptr;
+  int acc_mode = GPE2P_PHI_ACC_AUTO;
+  double drift_thr = 1e-10;
+  double int_phi0 = 0.0, abs_phi0 = 0.0, last_drift = 0.0;
+  long long switched_at = -1;
   std::string err;
 };
 
@@ -243,7 +251,6 @@ static KParams<real> kparams(const gpe2p_params& p) {
   P.w1 = (real)w1;
   P.w2 = (real)w2;
   P.w3 = (real)w3;
-  P.one_m_w0 = (real)(1.0 - w0);
   P.lap_c = (real)(6.0 / (p.dx * p.dx));
   P.grad_c = (real)(3.0 / p.dx);
   return P;
@@ -315,6 +322,7 @@ static cudaError_t enqueue_step(gpe2p_ctx* h, int cur, ProfHook* hook = nullptr)
   C.conservative = h->prm.ch_advection;
   C.acc = (real*)h->acc;
   C.phin = (const real*)h->phi;
+  C.phi_lo = (real*)h->phi_lo;
   if (C.conservative) {
     const real* u0[3] = {C.u0[0], C.u0[1], C.u0[2]};
     const real* u1[3] = {C.u1[0], C.u1[1], C.u1[2]};
@@ -540,6 +548,50 @@ extern "C" int gpe2p_create(const gpe2p_params* p, void* stream, gpe2p_handle* o
   return GPE2P_OK;
 }
 
+static size_t field_bytes(const gpe2p_ctx* h) {
+  return (size_t)h->pitch * h->prm.ny * (h->prm.dim == 3 ? h->prm.nz : 1) * h->esize;
+}
+
+static int diag_impl(gpe2p_ctx* h, gpe2p_diag* d);
+
+// the reference of the conservation drift: the integral of the stored initial
+// phi and the integral of |phi_0| (FP64, from the caller's values)
+static int drift_reference(gpe2p_ctx* h, const double* phi0) {
+  double a = 0.0;
+  for (long long q = 0; q < h->ncell; ++q) a += std::fabs(phi0[q]);
+  const double dx = h->prm.dx;
+  h->abs_phi0 = a * (h->prm.dim == 3 ? dx * dx * dx : dx * dx);
+  gpe2p_diag d{};
+  const int rc = diag_impl(h, &d);
+  if (rc != GPE2P_OK) return rc;
+  h->int_phi0 = d.int_phi;
+  h->last_drift = 0.0;
+  h->switched_at = -1;
+  return GPE2P_OK;
+}
+
+// start the compensated accumulation of phi: a zero low part; the step graphs
+// are rebuilt at the next step
+static int phi_acc_on(gpe2p_ctx* h) {
+  if (h->phi_lo || h->esize != 4) return GPE2P_OK;
+  CK(h, cudaMalloc(&h->phi_lo, field_bytes(h)), "low part of phi");
+  CK(h, cudaMemsetAsync(h->phi_lo, 0, field_bytes(h), h->stream), "low part of phi");
+  for (int c = 0; c < 2; ++c)
+    if (h->gexec[c]) { cudaGraphExecDestroy(h->gexec[c]); h->gexec[c] = nullptr; }
+  h->have_graph = false;
+  h->switched_at = h->step;
+  return GPE2P_OK;
+}
+
+// the automatic policy: switch to the compensated accumulation once the
+// relative drift of the phi integral passes the threshold
+static int phi_acc_check(gpe2p_ctx* h, const gpe2p_diag& d) {
+  if (h->esize != 4 || h->batch || !(h->abs_phi0 > 0.0)) return GPE2P_OK;
+  h->last_drift = std::fabs(d.int_phi - h->int_phi0) / h->abs_phi0;
+  if (h->acc_mode == GPE2P_PHI_ACC_AUTO && !h->phi_lo && h->last_drift > h->drift_thr) return phi_acc_on(h);
+  return GPE2P_OK;
+}
+
 template <typename real>
 static cudaError_t put_field(gpe2p_ctx* h, const double* src, void* dst, int comp) {
   const KParams<real> P = kparams<real>(h->prm);
@@ -576,9 +628,10 @@ extern "C" int gpe2p_init_fields(gpe2p_handle h, const double* phi, const double
   h->cur = 0;
   cudaError_t e = h->esize == 4 ? init_impl<float>(h, phi, u, v, w, p) : init_impl<double>(h, phi, u, v, w, p);
   if (e != cudaSuccess) return cuda_fail(h, e, "init_fields");
+  if (h->phi_lo) CK(h, cudaMemsetAsync(h->phi_lo, 0, field_bytes(h), h->stream), "init_fields");
   h->step = 0;
   h->initialized = true;
-  return GPE2P_OK;
+  return drift_reference(h, phi);
 }
 
 static int diag_impl(gpe2p_ctx* h, gpe2p_diag* d) {
@@ -587,17 +640,18 @@ static int diag_impl(gpe2p_ctx* h, gpe2p_diag* d) {
   if (h->esize == 4) {
     const KParams<float> P = kparams<float>(h->prm);
     const float* U[3] = {(float*)h->Q[cur][1], (float*)h->Q[cur][2], (float*)h->Q[cur][3]};
-    e = h->prm.dim == 2 ? launch_diag<float, 2>(P, (float*)h->Q[cur][0], U, (float*)h->phi, h->d_part, h->nblk,
-                                                h->d_out, h->stream)
-                        : launch_diag<float, 3>(P, (float*)h->Q[cur][0], U, (float*)h->phi, h->d_part, h->nblk,
-                                                h->d_out, h->stream);
+    const float* lo = (const float*)h->phi_lo;
+    e = h->prm.dim == 2 ? launch_diag<float, 2>(P, (float*)h->Q[cur][0], U, (float*)h->phi, lo, h->d_part,
+                                                h->nblk, h->d_out, h->stream)
+                        : launch_diag<float, 3>(P, (float*)h->Q[cur][0], U, (float*)h->phi, lo, h->d_part,
+                                                h->nblk, h->d_out, h->stream);
   } else {
     const KParams<double> P = kparams<double>(h->prm);
     const double* U[3] = {(double*)h->Q[cur][1], (double*)h->Q[cur][2], (double*)h->Q[cur][3]};
-    e = h->prm.dim == 2 ? launch_diag<double, 2>(P, (double*)h->Q[cur][0], U, (double*)h->phi, h->d_part,
-                                                 h->nblk, h->d_out, h->stream)
-                        : launch_diag<double, 3>(P, (double*)h->Q[cur][0], U, (double*)h->phi, h->d_part,
-                                                 h->nblk, h->d_out, h->stream);
+    e = h->prm.dim == 2 ? launch_diag<double, 2>(P, (double*)h->Q[cur][0], U, (double*)h->phi, nullptr,
+                                                 h->d_part, h->nblk, h->d_out, h->stream)
+                        : launch_diag<double, 3>(P, (double*)h->Q[cur][0], U, (double*)h->phi, nullptr,
+                                                 h->d_part, h->nblk, h->d_out, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "diagnostics");
   CK(h, cudaMemcpyAsync(h->h_out, h->d_out, 4 * sizeof(double) + sizeof(int), cudaMemcpyDeviceToHost, h->stream),
@@ -640,7 +694,9 @@ static int any_diag(gpe2p_ctx* h, gpe2p_diag* d) {
     const int rc = batch_diag(h->batch, -1, d, why);
     return rc == GPE2P_OK ? rc : fail(h, rc, why);
   }
-  return diag_impl(h, d);
+  const int rc = diag_impl(h, d);
+  if (rc != GPE2P_OK) return rc;
+  return phi_acc_check(h, *d);
 }
 
 extern "C" int gpe2p_advance(gpe2p_handle h, long long nsteps, gpe2p_diag* last) {
@@ -672,24 +728,56 @@ extern "C" int gpe2p_diagnostics(gpe2p_handle h, gpe2p_diag* out) {
   if (h->batch) return any_diag(h, out);
   if (!h->initialized) return fail(h, GPE2P_ESTATE, "diagnostics before gpe2p_init_fields");
   CK(h, cudaSetDevice(h->dev), "set device");
-  return diag_impl(h, out);
+  return any_diag(h, out);
+}
+
+extern "C" int gpe2p_set_phi_accumulation(gpe2p_handle h, int mode, double threshold) {
+  if (!h) return fail(nullptr, GPE2P_EINVAL, "handle is NULL");
+  if (h->batch) return fail(h, GPE2P_EINVAL, "a batch handle accumulates phi in its working precision");
+  if (mode != GPE2P_PHI_ACC_FP32 && mode != GPE2P_PHI_ACC_COMPENSATED && mode != GPE2P_PHI_ACC_AUTO)
+    return fail(h, GPE2P_EINVAL, "mode must be GPE2P_PHI_ACC_FP32, _COMPENSATED or _AUTO");
+  if (!(threshold > 0.0) || !std::isfinite(threshold)) return fail(h, GPE2P_EINVAL, "threshold must be positive");
+  CK(h, cudaSetDevice(h->dev), "set device");
+  h->acc_mode = mode;
+  h->drift_thr = threshold;
+  if (mode == GPE2P_PHI_ACC_COMPENSATED) return phi_acc_on(h);
+  if (mode == GPE2P_PHI_ACC_FP32 && h->phi_lo) {
+    CK(h, cudaStreamSynchronize(h->stream), "phi accumulation");
+    cudaFree(h->phi_lo);
+    h->phi_lo = nullptr;
+    for (int c = 0; c < 2; ++c)
+      if (h->gexec[c]) { cudaGraphExecDestroy(h->gexec[c]); h->gexec[c] = nullptr; }
+    h->have_graph = false;
+  }
+  return GPE2P_OK;
+}
+
+extern "C" int gpe2p_phi_accumulation(gpe2p_handle h, int* mode, int* active, double* drift,
+                                      long long* switched_at) {
+  if (!h) return fail(nullptr, GPE2P_EINVAL, "handle is NULL");
+  if (mode) *mode = h->acc_mode;
+  if (active) *active = h->phi_lo != nullptr;
+  if (drift) *drift = h->last_drift;
+  if (switched_at) *switched_at = h->switched_at;
+  return GPE2P_OK;
 }
 
 template <typename real>
-static cudaError_t get_field(gpe2p_ctx* h, const void* src, double* dst) {
+static cudaError_t get_field(gpe2p_ctx* h, const void* src, double* dst, const void* lo = nullptr) {
   cudaError_t e;
-  if (sizeof(real) == 8 && h->pitch == h->prm.nx) {
+  if (sizeof(real) == 8 && h->pitch == h->prm.nx && !lo) {
     e = cudaMemcpyAsync(dst, src, (size_t)h->ncell * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   } else {
-    e = launch_to_double<real>(kparams<real>(h->prm), (const real*)src, h->d_stage, h->ncell, h->stream);
+    e = launch_to_double<real>(kparams<real>(h->prm), (const real*)src, h->d_stage, h->ncell, h->stream,
+                               (const real*)lo);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(dst, h->d_stage, (size_t)h->ncell * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   }
   return e;
 }
 
-static cudaError_t get_any(gpe2p_ctx* h, const void* src, double* dst) {
-  return h->esize == 4 ? get_field<float>(h, src, dst) : get_field<double>(h, src, dst);
+static cudaError_t get_any(gpe2p_ctx* h, const void* src, double* dst, const void* lo = nullptr) {
+  return h->esize == 4 ? get_field<float>(h, src, dst, lo) : get_field<double>(h, src, dst, lo);
 }
 
 extern "C" int gpe2p_read_fields(gpe2p_handle h, double* phi, double* u, double* v, double* w, double* p,
@@ -701,7 +789,7 @@ extern "C" int gpe2p_read_fields(gpe2p_handle h, double* phi, double* u, double*
   double* dst[6] = {p, u, v, h->prm.dim == 3 ? w : nullptr, phi, mu};
   const void* src[6] = {h->Q[h->cur][0], h->Q[h->cur][1], h->Q[h->cur][2], h->Q[h->cur][3], h->phi, h->mu};
   for (int f = 0; f < 6; ++f)
-    if (dst[f]) CK(h, get_any(h, src[f], dst[f]), "read_fields");
+    if (dst[f]) CK(h, get_any(h, src[f], dst[f], f == 4 ? h->phi_lo : nullptr), "read_fields");
   CK(h, cudaStreamSynchronize(h->stream), "read_fields sync");
   return GPE2P_OK;
 }
@@ -823,6 +911,7 @@ extern "C" void gpe2p_destroy(gpe2p_handle h) {
   cudaSetDevice(h->dev);
   if (h->d_dist) cudaFree(h->d_dist);
   if (h->h_dist) cudaFreeHost(h->h_dist);
+  if (h->phi_lo) cudaFree(h->phi_lo);
   for (int c = 0; c < 2; ++c)
     if (h->gexec[c]) cudaGraphExecDestroy(h->gexec[c]);
   if (h->stream) cudaStreamSynchronize(h->stream);
@@ -969,6 +1058,7 @@ static int pack_any(gpe2p_handle h, int inst, PackOp op, float* t, int nch, cons
   if (op == OP_UNPACK) {
     if (h->batch) batch_mark_initialized(h->batch);
     else h->initialized = true;
+    if (!h->batch && h->phi_lo) CK(h, cudaMemsetAsync(h->phi_lo, 0, field_bytes(h), s), "unpack");
   }
   if (op == OP_DISTANCE) {
     CK(h, cudaMemcpyAsync(h->h_dist, h->d_dist + 8 * kDistanceBlocks, 8 * sizeof(double), cudaMemcpyDeviceToHost, s),

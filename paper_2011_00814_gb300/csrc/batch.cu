@@ -253,7 +253,6 @@ KParams<real> kp2(const gpe2p_params& p) {
   P.w1 = (real)(1.0 / 9.0);
   P.w2 = (real)(1.0 / 36.0);
   P.w3 = real(0);
-  P.one_m_w0 = (real)(1.0 - 4.0 / 9.0);
   P.lap_c = (real)(6.0 / (p.dx * p.dx));
   P.grad_c = (real)(3.0 / p.dx);
   return P;
@@ -657,7 +656,8 @@ static cudaError_t batch_diag_impl(BatchCtx* b, int k) {
   const BInst<real>* I = reinterpret_cast<const BInst<real>*>(b->insts_host.data());
   const int c = b->cur;
   const real* U[3] = {I[k].Q[c][1], I[k].Q[c][2], I[k].Q[c][2]};
-  return launch_diag<real, 2>(I[k].P, I[k].Q[c][0], U, I[k].phi, b->d_part, b->nblk, b->d_out, b->stream);
+  return launch_diag<real, 2>(I[k].P, I[k].Q[c][0], U, I[k].phi, nullptr, b->d_part, b->nblk, b->d_out,
+                              b->stream);
 }
 
 int batch_diag(BatchCtx* b, int k, gpe2p_diag* d, std::string& why) {

@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(NTHR) mu3d_kernel(const __grid_constant__ Maps
 #pragma unroll
       for (int dz = -1; dz <= 1; ++dz) S.r[dz + 1] = raw0 + R.slot(k + dz) * G::PE + cell0 + r * G::BX;
       const real f = S(0, 0, 0, 0);
-      m[r] = P.a4 * f * (f * f - real(1)) - P.kappa * lap_iso<real, 3, ISO>(S, P, 0);
+      m[r] = fma(P.a4 * f, fma(f, f, real(-1)), -(P.kappa * lap_iso<real, 3, ISO>(S, P, 0)));
     }
 #pragma unroll
     for (int r = 0; r < 2; ++r)

@@ -18,9 +18,15 @@ struct Shells {
   static constexpr bool s3 = ISO == 15 || ISO == 27;
 };
 
+// Eq. laplacian-iso written as sum_i w_i (f(x + e_i) - f(x)) (the same
+// operator, since the non-rest weights sum to 1 - w0): every difference
+// enters the two cells it joins with opposite signs and the same weight, so
+// the Laplacian sums to zero over a periodic grid in any precision, which
+// keeps the Cahn-Hilliard update conservative in FP32 as well
 template <typename real, int DIM, int ISO, typename T>
 __device__ __forceinline__ real lap_iso(const T& S, const KParams<real>& P, int f) {
   real s = real(0);
+  const real f0 = S(f, 0, 0, 0);
 #pragma unroll
   for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
 #pragma unroll
@@ -31,9 +37,9 @@ __device__ __forceinline__ real lap_iso(const T& S, const KParams<real>& P, int 
         if (sh == 0) continue;
         if (sh == 2 && !Shells<ISO>::s2) continue;
         if (sh == 3 && !Shells<ISO>::s3) continue;
-        s += shell_w(P, sh) * S(f, dx, dy, dz);
+        s += shell_w(P, sh) * (S(f, dx, dy, dz) - f0);
       }
-  return P.lap_c * (s - P.one_m_w0 * S(f, 0, 0, 0));
+  return P.lap_c * s;
 }
 
 // the DIM components of the isotropic gradient of staged field f
@@ -82,6 +88,7 @@ template <typename real>
 struct CHPoint {
   real uh[3];
   real pn, acc;
+  real pnl;  // low part of phi^{n+1/2} (compensated accumulation)
 };
 
 template <typename real, int DIM>
@@ -102,7 +109,10 @@ __device__ __forceinline__ void ch_point_load(const KParams<real>& P, const CHAr
     }
   }
   if (A.stage != 0) c.pn = A.phin[id];
-  if (A.scheme == 4 && A.stage >= 2) c.acc = A.acc[id];
+  c.pnl = (A.phi_lo && A.stage != 0) ? A.phi_lo[id] : real(0);
+  // RK4 stages 2-4 read the accumulated increments; with the compensated
+  // accumulation the RK2 stage 2 reads the increment of stage 1
+  if ((A.scheme == 4 && A.stage >= 2) || (A.phi_lo && A.scheme == 2 && A.stage == 2)) c.acc = A.acc[id];
 }
 
 // the CH rate of one cell: -uhat.grad(phi_s) + M lap(mu_s), or its conservative form
@@ -149,11 +159,31 @@ __device__ __forceinline__ void ch_finish(const KParams<real>& P, const CHArgs<r
   if (!A.conservative && A.compute_uh && A.stage != 0)
     for (int a = 0; a < DIM; ++a) A.uh[a][id] = c.uh[a];
   real o;
+  const bool last = A.stage == A.scheme;
+  if (A.phi_lo && last) {
+    // phi^{n+3/2} in FP64 from the high/low pair of phi^{n+1/2} and the stage
+    // increments (never from a rounded stage state), stored back as a pair:
+    // RK2 phi^n + (d1 + d2)/2, RK4 phi^n + (d1 + 2 d2 + 2 d3 + d4)/6
+    const double pn = (double)c.pn + (double)c.pnl;
+    const real d = P.dt * L;
+    double od;
+    if (A.scheme == 2) od = pn + 0.5 * ((double)c.acc + (double)d);
+    else od = pn + ((double)c.acc + (double)d) / 6.0;
+    const real hi = (real)od;
+    A.phi_lo[id] = (real)(od - (double)hi);
+    A.out[id] = hi;
+    return;
+  }
   if (A.stage == 0) {
     o = L;
   } else if (A.scheme == 2) {
-    if (A.stage == 1) o = c.pn + P.dt * L;
-    else o = real(0.5) * c.pn + real(0.5) * (phis0 + P.dt * L);
+    // explicit fused multiply-adds: the kernels that share this code round alike
+    if (A.stage == 1) {
+      o = fma(P.dt, L, c.pn);
+      if (A.phi_lo) A.acc[id] = P.dt * L;
+    } else {
+      o = fma(real(0.5), c.pn, real(0.5) * fma(P.dt, L, phis0));
+    }
   } else {
     const real d = P.dt * L;
     const real pn = c.pn;
@@ -226,7 +256,7 @@ __device__ __forceinline__ void mu2d_tile(const KParams<real>& P, const real* __
     S.sm = sm;
     S.c = (ty + 1) * SXv + (tx + 1);
     const real f = S(0, 0, 0, 0);
-    mu[lin(P, i, j, 0)] = P.a4 * f * (f * f - real(1)) - P.kappa * lap_iso<real, 2, 9>(S, P, 0);
+    mu[lin(P, i, j, 0)] = fma(P.a4 * f, fma(f, f, real(-1)), -(P.kappa * lap_iso<real, 2, 9>(S, P, 0)));
   }
   __syncthreads();
 }

@@ -28,7 +28,7 @@ template <typename real, int DIM>
 __global__ void __launch_bounds__(DIAG_THREADS) diag_partial_kernel(const KParams<real> P, const real* p,
                                                                     const real* u0, const real* u1,
                                                                     const real* u2, const real* phi,
-                                                                    double* partial) {
+                                                                    const real* phi_lo, double* partial) {
   const long long n = (long long)P.n[0] * P.n[1] * P.n[2];
   double sphi = 0.0, ke = 0.0, umax = 0.0, bad = 0.0;
   const real* U[3] = {u0, u1, u2};
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_partial_kernel(const KParam
     const int j = (int)((id / P.n[0]) % P.n[1]);
     const int k = (int)(id / ((long long)P.n[0] * P.n[1]));
     const long long q = lin(P, i, j, k);
-    const double f = (double)phi[q];
+    const double f = (double)phi[q] + (phi_lo ? (double)phi_lo[q] : 0.0);
     sphi += f;
     if (!isfinite(f) || !isfinite((double)p[q])) bad = 1.0;
     const double rho0 = 0.5 * ((double)P.rhoL * (1.0 + f) + (double)P.rhoG * (1.0 - f));
@@ -113,10 +113,10 @@ __global__ void diag_final_kernel(const double* partial, int nblocks, double vol
 
 template <typename real, int DIM>
 cudaError_t launch_diag(const KParams<real>& P, const real* p, const real* const U[3], const real* phi,
-                        double* partial, int nblocks, double* out, cudaStream_t s) {
+                        const real* phi_lo, double* partial, int nblocks, double* out, cudaStream_t s) {
   const double dx = 1.0 / (double)P.inv_dx;
   const double vol = DIM == 3 ? dx * dx * dx : dx * dx;
-  diag_partial_kernel<real, DIM><<<nblocks, DIAG_THREADS, 0, s>>>(P, p, U[0], U[1], U[2], phi, partial);
+  diag_partial_kernel<real, DIM><<<nblocks, DIAG_THREADS, 0, s>>>(P, p, U[0], U[1], U[2], phi, phi_lo, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   diag_final_kernel<<<1, DIAG_THREADS, 0, s>>>(partial, nblocks, vol, out);
@@ -140,15 +140,16 @@ __global__ void from_double_kernel(const KParams<real> P, const double* src, rea
   }
 }
 
-// padded rows -> dense FP64
+// padded rows -> dense FP64 (plus a low part, when given)
 template <typename real>
-__global__ void to_double_kernel(const KParams<real> P, const real* src, double* dst, long long n) {
+__global__ void to_double_kernel(const KParams<real> P, const real* src, double* dst, long long n, const real* lo) {
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
        id += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(id % P.n[0]);
     const int j = (int)((id / P.n[0]) % P.n[1]);
     const int k = (int)(id / ((long long)P.n[0] * P.n[1]));
-    dst[id] = (double)src[lin(P, i, j, k)];
+    const long long q = lin(P, i, j, k);
+    dst[id] = (double)src[q] + (lo ? (double)lo[q] : 0.0);
   }
 }
 
@@ -167,26 +168,27 @@ cudaError_t launch_from_double(const KParams<real>& P, const double* src, real* 
 }
 
 template <typename real>
-cudaError_t launch_to_double(const KParams<real>& P, const real* src, double* dst, long long n, cudaStream_t s) {
-  to_double_kernel<real><<<grid_for(n), 256, 0, s>>>(P, src, dst, n);
+cudaError_t launch_to_double(const KParams<real>& P, const real* src, double* dst, long long n, cudaStream_t s,
+                             const real* lo) {
+  to_double_kernel<real><<<grid_for(n), 256, 0, s>>>(P, src, dst, n, lo);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_diag<float, 2>(const KParams<float>&, const float*, const float* const[3],
-                                           const float*, double*, int, double*, cudaStream_t);
+                                           const float*, const float*, double*, int, double*, cudaStream_t);
 template cudaError_t launch_diag<float, 3>(const KParams<float>&, const float*, const float* const[3],
-                                           const float*, double*, int, double*, cudaStream_t);
+                                           const float*, const float*, double*, int, double*, cudaStream_t);
 template cudaError_t launch_diag<double, 2>(const KParams<double>&, const double*, const double* const[3],
-                                            const double*, double*, int, double*, cudaStream_t);
+                                            const double*, const double*, double*, int, double*, cudaStream_t);
 template cudaError_t launch_diag<double, 3>(const KParams<double>&, const double*, const double* const[3],
-                                            const double*, double*, int, double*, cudaStream_t);
+                                            const double*, const double*, double*, int, double*, cudaStream_t);
 template cudaError_t launch_from_double<float>(const KParams<float>&, const double*, float*, int, long long,
                                                cudaStream_t);
 template cudaError_t launch_from_double<double>(const KParams<double>&, const double*, double*, int,
                                                 long long, cudaStream_t);
 template cudaError_t launch_to_double<float>(const KParams<float>&, const float*, double*, long long,
-                                             cudaStream_t);
+                                             cudaStream_t, const float*);
 template cudaError_t launch_to_double<double>(const KParams<double>&, const double*, double*, long long,
-                                              cudaStream_t);
+                                              cudaStream_t, const double*);
 
 }  // namespace gpe2p

@@ -35,7 +35,6 @@ struct KParams {
   int bulk, pavg;
   // isotropic stencils (Eqs. 1st-der-iso, laplacian-iso)
   real w1, w2, w3;     // weights of the shells |e|^2 = 1, 2, 3 (0 if absent)
-  real one_m_w0;       // 1 - w0
   real lap_c, grad_c;  // 6/dx^2 and 3/dx
 };
 

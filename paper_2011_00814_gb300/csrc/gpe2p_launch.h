@@ -41,6 +41,9 @@ struct CHArgs {
   int stage;           // 1..scheme; 0 = write the rate L only
   int compute_uh;      // 1: build uhat (Eq. u-center-2d) from u0, u1 and store it
   int conservative;    // 1: -div(uhat phi) instead of -uhat.grad(phi)
+  // low part of phi^{n+1/2} (phi = phin + phi_lo): when set, the final stage
+  // forms phi^{n+3/2} in FP64 and stores it back as this high/low pair
+  real* phi_lo = nullptr;
 };
 
 // 3D launches read their haloed inputs through TMA tensor maps (one per
@@ -69,6 +72,7 @@ cudaError_t launch_center_velocity(const KParams<real>& P, const real* const u0[
 // 4 * nblocks doubles.
 template <typename real, int DIM>
 cudaError_t launch_diag(const KParams<real>& P, const real* p, const real* const U[3], const real* phi,
+                        const real* phi_lo,
                         double* partial, int nblocks, double* out, cudaStream_t s);
 
 // FP64 <-> working precision copies with the wall faces of component c zeroed (c < 0: none)
@@ -76,7 +80,8 @@ template <typename real>
 cudaError_t launch_from_double(const KParams<real>& P, const double* src, real* dst, int c, long long n,
                                cudaStream_t s);
 template <typename real>
-cudaError_t launch_to_double(const KParams<real>& P, const real* src, double* dst, long long n, cudaStream_t s);
+cudaError_t launch_to_double(const KParams<real>& P, const real* src, double* dst, long long n, cudaStream_t s,
+                             const real* lo = nullptr);
 
 // 2D state <-> network tensor [ny][nx][nch] (phi, u, v, p[, rho/rho_L]); see pack.cu
 constexpr int kDistanceBlocks = 304;

@@ -119,6 +119,9 @@ def lib():
         L.gpe2p_state_distance.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, fp, fp,
                                            ctypes.POINTER(ctypes.c_double)]
         L.gpe2p_state_distance.restype = ctypes.c_int
+        L.gpe2p_set_phi_accumulation.argtypes = [vp, ctypes.c_int, ctypes.c_double]
+        L.gpe2p_phi_accumulation.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
         L.gpe2p_last_error.argtypes = [vp]
         L.gpe2p_last_error.restype = ctypes.c_char_p
         L.gpe2p_destroy.argtypes = [vp]
@@ -190,6 +193,9 @@ def _tensor_call(obj, op, inst, tensor, mean, scale):
         out = (ctypes.c_double * 8)()
         obj._check(L.gpe2p_state_distance(obj.h, int(inst), ctypes.c_void_p(ptr), nch, m, s, out))
         return list(out)
+
+
+PHI_ACC_FP32, PHI_ACC_COMPENSATED, PHI_ACC_AUTO = 0, 1, 2
 
 
 class Solver:
@@ -265,6 +271,16 @@ class Solver:
         self._check(lib().gpe2p_profile_steps(self.h, int(nsteps), ms, 64, ctypes.byref(n), names, 2048))
         nm = names.value.decode().split(",")
         return [(nm[i], ms[i]) for i in range(n.value)]
+
+    def set_phi_accumulation(self, mode: int, threshold: float = 1e-10):
+        """PHI_ACC_FP32, PHI_ACC_COMPENSATED or PHI_ACC_AUTO (see gpe2p_set_phi_accumulation)."""
+        self._check(lib().gpe2p_set_phi_accumulation(self.h, int(mode), float(threshold)))
+
+    def phi_accumulation(self) -> dict:
+        m, a, d, sw = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_longlong()
+        self._check(lib().gpe2p_phi_accumulation(self.h, ctypes.byref(m), ctypes.byref(a), ctypes.byref(d),
+                                                 ctypes.byref(sw)))
+        return {"mode": m.value, "active": bool(a.value), "drift": d.value, "switched_at": sw.value}
 
     def pack(self, tensor, mean=None, scale=None):
         """State -> tensor [ny, nx, nch] (phi, u, v, p[, rho/rho_L]), normalised."""

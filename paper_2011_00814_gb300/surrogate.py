@@ -391,7 +391,9 @@ def compare_to_solver(sur: Surrogate, prm, fields, calls: int, check_every: int 
         e1.synchronize()
         return e0.elapsed_time(e1), out
 
+    # both solvers accumulate phi in plain FP32 (the baseline is the plain FP32 solver)
     with gpe2p.Solver(prm, stream=sur.stream) as ref:
+        ref.set_phi_accumulation(gpe2p.PHI_ACC_FP32)
         ref.init_fields(fields)
         ref.advance(1)                                       # graphs built outside the timing
         best = float("inf")
@@ -402,6 +404,7 @@ def compare_to_solver(sur: Surrogate, prm, fields, calls: int, check_every: int 
         res["solver_ms"] = best
         phi_ref = ref.read_fields()["phi"]
     with gpe2p.Solver(prm, stream=sur.stream) as s:
+        s.set_phi_accumulation(gpe2p.PHI_ACC_FP32)
         s.init_fields(fields)
         s.advance(1)
         best, stats = float("inf"), None

@@ -118,6 +118,8 @@ def test_invalid_parameters_are_rejected_on_the_host(lib, bad):
 
 
 def test_null_arguments_do_not_crash(lib):
+    assert lib.gpe2p_set_phi_accumulation(None, gpe2p.PHI_ACC_AUTO, 1e-10) == gpe2p.EINVAL
+    assert lib.gpe2p_phi_accumulation(None, None, None, None, None) == gpe2p.EINVAL
     assert lib.gpe2p_step(None) == gpe2p.EINVAL
     assert lib.gpe2p_advance(None, 1, None) == gpe2p.EINVAL
     assert lib.gpe2p_read_fields(None, None, None, None, None, None, None) == gpe2p.EINVAL

@@ -64,6 +64,10 @@ def test_unpack_round_trip_and_mu():
     prm, f = _state(32)
     t = torch.empty((64, 64, 5), dtype=torch.float32, device="cuda")
     with gpe2p.Solver(prm) as a, gpe2p.Solver(prm) as b:
+        # the same accumulation policy on both (the automatic switch follows the
+        # drift since gpe2p_init_fields, which only `a` has)
+        a.set_phi_accumulation(gpe2p.PHI_ACC_FP32)
+        b.set_phi_accumulation(gpe2p.PHI_ACC_FP32)
         a.init_fields(f)
         a.advance(5)
         a.pack(t)
