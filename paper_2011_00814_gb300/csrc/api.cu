@@ -555,12 +555,9 @@ static size_t field_bytes(const gpe2p_ctx* h) {
 static int diag_impl(gpe2p_ctx* h, gpe2p_diag* d);
 
 // the reference of the conservation drift: the integral of the stored initial
-// phi and the integral of |phi_0| (FP64, from the caller's values)
-static int drift_reference(gpe2p_ctx* h, const double* phi0) {
-  double a = 0.0;
-  for (long long q = 0; q < h->ncell; ++q) a += std::fabs(phi0[q]);
-  const double dx = h->prm.dx;
-  h->abs_phi0 = a * (h->prm.dim == 3 ? dx * dx * dx : dx * dx);
+// phi (the integral of |phi_0| is taken by init_fields)
+static int drift_reference(gpe2p_ctx* h) {
+  if (h->esize != 4) return GPE2P_OK;  // FP64 problems ignore the policy
   gpe2p_diag d{};
   const int rc = diag_impl(h, &d);
   if (rc != GPE2P_OK) return rc;
@@ -609,6 +606,12 @@ static cudaError_t init_impl(gpe2p_ctx* h, const double* phi, const double* u, c
   for (int f = 0; f < 1 + h->prm.dim; ++f)
     if ((e = put_field<real>(h, src[f], h->Q[0][f], f - 1)) != cudaSuccess) return e;
   if ((e = put_field<real>(h, phi, h->phi, -1)) != cudaSuccess) return e;
+  // the integral of |phi_0| (reference of the conservation drift) from the FP64 staging copy
+  const double dx = h->prm.dx, vol = h->prm.dim == 3 ? dx * dx * dx : dx * dx;
+  if ((e = launch_abs_sum(h->d_stage, h->ncell, h->d_part, h->nblk, vol, h->d_out, h->stream)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(h->h_out, h->d_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+    return e;
   const KParams<real> P = kparams<real>(h->prm);
   if (h->prm.dim == 2)
     e = launch_mu<real, 2>(P, (real*)h->phi, (real*)h->mu, h->prm.iso, h->kchunk, h->stream, nullptr, h->d_err);
@@ -631,7 +634,8 @@ extern "C" int gpe2p_init_fields(gpe2p_handle h, const double* phi, const double
   if (h->phi_lo) CK(h, cudaMemsetAsync(h->phi_lo, 0, field_bytes(h), h->stream), "init_fields");
   h->step = 0;
   h->initialized = true;
-  return drift_reference(h, phi);
+  h->abs_phi0 = h->h_out[0];
+  return drift_reference(h);
 }
 
 static int diag_impl(gpe2p_ctx* h, gpe2p_diag* d) {

@@ -123,6 +123,37 @@ cudaError_t launch_diag(const KParams<real>& P, const real* p, const real* const
   return cudaGetLastError();
 }
 
+// sum of |x| over a dense FP64 array, block partials in slot 0 of 4 (the
+// layout diag_final_kernel reduces)
+__global__ void __launch_bounds__(DIAG_THREADS) abs_sum_partial_kernel(const double* x, long long n,
+                                                                       double* partial) {
+  double s = 0.0;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
+       id += (long long)gridDim.x * blockDim.x)
+    s += fabs(x[id]);
+  __shared__ double red[DIAG_THREADS / 32];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < DIAG_THREADS / 32; ++w) a += red[w];
+    partial[4 * blockIdx.x + 0] = a;
+    partial[4 * blockIdx.x + 1] = 0.0;
+    partial[4 * blockIdx.x + 2] = 0.0;
+    partial[4 * blockIdx.x + 3] = 0.0;
+  }
+}
+
+cudaError_t launch_abs_sum(const double* x, long long n, double* partial, int nblocks, double vol, double* out,
+                           cudaStream_t s) {
+  abs_sum_partial_kernel<<<nblocks, DIAG_THREADS, 0, s>>>(x, n, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  diag_final_kernel<<<1, DIAG_THREADS, 0, s>>>(partial, nblocks, vol, out);
+  return cudaGetLastError();
+}
+
 // dense FP64 (host layout) -> padded rows in the working precision
 template <typename real>
 __global__ void from_double_kernel(const KParams<real> P, const double* src, real* dst, int c, long long n) {

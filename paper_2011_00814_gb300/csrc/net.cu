@@ -51,6 +51,11 @@ struct gpe2p_net {
   float *P = nullptr, *G = nullptr, *Am = nullptr, *Av = nullptr;
   long long adam_t = 0;
   int use_tc = 1;                // 3x3 forward / data gradient on tcgen05
+  // the inference forward captured in a CUDA graph for one (x, y, batch)
+  cudaGraphExec_t fwd_exec = nullptr;
+  const float* fwd_x = nullptr;
+  float* fwd_y = nullptr;
+  int fwd_b = 0;
   int* d_err = nullptr;          // device error word of the tcgen05 kernels
   int* h_err = nullptr;          // pinned copy
   Norm norm{};
@@ -64,6 +69,8 @@ struct gpe2p_net {
   std::vector<void*> allocs;
   std::string err;
 };
+
+static void drop_forward_graph(gpe2p_net* n);
 
 static int net_fail(gpe2p_net* n, int code, const std::string& m) {
   if (n) n->err = m;
@@ -403,6 +410,7 @@ extern "C" int gpe2p_net_set_normalization(gpe2p_net_handle n, const float* in_m
   }
   nm.residual = residual;
   n->norm = nm;
+  drop_forward_graph(n);
   return GPE2P_OK;
 }
 
@@ -422,6 +430,7 @@ extern "C" int gpe2p_net_sync(gpe2p_net_handle n) {
 extern "C" int gpe2p_net_set_backend(gpe2p_net_handle n, int tcgen05) {
   if (!n || (tcgen05 != 0 && tcgen05 != 1)) return net_fail(n, GPE2P_EINVAL, "bad arguments");
   n->use_tc = tcgen05;
+  drop_forward_graph(n);
   return GPE2P_OK;
 }
 
@@ -445,12 +454,44 @@ extern "C" int gpe2p_net_set_params(gpe2p_net_handle n, const float* host, long 
   return GPE2P_OK;
 }
 
+static void drop_forward_graph(gpe2p_net* n) {
+  if (n->fwd_exec) cudaGraphExecDestroy(n->fwd_exec);
+  n->fwd_exec = nullptr;
+  n->fwd_x = nullptr;
+  n->fwd_y = nullptr;
+  n->fwd_b = 0;
+}
+
+static cudaError_t enqueue_forward(gpe2p_net* n, const float* x, float* y, int batch) {
+  cudaError_t e = forward(n, x, batch, false);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(y, n->out, (size_t)npix_at(n, 0, batch) * n->out_ch * sizeof(float),
+                         cudaMemcpyDeviceToDevice, n->stream);
+}
+
+// The forward of a given (x, y, batch) is captured once into a CUDA graph and
+// replayed by later calls with the same arguments (the weights are read from
+// device memory, so training between calls needs no new capture).
 extern "C" int gpe2p_net_forward(gpe2p_net_handle n, const float* x, float* y, int batch) {
   if (!n || !x || !y || batch < 1 || batch > n->maxB) return net_fail(n, GPE2P_EINVAL, "bad arguments");
-  NK(n, forward(n, x, batch, false), "forward");
-  NK(n, cudaMemcpyAsync(y, n->out, (size_t)npix_at(n, 0, batch) * n->out_ch * sizeof(float), cudaMemcpyDeviceToDevice,
-                        n->stream),
-     "forward copy");
+  if (!(n->fwd_exec && n->fwd_x == x && n->fwd_y == y && n->fwd_b == batch)) {
+    drop_forward_graph(n);
+    cudaGraph_t g = nullptr;
+    NK(n, cudaStreamBeginCapture(n->stream, cudaStreamCaptureModeRelaxed), "forward capture");
+    const cudaError_t e = enqueue_forward(n, x, y, batch);
+    const cudaError_t e2 = cudaStreamEndCapture(n->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      NK(n, e != cudaSuccess ? e : e2, "forward capture");
+    }
+    const cudaError_t e3 = cudaGraphInstantiate(&n->fwd_exec, g, 0);
+    cudaGraphDestroy(g);
+    NK(n, e3, "forward graph");
+    n->fwd_x = x;
+    n->fwd_y = y;
+    n->fwd_b = batch;
+  }
+  NK(n, cudaGraphLaunch(n->fwd_exec, n->stream), "forward");
   return GPE2P_OK;
 }
 
@@ -508,6 +549,7 @@ extern "C" const char* gpe2p_net_last_error(gpe2p_net_handle n) { return n ? n->
 extern "C" void gpe2p_net_destroy(gpe2p_net_handle n) {
   if (!n) return;
   if (n->stream) cudaStreamSynchronize(n->stream);
+  drop_forward_graph(n);
   for (void* p : n->allocs) cudaFree(p);
   if (n->loss_h) cudaFreeHost(n->loss_h);
   if (n->h_err) cudaFreeHost(n->h_err);

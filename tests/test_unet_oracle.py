@@ -75,3 +75,19 @@ def test_gradient_matches_finite_differences(levels, channels):
         lm, _ = unet.loss_and_gradient(p - e, x, t, levels, channels, in_ch, out_ch)
         fd = (lp - lm) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])) + 1e-8, (i, fd, g[i])
+
+
+def test_adam_first_steps_closed_form():
+    """Bias-corrected Adam: at t = 1 each weight moves by lr g / (|g| + eps);
+    with a constant gradient every step moves by lr g / (|g| + eps) too,
+    since both corrected moments equal g and g^2."""
+    rng = np.random.default_rng(5)
+    w0 = rng.normal(size=50)
+    g = rng.normal(size=50)
+    lr, eps = 1e-3, 1e-8
+    w, m, v = unet.adam_step(w0, g, 0.0, 0.0, 1, lr, eps=eps)
+    assert np.allclose(w, w0 - lr * g / (np.abs(g) + eps), rtol=0, atol=1e-15)
+    for t in range(2, 6):
+        w_prev = w
+        w, m, v = unet.adam_step(w, g, m, v, t, lr, eps=eps)
+        assert np.allclose(w - w_prev, -lr * g / (np.abs(g) + eps), rtol=1e-12, atol=1e-15)
