@@ -242,6 +242,10 @@ KParams<real> kp2(const gpe2p_params& p) {
   P.rhoG = (real)p.rhoG;
   P.etaL = (real)p.etaL;
   P.etaG = (real)p.etaG;
+  P.rho_m = (real)(0.5 * (p.rhoL + p.rhoG));
+  P.rho_d = (real)(0.5 * (p.rhoL - p.rhoG));
+  P.eta_m = (real)(0.5 * (p.etaL + p.etaG));
+  P.eta_d = (real)(0.5 * (p.etaL - p.etaG));
   P.rho_ref = (real)p.rho_ref;
   P.sigma = (real)p.sigma;
   P.M = (real)p.M;

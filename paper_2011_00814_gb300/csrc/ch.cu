@@ -177,8 +177,13 @@ __global__ void __launch_bounds__(NTHR) mu3d_kernel(const __grid_constant__ Maps
   }
 }
 
+// plane slots of the CH and mu rings (power of two): more slots keep more TMA
+// copies in flight, fewer leave shared memory for more resident blocks
+#ifndef GPE2P_CH_RING
+#define GPE2P_CH_RING 4
+#endif
 template <typename real>
-constexpr int ch_ring() { return 8; }
+constexpr int ch_ring() { return GPE2P_CH_RING; }
 
 template <typename real, int DIM>
 __global__ void center_velocity_kernel(const KParams<real> P, const real* u00, const real* u01,

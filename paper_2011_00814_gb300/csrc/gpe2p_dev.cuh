@@ -30,6 +30,7 @@ struct KParams {
   long long sy, sz;    // element strides of y and z
   real dt, inv_dx, inv_dx2, inv_2dx, cs2;
   real rhoL, rhoG, etaL, etaG, rho_ref;
+  real rho_m, rho_d, eta_m, eta_d;  // (L + G)/2 and (L - G)/2 of density and viscosity
   real sigma, M, a4, kappa;  // a4 = 4a with a = 3/(4W); kappa = 3W/8
   real g[3];
   int bulk, pavg;
@@ -112,13 +113,15 @@ __device__ __forceinline__ real ld_cvec(const real* __restrict__ f, const KParam
 // material laws, Eq. density-viscosity-op-two-phase
 // ---------------------------------------------------------------------------
 
+// both laws are linear in phi, (1 + phi)/2 L + (1 - phi)/2 G = (L + G)/2 + phi (L - G)/2,
+// evaluated as one fused multiply-add with the two coefficients formed on the host
 template <typename real>
 __device__ __forceinline__ real rho_of(const KParams<real>& P, real phi) {
-  return real(0.5) * (P.rhoL * (real(1) + phi) + P.rhoG * (real(1) - phi));
+  return fma(P.rho_d, phi, P.rho_m);
 }
 template <typename real>
 __device__ __forceinline__ real eta_of(const KParams<real>& P, real phi) {
-  return real(0.5) * (P.etaL * (real(1) + phi) + P.etaG * (real(1) - phi));
+  return fma(P.eta_d, phi, P.eta_m);
 }
 
 // division: the FP32 path uses the fast approximate quotient (2 ulp), the
