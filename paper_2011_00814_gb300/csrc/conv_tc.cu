@@ -334,7 +334,6 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, int ti
 template <int MODE, int BN>
 cudaError_t launch_tc(const ConvArgs& a, int tiles_x, int tiles_y, int ntiles, int nout, cudaStream_t s) {
   static int attr_set = 0;
-  static int occ_res = 0, occ_str = 0;
   auto k = conv3_tc_kernel<MODE, BN>;
   cudaError_t e;
   if (!attr_set) {
@@ -342,19 +341,21 @@ cudaError_t launch_tc(const ConvArgs& a, int tiles_x, int tiles_y, int ntiles, i
     attr_set = 1;
   }
   const int nch = (MODE == 0 ? a.cin : a.cout) / KC;
-  const bool resident = smem_bytes(BN, nch, true) <= SMEM_MAX;
-  const int smem = smem_bytes(BN, nch, resident);
-  int occ = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, NTHR, smem)) != cudaSuccess) return e;
-  (void)occ_res;
-  (void)occ_str;
-  if (occ < 1) occ = 1;
-  // tensor memory: at most 512 columns per SM
-  const int tc_occ = 512 / Cfg<BN>::TCOLS;
-  if (occ > tc_occ) occ = tc_occ;
-  int dev = 0, nsm = 152;
+  // resident CTAs per SM, from the SM's shared memory (with the per-block
+  // reservation), its 512 tensor-memory columns and its 2048 threads; the
+  // weights stay resident in shared memory only if that leaves two CTAs per SM
+  int dev = 0, nsm = 152, sm_smem = 233472, reserved = 1024;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  const int smem_res = smem_bytes(BN, nch, true);
+  const bool resident = smem_res <= SMEM_MAX && sm_smem / (smem_res + reserved) >= 2;
+  const int smem = smem_bytes(BN, nch, resident);
+  int occ = sm_smem / (smem + reserved);
+  if (occ > 512 / Cfg<BN>::TCOLS) occ = 512 / Cfg<BN>::TCOLS;
+  if (occ > 2048 / NTHR) occ = 2048 / NTHR;
+  if (occ < 1) occ = 1;
   const int nblk_n = nout / BN;
   long long gx = ((long long)occ * nsm + nblk_n - 1) / nblk_n;
   if (gx > ntiles) gx = ntiles;
