@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(NTHR) ch3d_kernel(const __grid_constant__ Maps
     for (int r = 0; r < 2; ++r)
       if (act[r]) ch_point_load<real, 3>(P, A, i, ja + r, k, c[r]);
     if (!ring_acquire(R, P, maps.m, k + 1, true, edge_tile, fix)) { R.fail(err, k + 1); return; }
-    __syncthreads();
+    if (edge_tile || k + 1 >= P.n[2]) __syncthreads();  // out-of-domain writes seen by all
     real L[2], ph0[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(NTHR) mu3d_kernel(const __grid_constant__ Maps
   const int raw0 = (int)(R.raw - smr), cell0 = G::at(tx + 1, 2 * ty + 1);
   for (int k = kbeg; k < kend; ++k) {
     if (!ring_acquire(R, P, maps.m, k + 1, true, edge_tile, fix)) { R.fail(err, k + 1); return; }
-    __syncthreads();
+    if (edge_tile || k + 1 >= P.n[2]) __syncthreads();  // out-of-domain writes seen by all
     real m[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {

@@ -141,7 +141,10 @@ __global__ void __launch_bounds__(NTHR, GPE2P_FLOW_MINB) flow3d_kernel(const __g
         }
     }
     if (!acquire(k + 1, true)) { R.fail(err, k + 1); return; }
-    __syncthreads();
+    // the threads' writes of out-of-domain cells must be seen by all before the
+    // stencil reads them; a plane that needed none is visible to every thread
+    // after its own wait on the plane's barrier
+    if (edge_tile || k + 1 >= nz) __syncthreads();
     using Ops = FlowOps<real, 3, RingTile<real, PAVG>>;
     real out[2][4];
 #pragma unroll
