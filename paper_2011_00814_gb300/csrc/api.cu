@@ -51,7 +51,9 @@ struct gpe2p_ctx {
   Maps<1> mu_maps[3];           // phi, phis0, phis1
   int cur = 0;                  // which Q set holds q^n (0 or 1)
   long long step = 0;
-  int kchunk = 8;
+  int kchunk = 8;                // z-chunk of the flow stage
+  int kchunk_ch = 8;             // ... of the CH stage
+  int kchunk_mu = 8;             // ... of mu
   bool initialized = false;
   bool have_graph = false;
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -342,11 +344,11 @@ static cudaError_t enqueue_step(gpe2p_ctx* h, int cur, ProfHook* hook = nullptr)
   const int iso = h->prm.iso;
   auto ch = [&](const real* phis) {
     const int mi = phis == phi ? 0 : (phis == F0 ? 1 : 2);
-    return launch_ch_stage<real, DIM>(P, C, iso, h->kchunk, s, &h->ch_maps[mi], h->d_err);
+    return launch_ch_stage<real, DIM>(P, C, iso, h->kchunk_ch, s, &h->ch_maps[mi], h->d_err);
   };
   auto mu_of = [&](const real* f, real* out) {
     const int mi = f == phi ? 0 : (f == F0 ? 1 : 2);
-    return launch_mu<real, DIM>(P, f, out, iso, h->kchunk, s, &h->mu_maps[mi], h->d_err);
+    return launch_mu<real, DIM>(P, f, out, iso, h->kchunk_mu, s, &h->mu_maps[mi], h->d_err);
   };
   if (C.scheme == 2) {
     C.stage = 1; C.phis = phi; C.mus = mu; C.out = F0; C.compute_uh = !C.conservative;
@@ -537,16 +539,30 @@ extern "C" int gpe2p_create(const gpe2p_params* p, void* stream, gpe2p_handle* o
       return fail(nullptr, rc, why);
     }
   }
-  // z-chunk of the marching kernels: enough blocks to fill the GPU a few times
+  // z-chunks of the marching kernels: a block marches kc planes after a
+  // prologue of two, and the blocks run in waves of the resident slots; take
+  // the kc in [4, 64] that minimises waves x (kc + 2), the time of the slowest
+  // SM.  Resident blocks per SM (registers and shared memory, as ncu reports
+  // them): flow stage 2, CH stage 5, mu 8.
   if (h->prm.dim == 3) {
     const long long bxy = (long long)((h->prm.nx + TX - 1) / TX) * ((h->prm.ny + K3_TY - 1) / K3_TY);
-    long long zch = (152LL * 6 + bxy - 1) / bxy;
-    long long kc = (h->prm.nz + zch - 1) / zch;
-    if (kc < 4) kc = 4;
-    if (kc > h->prm.nz) kc = h->prm.nz;
-    h->kchunk = (int)kc;
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev);
+    auto pick = [&](int per_sm) {
+      const long long slots = (long long)per_sm * nsm;
+      long long best_kc = 4, best = -1;
+      for (long long kc = 4; kc <= 64 && kc <= h->prm.nz; ++kc) {
+        const long long nb = bxy * ((h->prm.nz + kc - 1) / kc);
+        const long long cost = ((nb + slots - 1) / slots) * (kc + 2);
+        if (best < 0 || cost < best) { best = cost; best_kc = kc; }
+      }
+      return (int)(best_kc > h->prm.nz ? h->prm.nz : best_kc);
+    };
+    h->kchunk = pick(2);
+    h->kchunk_ch = pick(5);
+    h->kchunk_mu = pick(8);
   } else {
-    h->kchunk = 1;
+    h->kchunk = h->kchunk_ch = h->kchunk_mu = 1;
   }
   *out = h;
   return GPE2P_OK;
@@ -620,7 +636,7 @@ static cudaError_t init_impl(gpe2p_ctx* h, const double* phi, const double* u, c
   if (h->prm.dim == 2)
     e = launch_mu<real, 2>(P, (real*)h->phi, (real*)h->mu, h->prm.iso, h->kchunk, h->stream, nullptr, h->d_err);
   else
-    e = launch_mu<real, 3>(P, (real*)h->phi, (real*)h->mu, h->prm.iso, h->kchunk, h->stream, &h->mu_maps[0],
+    e = launch_mu<real, 3>(P, (real*)h->phi, (real*)h->mu, h->prm.iso, h->kchunk_mu, h->stream, &h->mu_maps[0],
                            h->d_err);
   if (e != cudaSuccess) return e;
   return cudaStreamSynchronize(h->stream);
@@ -835,7 +851,7 @@ static cudaError_t rates_impl(gpe2p_ctx* h) {
   C.mus = (const real*)h->mu;
   C.phin = (const real*)h->phi;
   C.out = (real*)h->phis[0];
-  return launch_ch_stage<real, DIM>(P, C, h->prm.iso, h->kchunk, h->stream, &h->ch_maps[0], h->d_err);
+  return launch_ch_stage<real, DIM>(P, C, h->prm.iso, h->kchunk_ch, h->stream, &h->ch_maps[0], h->d_err);
 }
 
 extern "C" int gpe2p_eval_rates(gpe2p_handle h, double* Lp, double* Lu, double* Lv, double* Lw, double* Lphi) {
