@@ -281,3 +281,35 @@ def two_drops(seed: int, n: int = 256, gap=(2.0, 8.0), precision: int = 32):
 
     f["phi"] = np.maximum(np.tanh(2.0 * (R1 - pdist(c1)) / W), np.tanh(2.0 * (R2 - pdist(c2)) / W))
     return prm, f
+
+
+def capillary_wave(n: int = 64, nt: int = 384, cn: float = 0.0625, pe: float = 2.0e4, precision: int = 64):
+    """The 2D capillary wave of Sec. "Capillary wave in 2D", on the lower half
+    of the unit square (the wave is symmetric about y = 1/2).
+
+    L_c = 1 and U_c = sigma / eta_L = 1, so T_c = 1; Re = rho_L U_c L_c /
+    eta_L = 1000 gives eta_L = sigma = 10^-3; r_rho = r_eta = 20 (rho_L = 1,
+    equal kinematic viscosities); Cn = W / L_c = 0.0625; Pe = U_c L_c^2 / (M
+    sigma_ref) = 2 10^4 with the reference surface tension sigma_ref = 1 of
+    the chemical potential gives M = 5 10^-5.  dx = 1/n, dt = T_c / nt and c_s = nt /
+    (sqrt(3) n) U_c (the paper's N_L = 64, N_t = 384, c = 6).  x in [0, 1]
+    between no-slip walls; y in [0, 1/2] between symmetry planes (free-slip
+    walls).  Gas on the left, liquid on the right: phi = tanh(2 (x - h(y)) /
+    Cn), h(y) = 1/2 + 0.01 cos(2 pi (y + 1/2)).  u = v = p = 0.  The fine
+    mesh of the paper's refinement study is n = 128, nt = 1920, cn = 0.03125,
+    pe = 4 10^4.  Returns (params, fields)."""
+    Re, r, Cn, Pe, Ap = 1000.0, 20.0, cn, pe, 0.01
+    sigma = 1.0 / Re
+    etaL = sigma
+    M = 1.0 / Pe
+    dx, dt = 1.0 / n, 1.0 / nt
+    cs = nt / (math.sqrt(3.0) * n)
+    prm = base_params(2, n, n // 2, dx=dx, dt=dt, cs=cs, rhoL=1.0, rhoG=1.0 / r, etaL=etaL, etaG=etaL / r,
+                      sigma=sigma, M=M, W=Cn, bc=("noslip", "freeslip", "periodic"), ch_scheme=2, iso=9)
+    prm["precision"] = precision
+    prm["amplitude"] = Ap
+    f = zero_fields(prm)
+    x, y = cell_centres(prm)
+    h = 0.5 + Ap * np.cos(2.0 * math.pi * (y + 0.5))
+    f["phi"] = np.tanh(2.0 * (x - h) / Cn)
+    return prm, f
