@@ -37,7 +37,7 @@ class _Par(ctypes.Structure):
         ("sigma", ctypes.c_double), ("M", ctypes.c_double), ("W", ctypes.c_double),
         ("g", ctypes.c_double * 3), ("bc", ctypes.c_int * 3),
         ("ch_scheme", ctypes.c_int), ("iso", ctypes.c_int), ("bulk_visc", ctypes.c_int),
-        ("p_average", ctypes.c_int), ("ch_advection", ctypes.c_int),
+        ("p_average", ctypes.c_int), ("ch_advection", ctypes.c_int), ("axisym", ctypes.c_int),
     ]
 
 
@@ -95,6 +95,7 @@ def _par(prm: dict) -> _Par:
     q.bulk_visc = int(prm.get("bulk_visc", 1))
     q.p_average = int(prm.get("p_average", 1))
     q.ch_advection = int(prm.get("ch_advection", 0))
+    q.axisym = int(prm.get("axisym", 0))
     return q
 
 

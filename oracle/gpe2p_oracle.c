@@ -27,6 +27,18 @@
  * of a tangential component are odd (no-slip) or even (free-slip) about the
  * wall; ghosts of p, phi, mu (hence rho, eta, nu) are even (zero normal
  * gradient, 90 degree contact angle, no diffusive flux through the wall).
+ *
+ * Axisymmetric form (Eqs. gpe-pressure-two-phase-axisym,
+ * gpe-momentum-two-phase-axisym-z and -r, che-axisym, div-v-axisym,
+ * chem-pot-axisym), axisym = 1, 2D only: x is the radius r and y the axis
+ * coordinate z, so u is u_r and v is u_z; cell i is centred at
+ * r = (i + 1/2) dx and the u face i lies at r = i dx.  The low-x side is the
+ * axis: u_r = 0 on it and every ghost across it is even (a symmetry line,
+ * whatever bc[0] says); bc[0] applies to the outer wall only.  The terms the
+ * axisymmetric equations add to the planar ones are evaluated as printed,
+ * with the derivatives by central differences at the point where the
+ * equation lives and the viscosity on a face as the mean of the two cells it
+ * separates (the same mean the planar scheme takes for the density there).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -49,6 +61,7 @@ typedef struct {
   int bulk_visc;      /* 1: eta_b = eta (Sec. 2), 0: eta_b = 0 */
   int p_average;      /* 1: averaged pressure in grad p (Eqs. gradp-u-*) */
   int ch_advection;   /* 0: u.grad(phi) as in Eq. che; 1: div(u phi) */
+  int axisym;         /* 1: axisymmetric (r, z) form, x = r, y = z (2D only) */
 } orc_par;
 
 /* ------------------------------------------------------------------ */
@@ -93,7 +106,10 @@ static double fac(const orc_par *P, const double *f, int c, int i, int j, int k)
       else if (x[a] > n) { x[a] = 2 * n - x[a]; s = -s; }
       if (x[a] == 0 || x[a] == n) return 0.0;
     } else {
-      if (x[a] < 0) { x[a] = -1 - x[a]; if (P->bc[a] == ORC_NOSLIP) s = -s; }
+      /* the axis (low x of the axisymmetric form) mirrors tangential
+       * components evenly */
+      int axis = P->axisym && a == 0;
+      if (x[a] < 0) { x[a] = -1 - x[a]; if (P->bc[a] == ORC_NOSLIP && !axis) s = -s; }
       else if (x[a] >= n) { x[a] = 2 * n - 1 - x[a]; if (P->bc[a] == ORC_NOSLIP) s = -s; }
     }
   }
@@ -151,7 +167,13 @@ static double u_at(const orc_par *P, const double *const U[3], int c, const int 
   return fac(P, U[c], c, x[0] + o[0], x[1] + o[1], x[2] + o[2]);
 }
 
-/* velocity divergence at a (possibly ghost) cell, Eq. div-v-discretization */
+/* radius of the centre of cell column i and of the u face i (axisymmetric form) */
+static double r_cell(const orc_par *P, int i) { return (i + 0.5) * P->dx; }
+static double r_face(const orc_par *P, int i) { return i * P->dx; }
+
+/* velocity divergence at a (possibly ghost) cell, Eq. div-v-discretization;
+ * the axisymmetric form adds u_r / r (Eq. div-v-axisym) with u_r at the cell
+ * centre the mean of its two faces */
 static double divu(const orc_par *P, const double *const U[3], const int x[3], const int o[3]) {
   double d = 0.0;
   for (int a = 0; a < P->dim; ++a) {
@@ -159,7 +181,13 @@ static double divu(const orc_par *P, const double *const U[3], const int x[3], c
     op[a] += 1;
     d += u_at(P, U, a, x, op) - u_at(P, U, a, x, o);
   }
-  return d / P->dx;
+  double div = d / P->dx;
+  if (P->axisym) {
+    int op[3] = {o[0] + 1, o[1], o[2]};
+    double ur = 0.5 * (u_at(P, U, 0, x, o) + u_at(P, U, 0, x, op));
+    div += ur / r_cell(P, x[0] + o[0]);
+  }
+  return div;
 }
 
 /* averaged pressure of the cell at x+o, for the gradient along axis c
@@ -209,6 +237,12 @@ static double Lp_cell(const orc_par *P, const double *p, const double *const U[3
     double num = 0.5 * (nu_at(P, phi, x, o0) + nu_at(P, phi, x, om));
     diff += (nup * (p_at(P, p, x, op) - p_at(P, p, x, o0))
              - num * (p_at(P, p, x, o0) - p_at(P, p, x, om))) / dx2;
+  }
+  if (P->axisym) {
+    /* + (nu / r) dp/dr at the cell centre, Eq. gpe-pressure-two-phase-axisym */
+    const int xp[3] = {1, 0, 0}, xm[3] = {-1, 0, 0};
+    double dpdr = (p_at(P, p, x, xp) - p_at(P, p, x, xm)) / (2.0 * P->dx);
+    diff += nu_at(P, phi, x, o0) / r_cell(P, x[0]) * dpdr;
   }
   return -rho_at(P, phi, x, o0) * P->cs * P->cs * divu(P, U, x, o0) + diff;
 }
@@ -269,7 +303,24 @@ static double Lvel_face(const orc_par *P, int c, const double *p, const double *
 
   double grav = (rb - P->rho_ref) * P->g[c];
 
-  double force = -gradp + 2.0 * t_cc + t_tr + t_b + st + grav;
+  /* the axisymmetric extra viscous terms, viscosity on the face = mean of
+   * its two cells:
+   *   u_r (Eq. gpe-momentum-two-phase-axisym-r): (eta / r) (du_r/dr - u_r / r)
+   *   u_z (Eq. gpe-momentum-two-phase-axisym-z): (eta / r) du_z/dr */
+  double t_axi = 0.0;
+  if (P->axisym) {
+    double eta_f = 0.5 * (eta_at(P, phi, x, cm) + eta_at(P, phi, x, o0));
+    const int xp[3] = {1, 0, 0}, xm[3] = {-1, 0, 0};
+    double dudr = (u_at(P, U, c, x, xp) - u_at(P, U, c, x, xm)) / (2.0 * dx);
+    if (c == 0) {
+      double r = r_face(P, x[0]);
+      t_axi = eta_f / r * (dudr - u_at(P, U, 0, x, o0) / r);
+    } else {
+      t_axi = eta_f / r_cell(P, x[0]) * dudr;
+    }
+  }
+
+  double force = -gradp + 2.0 * t_cc + t_tr + t_b + st + grav + t_axi;
 
   double conv = u_at(P, U, c, x, o0) * (u_at(P, U, c, x, cp) - u_at(P, U, c, x, cm)) / (2.0 * dx) + conv_tr;
 
@@ -391,7 +442,10 @@ void orc_mu(const orc_par *P, const double *phi, double *mu) {
       for (int ii = 0; ii < P->nx; ++ii) {
         int x[3] = {ii, jj, kk};
         double f = phi[lin(P, x)];
-        mu[lin(P, x)] = 4.0 * a * f * (f * f - 1.0) - kappa * lap_iso_at(P, &L, phi, x);
+        double lap = lap_iso_at(P, &L, phi, x);
+        /* Eq. chem-pot-axisym: the Laplacian gains (1/r) dphi/dr */
+        if (P->axisym) lap += grad_iso_at(P, &L, phi, 0, x) / r_cell(P, ii);
+        mu[lin(P, x)] = 4.0 * a * f * (f * f - 1.0) - kappa * lap;
       }
 }
 
@@ -422,7 +476,10 @@ void orc_ch_rhs(const orc_par *P, const double *phi, const double *mu, const dou
             adv += 3.0 / P->dx * s;
           }
         }
-        Lphi[lin(P, x)] = -adv + P->M * lap_iso_at(P, &L, mu, x);
+        double lap = lap_iso_at(P, &L, mu, x);
+        /* Eq. che-axisym: the Laplacian of mu gains (1/r) dmu/dr */
+        if (P->axisym) lap += grad_iso_at(P, &L, mu, 0, x) / r_cell(P, ii);
+        Lphi[lin(P, x)] = -adv + P->M * lap;
       }
 }
 
