@@ -75,6 +75,16 @@ typedef struct {
   int ch_advection;        /* 0: u.grad(phi) as in Eq. che; 1: div(u phi) (conservative) */
   int check_stability;     /* 1: gpe2p_create refuses dt beyond gpe2p_stability_limits */
   int diag_every;          /* gpe2p_advance: check for NaN/Inf every this many steps (0: at the end) */
+  int axisym;              /* 1: the axisymmetric form (Sec. 2, Eqs. gpe-pressure-two-phase-axisym,
+                            * gpe-momentum-two-phase-axisym-z/-r, che-axisym, div-v-axisym,
+                            * chem-pot-axisym), dim = 2 only: x is the radius r, y the axis
+                            * coordinate z, u = u_r, v = u_z; cell column i is centred at
+                            * r = (i + 1/2) dx.  The low-x side is the axis, a symmetry line
+                            * (u_r = 0, every other ghost even) whatever bc[0] says; bc[0] is
+                            * the outer wall (NOSLIP or FREESLIP; PERIODIC is refused).  Needs
+                            * ch_advection = 0 and g[0] = 0.  The stability limits and the
+                            * diagnostics stay those of the planar (x, y) grid: int_phi and
+                            * kinetic sum over the (r, z) plane, not over the volume. */
 } gpe2p_params;
 
 typedef struct gpe2p_ctx *gpe2p_handle;

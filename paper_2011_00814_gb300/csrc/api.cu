@@ -135,6 +135,16 @@ static int validate(const gpe2p_params* p, std::string& why) {
     return GPE2P_EINVAL;
   }
   if (p->diag_every < 0) { why = "diag_every must be >= 0"; return GPE2P_EINVAL; }
+  if (p->axisym & ~1) { why = "axisym is 0 or 1"; return GPE2P_EINVAL; }
+  if (p->axisym) {
+    if (p->dim != 2) { why = "axisym needs dim = 2 (x = r, y = z)"; return GPE2P_EINVAL; }
+    if (p->bc[0] == GPE2P_PERIODIC) {
+      why = "axisym: bc[0] is the outer radial wall and must be NOSLIP or FREESLIP";
+      return GPE2P_EINVAL;
+    }
+    if (p->ch_advection) { why = "axisym takes the advective CH form (ch_advection = 0)"; return GPE2P_EINVAL; }
+    if (p->g[0] != 0.0) { why = "axisym: the body force must act along the axis (g[0] = 0)"; return GPE2P_EINVAL; }
+  }
   return GPE2P_OK;
 }
 
@@ -249,6 +259,7 @@ static KParams<real> kparams(const gpe2p_params& p) {
   for (int c = 0; c < 3; ++c) P.g[c] = (real)p.g[c];
   P.bulk = p.bulk_visc;
   P.pavg = p.p_average;
+  P.axisym = p.axisym;
   double w0, w1, w2 = 0.0, w3 = 0.0;
   if (p.iso == 9) { w0 = 4.0 / 9.0; w1 = 1.0 / 9.0; w2 = 1.0 / 36.0; }
   else if (p.iso == 15) { w0 = 2.0 / 9.0; w1 = 1.0 / 9.0; w3 = 1.0 / 72.0; }

@@ -254,6 +254,7 @@ KParams<real> kp2(const gpe2p_params& p) {
   for (int c = 0; c < 3; ++c) P.g[c] = (real)p.g[c];
   P.bulk = p.bulk_visc;
   P.pavg = p.p_average;
+  P.axisym = p.axisym;
   P.w1 = (real)(1.0 / 9.0);
   P.w2 = (real)(1.0 / 36.0);
   P.w3 = real(0);

@@ -66,6 +66,16 @@ __device__ __forceinline__ void grad_iso(const T& S, const KParams<real>& P, int
   for (int a = 0; a < DIM; ++a) g[a] = P.grad_c * s[a];
 }
 
+// (1/r) df/dr of the axisymmetric form (Eqs. che-axisym, chem-pot-axisym) at
+// the cell of a 2D tile, column i at r = (i + 1/2) dx: the x component of the
+// D2Q9 isotropic gradient over r
+template <typename real, typename T>
+__device__ __forceinline__ real axis_grad_over_r(const T& S, const KParams<real>& P, int f) {
+  const real sx = P.w1 * (S(f, 1, 0, 0) - S(f, -1, 0, 0)) +
+                  P.w2 * ((S(f, 1, 1, 0) - S(f, -1, 1, 0)) + (S(f, 1, -1, 0) - S(f, -1, -1, 0)));
+  return P.grad_c * sx * fdiv(real(2) * P.inv_dx, real(2 * S.gi + 1));
+}
+
 enum { C_PHI = 0, C_MU = 1, C_UH = 2, C_N = 5 };
 
 // face value of component C on the high face of cell (i,j,k) (the low face of
@@ -119,7 +129,10 @@ __device__ __forceinline__ void ch_point_load(const KParams<real>& P, const CHAr
 template <typename real, int DIM, int ISO, typename T>
 __device__ __forceinline__ real ch_rate(const T& S, const KParams<real>& P, const CHArgs<real>& A,
                                        const CHPoint<real>& c) {
-  const real lapmu = lap_iso<real, DIM, ISO>(S, P, C_MU);
+  real lapmu = lap_iso<real, DIM, ISO>(S, P, C_MU);
+  if constexpr (DIM == 2) {
+    if (P.axisym) lapmu += axis_grad_over_r(S, P, C_MU);
+  }
   real adv = real(0);
   if (!A.conservative) {
     real g[3];
@@ -229,6 +242,7 @@ __device__ __forceinline__ void ch2d_tile(const KParams<real>& P, const CHArgs<r
     Tile2<real, SXv, PLv> S;
     S.sm = sm;
     S.c = (ty + 1) * SXv + (tx + 1);
+    S.gi = i;
     CHPoint<real> c;
     ch_point_load<real, 2>(P, A, i, j, 0, c);
     ch_cell<real, 2, 9>(S, P, A, i, j, 0, c);
@@ -255,8 +269,11 @@ __device__ __forceinline__ void mu2d_tile(const KParams<real>& P, const real* __
     Tile2<real, SXv, PLv> S;
     S.sm = sm;
     S.c = (ty + 1) * SXv + (tx + 1);
+    S.gi = i;
     const real f = S(0, 0, 0, 0);
-    mu[lin(P, i, j, 0)] = fma(P.a4 * f, fma(f, f, real(-1)), -(P.kappa * lap_iso<real, 2, 9>(S, P, 0)));
+    real lap = lap_iso<real, 2, 9>(S, P, 0);
+    if (P.axisym) lap += axis_grad_over_r(S, P, 0);  // Eq. chem-pot-axisym
+    mu[lin(P, i, j, 0)] = fma(P.a4 * f, fma(f, f, real(-1)), -(P.kappa * lap));
   }
   __syncthreads();
 }

@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(NTHR, GPE2P_FLOW_MINB) flow3d_kernel(const __g
       S.P = &P;
 #pragma unroll
       for (int dz = -1; dz <= 1; ++dz) S.r[dz + 1] = raw0 + R.slot(k + dz) * NRAW_FLOW * G::PE + cell0 + r * G::BX;
-      const real D0 = Ops::divsum(S, 0, 0, 0);
+      const real D0 = Ops::divsum(S, P, 0, 0, 0);
       real L[4];
       L[0] = Ops::rate_p(S, P, D0);
       L[1] = Ops::template rate_vel<0>(S, P, D0);

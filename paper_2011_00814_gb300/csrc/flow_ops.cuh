@@ -7,6 +7,15 @@
 // diff-p-discretization, conv-u-discretization, u-stress-discretization
 // (a)-(d), st-u-discretization, gradp-u-discretization and gradp-u-p-ave-3d,
 // phi and mu frozen (Sec. 3, after Eq. tvd-rk3).
+//
+// The axisymmetric form (2D, KParams::axisym; x = r, y = z, cell column i
+// centred at r = (i + 1/2) dx, u face i at r = i dx) adds, as printed in
+// Eqs. div-v-axisym, gpe-pressure-two-phase-axisym and
+// gpe-momentum-two-phase-axisym-r/-z: u_r / r to the divergence (u_r at the
+// centre = mean of its faces), (nu / r) dp/dr to the pressure rate,
+// (eta / r)(du_r/dr - u_r / r) to the radial and (eta / r) du_z/dr to the
+// axial momentum, with central differences and the face viscosity the mean
+// of the two cells the face separates.
 #pragma once
 
 #include "gpe2p_dev.cuh"
@@ -21,10 +30,20 @@ enum { F_P = 0, F_U = 1, F_V = 2, F_W = 3, F_PHI = 4, F_RHO = 5, F_ETA = 6, F_NU
 // pressures are formed unnormalised and scaled together at the end.
 template <typename real, int DIM, typename T>
 struct FlowOps {
+  // dx / (2 r) at the centre of the cell column at x offset ox (axisymmetric form, 2D tiles)
+  __device__ __forceinline__ static real dx_2r(const T& S, int ox) {
+    return fdiv(real(1), real(2 * (S.gi + ox) + 1));
+  }
+
   // velocity divergence of the cell at offset (ox,oy,oz) times dx, Eq. div-v-discretization
-  __device__ __forceinline__ static real divsum(const T& S, int ox, int oy, int oz) {
+  // (plus dx u_r / r, Eq. div-v-axisym, in the axisymmetric form)
+  __device__ __forceinline__ static real divsum(const T& S, const KParams<real>& P, int ox, int oy, int oz) {
     real d = (S(F_U, ox + 1, oy, oz) - S(F_U, ox, oy, oz)) + (S(F_V, ox, oy + 1, oz) - S(F_V, ox, oy, oz));
-    if (DIM == 3) d += S(F_W, ox, oy, oz + 1) - S(F_W, ox, oy, oz);
+    if constexpr (DIM == 3) {
+      d += S(F_W, ox, oy, oz + 1) - S(F_W, ox, oy, oz);
+    } else {
+      if (P.axisym) d += (S(F_U, ox, oy, oz) + S(F_U, ox + 1, oy, oz)) * dx_2r(S, ox);
+    }
     return d;
   }
 
@@ -78,6 +97,10 @@ struct FlowOps {
       diff += (nu0 + S(F_NU, ex, ey, ez)) * (S(F_P, ex, ey, ez) - p0) -
               (nu0 + S(F_NU, -ex, -ey, -ez)) * (p0 - S(F_P, -ex, -ey, -ez));
     }
+    if constexpr (DIM == 2) {
+      // (nu / r) dp/dr, Eq. gpe-pressure-two-phase-axisym
+      if (P.axisym) diff += real(2) * nu0 * (S(F_P, 1, 0, 0) - S(F_P, -1, 0, 0)) * dx_2r(S, 0);
+    }
     return -S(F_RHO, 0, 0, 0) * P.cs2 * (d0 * P.inv_dx) + diff * (real(0.5) * P.inv_dx2);
   }
 
@@ -111,7 +134,21 @@ struct FlowOps {
       conv4 += ((ut0 + utc) + (utp + utpc)) * (ucp - ucm);
     }
     real visc = real(2) * tcc + real(0.25) * edge;
-    if (P.bulk) visc += S(F_ETA, 0, 0, 0) * d0 - S(F_ETA, -cx, -cy, -cz) * divsum(S, -cx, -cy, -cz);
+    if (P.bulk) visc += S(F_ETA, 0, 0, 0) * d0 - S(F_ETA, -cx, -cy, -cz) * divsum(S, P, -cx, -cy, -cz);
+    if constexpr (DIM == 2) {
+      if (P.axisym) {
+        const real eta_f = real(0.5) * (S(F_ETA, -cx, -cy, 0) + S(F_ETA, 0, 0, 0));
+        const real dudr2 = S(FC, 1, 0, 0) - S(FC, -1, 0, 0);  // 2 dx du_c/dr
+        if (C == 0) {
+          // (eta / r)(du_r/dr - u_r / r) on the u face i, r = i dx (i >= 1)
+          const real ir = fdiv(real(1), real(S.gi));
+          visc += eta_f * ir * (real(0.5) * dudr2 - uc0 * ir);
+        } else {
+          // (eta / r) du_z/dr on the v face of column i, r = (i + 1/2) dx
+          visc += eta_f * dudr2 * dx_2r(S, 0);
+        }
+      }
+    }
     const real st = -P.sigma * (S(F_PHI, 0, 0, 0) + S(F_PHI, -cx, -cy, -cz)) *
                     (S(F_MU, 0, 0, 0) - S(F_MU, -cx, -cy, -cz)) * P.inv_2dx;
     const real grav = (real(0.5) * rb2 - P.rho_ref) * P.g[C];
@@ -126,7 +163,8 @@ template <typename real, int SXv, int PLv>
 struct Tile2 {
   static constexpr int PAVG = -1;  // pressure averaging decided at run time
   const real* sm;
-  int c;  // the thread's cell within a staged field
+  int c;   // the thread's cell within a staged field
+  int gi;  // its global column index (the radius of the axisymmetric form)
   __device__ __forceinline__ real operator()(int f, int dx, int dy, int) const {
     return sm[f * PLv + c + dy * SXv + dx];
   }
@@ -165,8 +203,9 @@ __device__ __forceinline__ void flow2d_tile(const KParams<real>& P, const FlowAr
     Tile2<real, SXv, PLv> S;
     S.sm = sm;
     S.c = (ty + 1) * SXv + (tx + 1);
+    S.gi = i;
     using Ops = FlowOps<real, 2, Tile2<real, SXv, PLv>>;
-    const real D0 = Ops::divsum(S, 0, 0, 0);
+    const real D0 = Ops::divsum(S, P, 0, 0, 0);
     real L[3];
     L[0] = Ops::rate_p(S, P, D0);
     L[1] = (P.bc[0] != BC_PERIODIC && i == 0) ? real(0) : Ops::template rate_vel<0>(S, P, D0);

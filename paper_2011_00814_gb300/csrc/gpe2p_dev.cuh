@@ -34,6 +34,7 @@ struct KParams {
   real sigma, M, a4, kappa;  // a4 = 4a with a = 3/(4W); kappa = 3W/8
   real g[3];
   int bulk, pavg;
+  int axisym;          // 1: axisymmetric (r, z) form, 2D: x = r with the axis at x = 0, y = z
   // isotropic stencils (Eqs. 1st-der-iso, laplacian-iso)
   real w1, w2, w3;     // weights of the shells |e|^2 = 1, 2, 3 (0 if absent)
   real lap_c, grad_c;  // 6/dx^2 and 3/dx
@@ -65,7 +66,8 @@ __device__ __forceinline__ real ld_cen(const real* __restrict__ f, const KParams
 }
 
 // velocity component C on low faces: zero on the wall faces 0 and n and odd
-// beyond them along C; odd (no-slip) or even (free-slip) across the other walls
+// beyond them along C; odd (no-slip) or even (free-slip) across the other walls,
+// and even across the axis of the axisymmetric form (a symmetry line at x = 0)
 template <int C, typename real>
 __device__ __forceinline__ real ld_face(const real* __restrict__ f, const KParams<real>& P, int i, int j,
                                         int k) {
@@ -80,7 +82,7 @@ __device__ __forceinline__ real ld_face(const real* __restrict__ f, const KParam
       if (x[a] < 0) { x[a] = -x[a]; neg = !neg; }
       if (x[a] == 0 || x[a] >= n) return real(0);
     } else {
-      if (x[a] < 0) { x[a] = -1 - x[a]; if (P.bc[a] == BC_NOSLIP) neg = !neg; }
+      if (x[a] < 0) { x[a] = -1 - x[a]; if (P.bc[a] == BC_NOSLIP && !(a == 0 && P.axisym)) neg = !neg; }
       else if (x[a] >= n) { x[a] = 2 * n - 1 - x[a]; if (P.bc[a] == BC_NOSLIP) neg = !neg; }
     }
   }

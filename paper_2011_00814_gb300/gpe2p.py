@@ -5,8 +5,8 @@ CUDA kernels.  There is no CPU fallback; if the library is missing the
 import of :func:`lib` raises.
 
 Parameters are a plain ``dict`` (see :mod:`paper_2011_00814_gb300.inputs`)
-plus the solver keys ``precision`` (32 | 64), ``check_stability`` (0 | 1) and
-``diag_every`` (int).  Fields are numpy float64 arrays of shape ``(ny, nx)``
+plus the solver keys ``precision`` (32 | 64), ``check_stability`` (0 | 1),
+``diag_every`` (int) and ``axisym`` (0 | 1, the axisymmetric (r, z) form).  Fields are numpy float64 arrays of shape ``(ny, nx)``
 or ``(nz, ny, nx)``; the library copies them.
 """
 from __future__ import annotations
@@ -36,6 +36,7 @@ class Params(ctypes.Structure):
         ("bc", ctypes.c_int * 3), ("precision", ctypes.c_int), ("ch_scheme", ctypes.c_int),
         ("iso", ctypes.c_int), ("bulk_visc", ctypes.c_int), ("p_average", ctypes.c_int),
         ("ch_advection", ctypes.c_int), ("check_stability", ctypes.c_int), ("diag_every", ctypes.c_int),
+        ("axisym", ctypes.c_int),
     ]
 
 
@@ -155,6 +156,7 @@ def params(prm: dict) -> Params:
     q.ch_advection = int(prm.get("ch_advection", 0))
     q.check_stability = int(prm.get("check_stability", 0))
     q.diag_every = int(prm.get("diag_every", 0))
+    q.axisym = int(prm.get("axisym", 0))
     return q
 
 

@@ -313,3 +313,65 @@ def capillary_wave(n: int = 64, nt: int = 384, cn: float = 0.0625, pe: float = 2
     h = 0.5 + Ap * np.cos(2.0 * math.pi * (y + 0.5))
     f["phi"] = np.tanh(2.0 * (x - h) / Cn)
     return prm, f
+
+
+# ---------------------------------------------------------------------------
+# axisymmetric workloads (x = r with the axis at x = 0, y = z; "axisym": 1)
+# ---------------------------------------------------------------------------
+
+def _axisym_drop(prm: dict, zc: float, R: float, cn: float, noise: float, seed: int) -> dict:
+    f = zero_fields(prm)
+    r, z = cell_centres(prm)
+    rdc = np.sqrt((z - zc) ** 2 + r**2)
+    f["phi"] = -np.tanh(2.0 * (rdc - R) / cn)
+    if noise > 0:
+        f["phi"] = f["phi"] + uniform_noise(seed, f["phi"].shape, noise)
+    return f
+
+
+def falling_drop(n_l: int = 50, n_t: int = 4000, cn: float = 0.06, pe: float = 1000.0, precision: int = 64,
+                 noise: float = 0.0, seed: int = 0):
+    """The axisymmetric falling drop of Sec. "Falling drop": L_c = R = 1 with
+    n_l cells per R, domain r in [0, 8], z in [0, 24] (at n_l = 50: 400 x 1200
+    cells), axis at r = 0, no-slip walls elsewhere.  r_rho = 1.15, r_eta = 1,
+    Eo = g (rho_L - rho_G) D^2 / sigma = 144, Oh = eta_L / sqrt(rho_L D sigma)
+    = 0.0466 (D = 2R), rho_ref = rho_G, gravity along +z; the drop starts at
+    (z, r) = (2, 0).  U_c = sigma / eta_L = 1 and T_c = L_c / U_c = 1, so
+    sigma = eta_L = 2 Oh^2 and g = Eo sigma / ((rho_L - rho_G) D^2);
+    dx = 1/n_l, dt = 1/n_t, c_s = (dx / dt) / sqrt 3 (the paper's N_L = 50,
+    N_t = 4000, c = 80), W = Cn, M = 1/Pe (Pe with the chemical potential's
+    sigma_ref = 1).  One T'_c = sqrt(D/g) is about 1.29 T_c.  Returns
+    (params, fields)."""
+    R, D, rhoL, r_rho, Eo, Oh = 1.0, 2.0, 1.0, 1.15, 144.0, 0.0466
+    rhoG = rhoL / r_rho
+    etaL = 2.0 * Oh * Oh * rhoL
+    sigma = etaL  # U_c = sigma / eta_L = 1
+    g = Eo * sigma / ((rhoL - rhoG) * D * D)
+    dx, dt = R / n_l, 1.0 / n_t
+    prm = base_params(2, 8 * n_l, 24 * n_l, dx=dx, dt=dt, cs=(dx / dt) / math.sqrt(3.0), rhoL=rhoL,
+                      rhoG=rhoG, etaL=etaL, etaG=etaL, rho_ref=rhoG, sigma=sigma, M=1.0 / pe, W=cn * R,
+                      g=(0.0, g, 0.0), bc=("noslip", "noslip", "periodic"), ch_scheme=2, iso=9, axisym=1)
+    prm["precision"] = precision
+    return prm, _axisym_drop(prm, 2.0 * R, R, cn * R, noise, seed)
+
+
+def drop_coalescence(oh: float = 0.119, n_l: int = 40, n_t: int = None, cn: float = 0.1, pe: float = 8.0e3,
+                     precision: int = 64, noise: float = 0.0, seed: int = 0):
+    """The axisymmetric coalescence of two equal drops of Sec. "Drop
+    coalescence (axisymmetric)": the quarter r in [0, 3], z in [0, 3] with
+    symmetric boundaries on every side (the plane z = 0 mirrors the second
+    drop), L_c = R = 1 with n_l cells per R (120 x 120 at n_l = 40), the drop
+    centred at (z, r) = (1, 0).  r_rho = 50, r_eta = 58.8, Oh = eta_L /
+    sqrt(rho_L sigma R) in {0.037, 0.119, 0.3}; U_c = sigma / eta_L = 1, so
+    sigma = eta_L = Oh^2.  n_t defaults to the paper's 400 (c = 10), or 2000
+    (c = 50) at Oh = 0.3.  Returns (params, fields)."""
+    R, rhoL = 1.0, 1.0
+    if n_t is None:
+        n_t = 2000 if oh >= 0.3 else 400
+    etaL = oh * oh * rhoL
+    dx, dt = R / n_l, 1.0 / n_t
+    prm = base_params(2, 3 * n_l, 3 * n_l, dx=dx, dt=dt, cs=(dx / dt) / math.sqrt(3.0), rhoL=rhoL,
+                      rhoG=rhoL / 50.0, etaL=etaL, etaG=etaL / 58.8, rho_ref=0.0, sigma=etaL, M=1.0 / pe,
+                      W=cn * R, bc=("freeslip", "freeslip", "periodic"), ch_scheme=2, iso=9, axisym=1)
+    prm["precision"] = precision
+    return prm, _axisym_drop(prm, 1.0 * R, R, cn * R, noise, seed)

@@ -56,7 +56,7 @@ int main(void) {
   printf("gpe2p_params %zu\n", sizeof(gpe2p_params));
   printf("gpe2p_diag %zu\n", sizeof(gpe2p_diag));
   O(gpe2p_params, dx); O(gpe2p_params, g); O(gpe2p_params, bc); O(gpe2p_params, precision);
-  O(gpe2p_params, diag_every); O(gpe2p_diag, nan_flag); O(gpe2p_diag, step); O(gpe2p_diag, t);
+  O(gpe2p_params, diag_every); O(gpe2p_params, axisym); O(gpe2p_diag, nan_flag); O(gpe2p_diag, step); O(gpe2p_diag, t);
   return 0;
 }
 """
@@ -74,7 +74,7 @@ def test_ctypes_structs_match_header_layout():
     lay = _c_layout()
     assert lay["gpe2p_params"] == ctypes.sizeof(gpe2p.Params)
     assert lay["gpe2p_diag"] == ctypes.sizeof(gpe2p.Diag)
-    for f in ("dx", "g", "bc", "precision", "diag_every"):
+    for f in ("dx", "g", "bc", "precision", "diag_every", "axisym"):
         assert lay[f"gpe2p_params.{f}"] == getattr(gpe2p.Params, f).offset, f
     for f in ("nan_flag", "step", "t"):
         assert lay[f"gpe2p_diag.{f}"] == getattr(gpe2p.Diag, f).offset, f
@@ -93,6 +93,10 @@ def test_stability_limits_of_the_workloads(lib):
     assert prm["dt"] < min(ac, vi, ch)
     ac0, _, _ = gpe2p.stability_limits(dict(prm, p_average=0))
     assert prm["dt"] > ac0
+    # the axisymmetric workloads at the paper's resolutions
+    for prm, _ in (inputs.falling_drop(), inputs.drop_coalescence(0.037), inputs.drop_coalescence(0.119),
+                   inputs.drop_coalescence(0.3)):
+        assert prm["dt"] < min(gpe2p.stability_limits(prm))
     # the Rayleigh-Taylor case at Pe = 1000: the CH limit sets dt
     prm, _ = inputs.rayleigh_taylor()
     ac, vi, ch = gpe2p.stability_limits(prm)
@@ -102,7 +106,12 @@ def test_stability_limits_of_the_workloads(lib):
 @pytest.mark.parametrize("bad", [dict(dim=4), dict(nx=0), dict(nx=70000), dict(dx=0.0), dict(dt=-1.0),
                                  dict(rhoG=0.0), dict(etaL=-1.0), dict(W=0.0), dict(precision=16),
                                  dict(ch_scheme=3), dict(iso=15), dict(bc=("wall",) * 3),
-                                 dict(bulk_visc=2), dict(sigma=float("nan"))])
+                                 dict(bulk_visc=2), dict(sigma=float("nan")), dict(axisym=2),
+                                 # the axisymmetric form: 2D, an outer wall, advective CH, axial g
+                                 dict(axisym=1, dim=3, nz=8, iso=15, bc=("noslip",) * 3),
+                                 dict(axisym=1, bc=("periodic", "noslip", "periodic")),
+                                 dict(axisym=1, bc=("noslip",) * 3, ch_advection=1),
+                                 dict(axisym=1, bc=("noslip",) * 3, g=(0.1, 0.0, 0.0))])
 def test_invalid_parameters_are_rejected_on_the_host(lib, bad):
     prm = dict(inputs.base_params(2, 8, 8), precision=64)
     if bad.get("bc") == ("wall",) * 3:
