@@ -208,6 +208,49 @@ def measure_batch2d(stream, steps=20, warmup=3, n=96):
     return out
 
 
+def measure_axisym(stream, steps=400, warmup=5):
+    """The axisymmetric falling drop at the paper's resolution (50 cells per
+    radius, 400 x 1200 cells, Eo = 144, Oh = 0.0466): cell-updates/s of full
+    steps in FP32 and FP64, device-timed on the solver's stream.  The state (~25 MB) stays in
+    L2, so no HBM roofline applies; the step is bound by launch and load
+    latency."""
+    import torch
+    from paper_2011_00814_gb300 import gpe2p
+    out = {"workload": "axisymmetric falling drop 400x1200 (r x z), TVD-RK2 CH, D2Q9"}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for prec in (32, 64):
+        prm, f = inputs.falling_drop(precision=prec)
+        cells = prm["nx"] * prm["ny"]
+        with gpe2p.Solver(prm, stream=stream.cuda_stream) as s:
+            s.init_fields(f)
+            for _ in range(warmup):
+                s.step()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(steps):
+                s.step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            d = s.diagnostics()
+        out[f"fp{prec}"] = {"cell_updates_per_s": cells / (ms / 1e3), "ms_per_step": ms, "steps": steps,
+                            "nan": d["nan_flag"]}
+    out["cells"] = cells
+    return out
+
+
+def cpu_baseline_axisym(steps=2):
+    """The CPU oracle on a two-step sample of the axisymmetric falling drop."""
+    import oracle
+    prm, f = inputs.falling_drop()
+    st = oracle.init_state(prm, f["phi"], f["p"], f["u"], f["v"])
+    t0 = time.perf_counter()
+    oracle.step(prm, st, steps)
+    sec = time.perf_counter() - t0
+    return {"value": prm["nx"] * prm["ny"] * steps / sec, "unit": UNIT, "kind": "oracle",
+            "sample": f"falling drop 400x1200, {steps} steps", "cores": int(os.environ.get("OMP_NUM_THREADS", 1))}
+
+
 SURROGATE_WEIGHTS = os.path.join(ROOT, "paper_2011_00814_gb300", "data", "unet_two_drops_256.npz")
 
 
@@ -343,6 +386,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 2D measurement")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate measurement")
+    ap.add_argument("--no-axisym", action="store_true", help="skip the axisymmetric falling-drop measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -456,10 +500,14 @@ def main():
     }
     if not args.no_batch:
         line["batch2d"] = measure_batch2d(stream)
+    if not args.no_axisym and world == 1:
+        line["axisym"] = measure_axisym(stream)
     if not args.no_surrogate and world == 1:
         line["surrogate"] = measure_surrogate()
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline()
+        if not args.no_axisym:
+            line["cpu_baseline"]["axisym"] = cpu_baseline_axisym()
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
