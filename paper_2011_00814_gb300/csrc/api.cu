@@ -620,13 +620,38 @@ static int phi_acc_check(gpe2p_ctx* h, const gpe2p_diag& d) {
   return GPE2P_OK;
 }
 
+// The address at which the device can dereference a caller's host array, or
+// nullptr.  Pinned host memory (cudaHostAlloc, cudaHostRegister) is mapped
+// into the device's address space; the conversion kernels then read or write
+// it in place over the host link, with no FP64 staging copy in HBM and no
+// second pass.  Pageable memory (nullptr) goes through the staging buffer and
+// the copy engines.
+static const void* device_view(const void* host) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// one field from the caller's dense FP64 array into the padded working array
+// (comp: the velocity component whose wall faces are zeroed, -1 none; with
+// abs, phi: also the integral of |phi_0|, the reference of the conservation
+// drift, into d_out[0], from the same single read of the FP64 input)
 template <typename real>
-static cudaError_t put_field(gpe2p_ctx* h, const double* src, void* dst, int comp) {
+static cudaError_t put_field(gpe2p_ctx* h, const double* src, void* dst, int comp, bool abs = false) {
   const KParams<real> P = kparams<real>(h->prm);
-  cudaError_t e = cudaMemcpyAsync(h->d_stage, src, (size_t)h->ncell * sizeof(double), cudaMemcpyHostToDevice,
-                                  h->stream);
-  if (e != cudaSuccess) return e;
-  return launch_from_double<real>(P, h->d_stage, (real*)dst, comp, h->ncell, h->stream);
+  const double* dsrc = static_cast<const double*>(device_view(src));
+  if (!dsrc) {
+    cudaError_t e = cudaMemcpyAsync(h->d_stage, src, (size_t)h->ncell * sizeof(double), cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e != cudaSuccess) return e;
+    dsrc = h->d_stage;
+  }
+  if (!abs) return launch_from_double<real>(P, dsrc, (real*)dst, comp, h->ncell, h->stream);
+  const double dx = h->prm.dx, vol = h->prm.dim == 3 ? dx * dx * dx : dx * dx;
+  return launch_from_double_abs<real>(P, dsrc, (real*)dst, h->d_part, h->nblk, vol, h->d_out, h->stream);
 }
 
 template <typename real>
@@ -636,11 +661,7 @@ static cudaError_t init_impl(gpe2p_ctx* h, const double* phi, const double* u, c
   cudaError_t e;
   for (int f = 0; f < 1 + h->prm.dim; ++f)
     if ((e = put_field<real>(h, src[f], h->Q[0][f], f - 1)) != cudaSuccess) return e;
-  if ((e = put_field<real>(h, phi, h->phi, -1)) != cudaSuccess) return e;
-  // the integral of |phi_0| (reference of the conservation drift) from the FP64 staging copy
-  const double dx = h->prm.dx, vol = h->prm.dim == 3 ? dx * dx * dx : dx * dx;
-  if ((e = launch_abs_sum(h->d_stage, h->ncell, h->d_part, h->nblk, vol, h->d_out, h->stream)) != cudaSuccess)
-    return e;
+  if ((e = put_field<real>(h, phi, h->phi, -1, true)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(h->h_out, h->d_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
     return e;
   const KParams<real> P = kparams<real>(h->prm);
@@ -800,8 +821,13 @@ extern "C" int gpe2p_phi_accumulation(gpe2p_handle h, int* mode, int* active, do
 template <typename real>
 static cudaError_t get_field(gpe2p_ctx* h, const void* src, double* dst, const void* lo = nullptr) {
   cudaError_t e;
+  double* ddst = static_cast<double*>(const_cast<void*>(device_view(dst)));
   if (sizeof(real) == 8 && h->pitch == h->prm.nx && !lo) {
     e = cudaMemcpyAsync(dst, src, (size_t)h->ncell * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  } else if (ddst) {
+    // pinned destination: the conversion kernel writes the host array in place
+    e = launch_to_double<real>(kparams<real>(h->prm), (const real*)src, ddst, h->ncell, h->stream,
+                               (const real*)lo);
   } else {
     e = launch_to_double<real>(kparams<real>(h->prm), (const real*)src, h->d_stage, h->ncell, h->stream,
                                (const real*)lo);

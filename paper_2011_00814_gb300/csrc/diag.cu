@@ -123,85 +123,95 @@ cudaError_t launch_diag(const KParams<real>& P, const real* p, const real* const
   return cudaGetLastError();
 }
 
-// sum of |x| over a dense FP64 array, block partials in slot 0 of 4 (the
-// layout diag_final_kernel reduces)
-__global__ void __launch_bounds__(DIAG_THREADS) abs_sum_partial_kernel(const double* x, long long n,
-                                                                       double* partial) {
-  double s = 0.0;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
-       id += (long long)gridDim.x * blockDim.x)
-    s += fabs(x[id]);
-  __shared__ double red[DIAG_THREADS / 32];
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0;
-    for (int w = 0; w < DIAG_THREADS / 32; ++w) a += red[w];
-    partial[4 * blockIdx.x + 0] = a;
-    partial[4 * blockIdx.x + 1] = 0.0;
-    partial[4 * blockIdx.x + 2] = 0.0;
-    partial[4 * blockIdx.x + 3] = 0.0;
-  }
-}
-
-cudaError_t launch_abs_sum(const double* x, long long n, double* partial, int nblocks, double vol, double* out,
-                           cudaStream_t s) {
-  abs_sum_partial_kernel<<<nblocks, DIAG_THREADS, 0, s>>>(x, n, partial);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  diag_final_kernel<<<1, DIAG_THREADS, 0, s>>>(partial, nblocks, vol, out);
-  return cudaGetLastError();
-}
-
-// dense FP64 (host layout) -> padded rows in the working precision
-template <typename real>
-__global__ void from_double_kernel(const KParams<real> P, const double* src, real* dst, int c, long long n) {
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
-       id += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(id % P.n[0]);
-    const int j = (int)((id / P.n[0]) % P.n[1]);
-    const int k = (int)(id / ((long long)P.n[0] * P.n[1]));
-    real v = (real)src[id];
-    if (c >= 0 && P.bc[c] != BC_PERIODIC) {
-      const int x = c == 0 ? i : (c == 1 ? j : k);
-      if (x == 0) v = real(0);
+// dense FP64 (host layout) -> padded rows in the working precision.  Blocks
+// stride over the rows (j, k) and threads along x, so that both sides are
+// read and written in order; src may be a pinned host array read in place.
+// With ABS, the block also sums |src| (in FP64, fixed order) into partial[4 b]
+// in the layout diag_final_kernel reduces, so that the integral of |phi_0|
+// needs no second read of the input.
+template <typename real, bool ABS>
+__global__ void __launch_bounds__(DIAG_THREADS) from_double_kernel(const KParams<real> P, const double* src,
+                                                                   real* dst, int c, double* partial) {
+  const int nx = P.n[0], ny = P.n[1];
+  const long long rows = (long long)ny * P.n[2];
+  double a = 0.0;
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int j = (int)(r % ny), k = (int)(r / ny);
+    const bool wall_row = c >= 0 && P.bc[c] != BC_PERIODIC && ((c == 1 && j == 0) || (c == 2 && k == 0));
+    const double* s = src + r * nx;
+    real* d = dst + lin(P, 0, j, k);
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const double x = s[i];
+      if (ABS) a += fabs(x);
+      real v = (real)x;
+      if (wall_row || (c == 0 && P.bc[0] != BC_PERIODIC && i == 0)) v = real(0);
+      d[i] = v;
     }
-    dst[lin(P, i, j, k)] = v;
+  }
+  if (ABS) {
+    __shared__ double red[DIAG_THREADS / 32];
+    a = warp_sum(a);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < DIAG_THREADS / 32; ++w) t += red[w];
+      partial[4 * blockIdx.x + 0] = t;
+      partial[4 * blockIdx.x + 1] = 0.0;
+      partial[4 * blockIdx.x + 2] = 0.0;
+      partial[4 * blockIdx.x + 3] = 0.0;
+    }
   }
 }
 
-// padded rows -> dense FP64 (plus a low part, when given)
+// padded rows -> dense FP64 (plus a low part, when given); dst may be a
+// pinned host array written in place
 template <typename real>
-__global__ void to_double_kernel(const KParams<real> P, const real* src, double* dst, long long n, const real* lo) {
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
-       id += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(id % P.n[0]);
-    const int j = (int)((id / P.n[0]) % P.n[1]);
-    const int k = (int)(id / ((long long)P.n[0] * P.n[1]));
-    const long long q = lin(P, i, j, k);
-    dst[id] = (double)src[q] + (lo ? (double)lo[q] : 0.0);
+__global__ void to_double_kernel(const KParams<real> P, const real* src, double* dst, const real* lo) {
+  const int nx = P.n[0], ny = P.n[1];
+  const long long rows = (long long)ny * P.n[2];
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int j = (int)(r % ny), k = (int)(r / ny);
+    const long long q0 = lin(P, 0, j, k);
+    double* d = dst + r * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x)
+      d[i] = (double)src[q0 + i] + (lo ? (double)lo[q0 + i] : 0.0);
   }
 }
 
-static unsigned grid_for(long long n) {
-  long long nb = (n + 255) / 256;
-  if (nb > 152 * 32) nb = 152 * 32;
-  if (nb < 1) nb = 1;
-  return (unsigned)nb;
+// blocks for a row-strided conversion: every row gets a block up to 32 per SM
+template <typename real>
+static unsigned grid_rows(const KParams<real>& P) {
+  long long rows = (long long)P.n[1] * P.n[2];
+  if (rows > 152 * 32) rows = 152 * 32;
+  return (unsigned)(rows < 1 ? 1 : rows);
 }
 
 template <typename real>
 cudaError_t launch_from_double(const KParams<real>& P, const double* src, real* dst, int c, long long n,
                                cudaStream_t s) {
-  from_double_kernel<real><<<grid_for(n), 256, 0, s>>>(P, src, dst, c, n);
+  (void)n;
+  from_double_kernel<real, false><<<grid_rows(P), DIAG_THREADS, 0, s>>>(P, src, dst, c, nullptr);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_from_double_abs(const KParams<real>& P, const double* src, real* dst, double* partial,
+                                   int nblocks, double vol, double* out, cudaStream_t s) {
+  unsigned nb = grid_rows(P);
+  if (nb > (unsigned)nblocks) nb = (unsigned)nblocks;
+  from_double_kernel<real, true><<<nb, DIAG_THREADS, 0, s>>>(P, src, dst, -1, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  diag_final_kernel<<<1, DIAG_THREADS, 0, s>>>(partial, (int)nb, vol, out);
   return cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t launch_to_double(const KParams<real>& P, const real* src, double* dst, long long n, cudaStream_t s,
                              const real* lo) {
-  to_double_kernel<real><<<grid_for(n), 256, 0, s>>>(P, src, dst, n, lo);
+  (void)n;
+  to_double_kernel<real><<<grid_rows(P), 256, 0, s>>>(P, src, dst, lo);
   return cudaGetLastError();
 }
 
@@ -217,6 +227,10 @@ template cudaError_t launch_from_double<float>(const KParams<float>&, const doub
                                                cudaStream_t);
 template cudaError_t launch_from_double<double>(const KParams<double>&, const double*, double*, int,
                                                 long long, cudaStream_t);
+template cudaError_t launch_from_double_abs<float>(const KParams<float>&, const double*, float*, double*, int,
+                                                   double, double*, cudaStream_t);
+template cudaError_t launch_from_double_abs<double>(const KParams<double>&, const double*, double*, double*, int,
+                                                    double, double*, cudaStream_t);
 template cudaError_t launch_to_double<float>(const KParams<float>&, const float*, double*, long long,
                                              cudaStream_t, const float*);
 template cudaError_t launch_to_double<double>(const KParams<double>&, const double*, double*, long long,

@@ -75,14 +75,15 @@ cudaError_t launch_diag(const KParams<real>& P, const real* p, const real* const
                         const real* phi_lo,
                         double* partial, int nblocks, double* out, cudaStream_t s);
 
-// vol * sum |x| of a dense FP64 device array into out[0] (partial: 4 doubles per block)
-cudaError_t launch_abs_sum(const double* x, long long n, double* partial, int nblocks, double vol, double* out,
-                           cudaStream_t s);
-
 // FP64 <-> working precision copies with the wall faces of component c zeroed (c < 0: none)
 template <typename real>
 cudaError_t launch_from_double(const KParams<real>& P, const double* src, real* dst, int c, long long n,
                                cudaStream_t s);
+// the same for phi, also reducing the integral of |src| times vol into out[0]
+// (partial: 4 doubles per block, at most nblocks blocks)
+template <typename real>
+cudaError_t launch_from_double_abs(const KParams<real>& P, const double* src, real* dst, double* partial,
+                                   int nblocks, double vol, double* out, cudaStream_t s);
 template <typename real>
 cudaError_t launch_to_double(const KParams<real>& P, const real* src, double* dst, long long n, cudaStream_t s,
                              const real* lo = nullptr);
