@@ -449,9 +449,9 @@ static bool encode_map(gpe2p_ctx* h, CUtensorMap* m, void* base, int rows) {
 static int build_maps(gpe2p_ctx* h) {
   bool ok = true;
   for (int s = 0; s < 3; ++s) {
-    for (int f = 0; f < 4; ++f) ok = ok && encode_map(h, &h->flow_maps[s].m[f], h->Q[s][f], K3_SY);
-    ok = ok && encode_map(h, &h->flow_maps[s].m[4], h->phi, K3_SY);
-    ok = ok && encode_map(h, &h->flow_maps[s].m[5], h->mu, K3_SY);
+    for (int f = 0; f < 4; ++f) ok = ok && encode_map(h, &h->flow_maps[s].m[f], h->Q[s][f], FLOW_K3_SY);
+    ok = ok && encode_map(h, &h->flow_maps[s].m[4], h->phi, FLOW_K3_SY);
+    ok = ok && encode_map(h, &h->flow_maps[s].m[5], h->mu, FLOW_K3_SY);
   }
   void* phis[3] = {h->phi, h->phis[0], h->phis[1]};
   void* mus[3] = {h->mu, h->mus, h->mus};
@@ -554,12 +554,13 @@ extern "C" int gpe2p_create(const gpe2p_params* p, void* stream, gpe2p_handle* o
   // prologue of two, and the blocks run in waves of the resident slots; take
   // the kc in [4, 64] that minimises waves x (kc + 2), the time of the slowest
   // SM.  Resident blocks per SM (registers and shared memory, as ncu reports
-  // them): flow stage 2, CH stage 5, mu 8.
+  // them): flow stage FLOW_MINB, CH stage 5, mu 8.
   if (h->prm.dim == 3) {
-    const long long bxy = (long long)((h->prm.nx + TX - 1) / TX) * ((h->prm.ny + K3_TY - 1) / K3_TY);
+    const long long bx = (h->prm.nx + TX - 1) / TX;
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev);
-    auto pick = [&](int per_sm) {
+    auto pick = [&](int per_sm, int rows) {
+      const long long bxy = bx * ((h->prm.ny + rows - 1) / rows);
       const long long slots = (long long)per_sm * nsm;
       long long best_kc = 4, best = -1;
       for (long long kc = 4; kc <= 64 && kc <= h->prm.nz; ++kc) {
@@ -569,9 +570,9 @@ extern "C" int gpe2p_create(const gpe2p_params* p, void* stream, gpe2p_handle* o
       }
       return (int)(best_kc > h->prm.nz ? h->prm.nz : best_kc);
     };
-    h->kchunk = pick(2);
-    h->kchunk_ch = pick(5);
-    h->kchunk_mu = pick(8);
+    h->kchunk = pick(FLOW_MINB, FLOW_K3_TY);
+    h->kchunk_ch = pick(5, K3_TY);
+    h->kchunk_mu = pick(8, K3_TY);
   } else {
     h->kchunk = h->kchunk_ch = h->kchunk_mu = 1;
   }

@@ -33,7 +33,7 @@ enum { R_P = 0, R_U = 1, R_V = 2, R_W = 3, R_PHI = 4, R_MU = 5, NRAW_FLOW = 6 };
 template <typename real, int PAVG_>
 struct RingTile {
   static constexpr int PAVG = PAVG_;
-  using G = RingGeom<real, K3_SY>;
+  using G = RingGeom<real, FLOW_K3_SY>;
   const real* sm;           // the block's shared memory
   const KParams<real>* P;
   int r[3];                 // index of the thread's cell in raw field 0 of planes k-1, k, k+1
@@ -57,22 +57,20 @@ struct RingTile {
   }
 };
 
-// One block: a TX x K3_TY column of cells over the planes [kbeg, kend);
+// One block: a TX x FLOW_K3_TY column of cells over the planes [kbeg, kend);
 // thread (tx, ty) computes the cells (i0 + tx, j0 + 2 ty + r), r = 0, 1.  The
 // two cells share most of their stencil, so the loads and sub-expressions
 // they have in common are formed once.
-// resident blocks per SM the 3D flow stage is compiled for (2: up to 128
-// registers, no spills; 3 caps them at 80 with spills and measured slower,
-// 5.61 against 4.88 ms per step of the 256x256x512 bubble)
-#ifndef GPE2P_FLOW_MINB
-#define GPE2P_FLOW_MINB 2
-#endif
+// resident blocks per SM the 3D flow stage is compiled for (FLOW_MINB: up to
+// 128 registers, no spills; three blocks of 256 threads cap them at 80 with
+// spills and measured slower, 5.61 against 4.88 ms per step of the
+// 256x256x512 bubble)
 
 template <typename real, int MODE, int RING, int PAVG>
-__global__ void __launch_bounds__(NTHR, GPE2P_FLOW_MINB) flow3d_kernel(const __grid_constant__ Maps<NRAW_FLOW> maps,
+__global__ void __launch_bounds__(FLOW_NTHR, FLOW_MINB) flow3d_kernel(const __grid_constant__ Maps<NRAW_FLOW> maps,
                                                       const __grid_constant__ KParams<real> P,
                                                       const FlowArgs<real> A, const int kchunk, int* err) {
-  constexpr int SYv = K3_SY;
+  constexpr int SYv = FLOW_K3_SY;
   using G = RingGeom<real, SYv>;
   extern __shared__ __align__(128) unsigned char smraw[];
   Ring<real, NRAW_FLOW, RING, SYv> R;
@@ -80,12 +78,12 @@ __global__ void __launch_bounds__(NTHR, GPE2P_FLOW_MINB) flow3d_kernel(const __g
   R.bar = reinterpret_cast<uint64_t*>(sbase);
   R.raw = reinterpret_cast<real*>(sbase + 128);
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * K3_TY;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * FLOW_K3_TY;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(kbeg + kchunk, P.n[2]);
   const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
-  const bool edge_tile = i0 == 0 || i0 + TX + 1 > nx || j0 == 0 || j0 + K3_TY + 1 > ny;
-  const bool ragged = i0 + TX > nx || j0 + K3_TY > ny;
+  const bool edge_tile = i0 == 0 || i0 + TX + 1 > nx || j0 == 0 || j0 + FLOW_K3_TY + 1 > ny;
+  const bool ragged = i0 + TX > nx || j0 + FLOW_K3_TY > ny;
   const int i = i0 + tx, ja = j0 + 2 * ty;
   const bool act[2] = {i < nx && ja < ny, i < nx && ja + 1 < ny};
 
@@ -104,7 +102,7 @@ __global__ void __launch_bounds__(NTHR, GPE2P_FLOW_MINB) flow3d_kernel(const __g
     for (int f = 0; f < NRAW_FLOW; ++f) pl[f] = R.plane(kk, f);
     const bool full = ghost_plane || ragged;
     const int ncell = full ? SX * SYv : perim<SYv>();
-    for (int q = tid; q < ncell; q += NTHR) {
+    for (int q = tid; q < ncell; q += FLOW_NTHR) {
       int lx, ly;
       if (full) { ly = q / SX; lx = q - ly * SX; }
       else perim_cell<SYv>(q, lx, ly);
@@ -205,8 +203,9 @@ cudaError_t launch_flow_stage(const KParams<real>& P, const FlowArgs<real>& A, i
   cudaError_t e;
   if constexpr (DIM == 3) {
     constexpr int RING = flow_ring<real>();
-    const size_t sm = ring_smem_bytes<real, NRAW_FLOW, 0, RING, K3_SY>();
-    grd.y = (P.n[1] + K3_TY - 1) / K3_TY;
+    const size_t sm = ring_smem_bytes<real, NRAW_FLOW, 0, RING, FLOW_K3_SY>();
+    blk.y = FLOW_TY;
+    grd.y = (P.n[1] + FLOW_K3_TY - 1) / FLOW_K3_TY;
 #define GPE2P_FLOW3_CASE(M)                                                                                 \
   if (P.pavg) {                                                                                             \
     e = cudaFuncSetAttribute(flow3d_kernel<real, M, RING, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \

@@ -15,6 +15,20 @@ namespace gpe2p {
 constexpr int K3_TY = 2 * TY;
 constexpr int K3_SY = K3_TY + 2;
 
+// the 3D flow stage's block: TX x FLOW_TY threads, FLOW_K3_TY = 2 FLOW_TY rows
+// of cells, FLOW_MINB resident blocks per SM (registers: 128 per thread, so
+// 16 warps per SM at any block height).  Four warps per block rather than
+// eight: the per-plane barrier then holds back half as many warps, which
+// measured 0.645 against 0.684 ms per stage on the 256x256x512 bubble.
+#ifndef GPE2P_FLOW_TY
+#define GPE2P_FLOW_TY 4
+#endif
+constexpr int FLOW_TY = GPE2P_FLOW_TY;
+constexpr int FLOW_NTHR = TX * FLOW_TY;
+constexpr int FLOW_K3_TY = 2 * FLOW_TY;
+constexpr int FLOW_K3_SY = FLOW_K3_TY + 2;
+constexpr int FLOW_MINB = 16 / FLOW_TY;
+
 // one flow stage: out = a q0 + b (q + dt L(q))   (Eq. tvd-rk3)
 template <typename real>
 struct FlowArgs {
