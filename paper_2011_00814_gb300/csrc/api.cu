@@ -456,10 +456,10 @@ static int build_maps(gpe2p_ctx* h) {
   void* phis[3] = {h->phi, h->phis[0], h->phis[1]};
   void* mus[3] = {h->mu, h->mus, h->mus};
   for (int c = 0; c < 3; ++c) {
-    ok = ok && encode_map(h, &h->ch_maps[c].m[0], phis[c], K3_SY);
-    ok = ok && encode_map(h, &h->ch_maps[c].m[1], mus[c], K3_SY);
-    for (int a = 0; a < 3; ++a) ok = ok && encode_map(h, &h->ch_maps[c].m[2 + a], h->uh[a], K3_SY);
-    ok = ok && encode_map(h, &h->mu_maps[c].m[0], phis[c], K3_SY);
+    ok = ok && encode_map(h, &h->ch_maps[c].m[0], phis[c], CH_K3_SY);
+    ok = ok && encode_map(h, &h->ch_maps[c].m[1], mus[c], CH_K3_SY);
+    for (int a = 0; a < 3; ++a) ok = ok && encode_map(h, &h->ch_maps[c].m[2 + a], h->uh[a], CH_K3_SY);
+    ok = ok && encode_map(h, &h->mu_maps[c].m[0], phis[c], MU_K3_SY);
   }
   if (!ok) return fail(h, GPE2P_ECUDA, "cuTensorMapEncodeTiled failed or is unavailable");
   return GPE2P_OK;
@@ -554,7 +554,7 @@ extern "C" int gpe2p_create(const gpe2p_params* p, void* stream, gpe2p_handle* o
   // prologue of two, and the blocks run in waves of the resident slots; take
   // the kc in [4, 64] that minimises waves x (kc + 2), the time of the slowest
   // SM.  Resident blocks per SM (registers and shared memory, as ncu reports
-  // them): flow stage FLOW_MINB, CH stage 5, mu 8.
+  // them): flow stage FLOW_MINB, CH stage CH_RESIDENT, mu MU_RESIDENT.
   if (h->prm.dim == 3) {
     const long long bx = (h->prm.nx + TX - 1) / TX;
     int nsm = 152;
@@ -571,8 +571,8 @@ extern "C" int gpe2p_create(const gpe2p_params* p, void* stream, gpe2p_handle* o
       return (int)(best_kc > h->prm.nz ? h->prm.nz : best_kc);
     };
     h->kchunk = pick(FLOW_MINB, FLOW_K3_TY);
-    h->kchunk_ch = pick(5, K3_TY);
-    h->kchunk_mu = pick(8, K3_TY);
+    h->kchunk_ch = pick(CH_RESIDENT, CH_K3_TY);
+    h->kchunk_mu = pick(MU_RESIDENT, MU_K3_TY);
   } else {
     h->kchunk = h->kchunk_ch = h->kchunk_mu = 1;
   }

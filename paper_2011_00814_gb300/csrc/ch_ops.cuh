@@ -42,6 +42,31 @@ __device__ __forceinline__ real lap_iso(const T& S, const KParams<real>& P, int 
   return P.lap_c * s;
 }
 
+// the same operator as a weighted sum per shell, sum_s w_s (sum_{|e|^2 = s}
+// f(x + e) - n_s f(x)): fewer operations, but rounding that depends on the
+// cell, so the Laplacians it sums need not cancel over the grid.  For mu,
+// which nothing conserves.
+template <typename real, int DIM, int ISO, typename T>
+__device__ __forceinline__ real lap_iso_shells(const T& S, const KParams<real>& P, int f) {
+  real s1 = real(0), s2 = real(0), s3 = real(0);
+  const real f0 = S(f, 0, 0, 0);
+#pragma unroll
+  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int sh = dx * dx + dy * dy + dz * dz;
+        if (sh == 1) s1 += S(f, dx, dy, dz);
+        if (sh == 2 && Shells<ISO>::s2) s2 += S(f, dx, dy, dz);
+        if (sh == 3 && Shells<ISO>::s3) s3 += S(f, dx, dy, dz);
+      }
+  real s = P.w1 * fma(real(-2 * DIM), f0, s1);
+  if (Shells<ISO>::s2) s = fma(P.w2, fma(real(DIM == 3 ? -12 : -4), f0, s2), s);
+  if (Shells<ISO>::s3) s = fma(P.w3, fma(real(-8), f0, s3), s);
+  return P.lap_c * s;
+}
+
 // the DIM components of the isotropic gradient of staged field f
 template <typename real, int DIM, int ISO, typename T>
 __device__ __forceinline__ void grad_iso(const T& S, const KParams<real>& P, int f, real g[3]) {

@@ -10,11 +10,9 @@
 namespace gpe2p {
 
 // 3D ring kernels (flow stage, CH stage, mu): each thread computes two cells
-// adjacent in y, so a block's tile has K3_TY = 2 TY rows and its staged
-// planes K3_SY rows
-constexpr int K3_TY = 2 * TY;
-constexpr int K3_SY = K3_TY + 2;
-
+// adjacent in y, so a block of TX x T threads has a tile of 2T rows and
+// stages planes of 2T + 2 rows.
+//
 // the 3D flow stage's block: TX x FLOW_TY threads, FLOW_K3_TY = 2 FLOW_TY rows
 // of cells, FLOW_MINB resident blocks per SM (registers: 128 per thread, so
 // 16 warps per SM at any block height).  Four warps per block rather than
@@ -28,6 +26,28 @@ constexpr int FLOW_NTHR = TX * FLOW_TY;
 constexpr int FLOW_K3_TY = 2 * FLOW_TY;
 constexpr int FLOW_K3_SY = FLOW_K3_TY + 2;
 constexpr int FLOW_MINB = 16 / FLOW_TY;
+
+// the blocks of the 3D CH stage and of mu, likewise (2 CH_TY and 2 MU_TY rows
+// of cells), and the blocks of each that fit on an SM: the FP32 CH stage is
+// held by registers (48 a thread) to 40 warps, mu by threads to 64.  Four
+// warps per CH block measured 0.552 against 0.576 ms for stage 1 (the other
+// stages unchanged); mu keeps eight (four measured 1.5 % slower).
+#ifndef GPE2P_CH_TY
+#define GPE2P_CH_TY 4
+#endif
+#ifndef GPE2P_MU_TY
+#define GPE2P_MU_TY 8
+#endif
+constexpr int CH_TY = GPE2P_CH_TY;
+constexpr int CH_NTHR = TX * CH_TY;
+constexpr int CH_K3_TY = 2 * CH_TY;
+constexpr int CH_K3_SY = CH_K3_TY + 2;
+constexpr int CH_RESIDENT = 40 / CH_TY;
+constexpr int MU_TY = GPE2P_MU_TY;
+constexpr int MU_NTHR = TX * MU_TY;
+constexpr int MU_K3_TY = 2 * MU_TY;
+constexpr int MU_K3_SY = MU_K3_TY + 2;
+constexpr int MU_RESIDENT = 64 / MU_TY;
 
 // one flow stage: out = a q0 + b (q + dt L(q))   (Eq. tvd-rk3)
 template <typename real>
