@@ -29,40 +29,50 @@ __global__ void __launch_bounds__(DIAG_THREADS) diag_partial_kernel(const KParam
                                                                     const real* u0, const real* u1,
                                                                     const real* u2, const real* phi,
                                                                     const real* phi_lo, double* partial) {
-  const long long n = (long long)P.n[0] * P.n[1] * P.n[2];
-  double sphi = 0.0, ke = 0.0, umax = 0.0, bad = 0.0;
+  // blocks stride over the rows (j, k), threads along x; per cell, in FP64:
+  // phi, and for each face the face density (the mean of the two cells'
+  // rho(phi) = (rhoL + rhoG)/2 + phi (rhoL - rhoG)/2) times u^2; the factor
+  // 1/2 of the kinetic energy is applied once per thread
+  const int nx = P.n[0], ny = P.n[1];
+  const long long rows = (long long)ny * P.n[2];
+  const double rm = 0.5 * ((double)P.rhoL + (double)P.rhoG), rd = 0.25 * ((double)P.rhoL - (double)P.rhoG);
+  double sphi = 0.0, ke = 0.0;
+  real umax = real(0);
+  bool bad = false;
   const real* U[3] = {u0, u1, u2};
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
-       id += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(id % P.n[0]);
-    const int j = (int)((id / P.n[0]) % P.n[1]);
-    const int k = (int)(id / ((long long)P.n[0] * P.n[1]));
-    const long long q = lin(P, i, j, k);
-    const double f = (double)phi[q] + (phi_lo ? (double)phi_lo[q] : 0.0);
-    sphi += f;
-    if (!isfinite(f) || !isfinite((double)p[q])) bad = 1.0;
-    const double rho0 = 0.5 * ((double)P.rhoL * (1.0 + f) + (double)P.rhoG * (1.0 - f));
+  for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int j = (int)(r % ny), k = (int)(r / ny);
+    const long long q0 = lin(P, 0, j, k);
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const long long q = q0 + i;
+      const real fr = phi[q];
+      const double f = (double)fr + (phi_lo ? (double)phi_lo[q] : 0.0);
+      sphi += f;
+      bad = bad || !isfinite(fr) || !isfinite(p[q]);
 #pragma unroll
-    for (int c = 0; c < DIM; ++c) {
-      const double fm = (double)ld_cen(phi, P, i - (c == 0), j - (c == 1), k - (c == 2));
-      const double rhom = 0.5 * ((double)P.rhoL * (1.0 + fm) + (double)P.rhoG * (1.0 - fm));
-      const double uc = (double)U[c][q];
-      ke += 0.5 * (0.5 * (rhom + rho0)) * uc * uc;
-      umax = fmax(umax, fabs(uc));
-      if (!isfinite(uc)) bad = 1.0;
+      for (int c = 0; c < DIM; ++c) {
+        const double fm = (double)ld_cen(phi, P, i - (c == 0), j - (c == 1), k - (c == 2));
+        const real uc = U[c][q];
+        const double ud = (double)uc;
+        ke = fma(fma(rd, fm + f, rm), ud * ud, ke);
+        umax = fmax(umax, fabs(uc));
+        bad = bad || !isfinite(uc);
+      }
     }
   }
+  ke *= 0.5;
+  double umaxd = (double)umax, badd = bad ? 1.0 : 0.0;
   __shared__ double red[4][DIAG_THREADS / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   sphi = warp_sum(sphi);
   ke = warp_sum(ke);
-  umax = warp_max(umax);
-  bad = warp_max(bad);
+  umaxd = warp_max(umaxd);
+  badd = warp_max(badd);
   if (lane == 0) {
     red[0][wid] = sphi;
     red[1][wid] = ke;
-    red[2][wid] = umax;
-    red[3][wid] = bad;
+    red[2][wid] = umaxd;
+    red[3][wid] = badd;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
