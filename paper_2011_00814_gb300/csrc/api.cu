@@ -38,6 +38,7 @@ struct gpe2p_ctx {
   void* mus = nullptr;          // mu of a CH stage state
   void* acc = nullptr;          // RK4 accumulator
   void* uh[3] = {};             // time-centred cell velocity
+  void* usum[3] = {};           // u^n + u^{n+1} per face (3D advective steps)
   double* d_stage = nullptr;    // one FP64 field for host transfers
   double* d_part = nullptr;     // reduction scratch: 4 doubles per block
   double* d_out = nullptr;      // 4 reduced values
@@ -324,6 +325,10 @@ static cudaError_t enqueue_step(gpe2p_ctx* h, int cur, ProfHook* hook = nullptr)
   for (int f = 0; f < 4; ++f) { A.q[f] = q(s2, f); A.out[f] = q(s1, f); }
   A.a = real(1.0 / 3.0);
   A.b = real(2.0 / 3.0);
+  // 3D advective steps: the last stage also leaves u^n + u^{n+1} per face
+  const bool usum = DIM == 3 && !h->prm.ch_advection;
+  if (usum)
+    for (int a = 0; a < 3; ++a) A.usum[a] = (real*)h->usum[a];
   if ((e = launch_flow_stage<real, DIM>(P, A, 2, h->kchunk, s, &h->flow_maps[s2], h->d_err)) != cudaSuccess)
     return e;
   if ((e = mark("flow_stage3")) != cudaSuccess) return e;
@@ -334,6 +339,7 @@ static cudaError_t enqueue_step(gpe2p_ctx* h, int cur, ProfHook* hook = nullptr)
     C.uh[a] = (real*)h->uh[a];
     C.u0[a] = q(cur, 1 + a);
     C.u1[a] = q(s1, 1 + a);
+    C.usum[a] = usum ? (const real*)h->usum[a] : nullptr;
   }
   C.scheme = h->prm.ch_scheme;
   C.conservative = h->prm.ch_advection;
@@ -505,11 +511,12 @@ extern "C" int gpe2p_create(const gpe2p_params* p, void* stream, gpe2p_handle* o
     }
     h->own_stream = true;
   }
-  // layout: 12 velocity/pressure fields, phi, mu, 2 stage phi, mus, acc, 3 uhat;
+  // layout: 12 velocity/pressure fields, phi, mu, 2 stage phi, mus, acc, 3 uhat,
+  // 3 face-velocity sums;
   // every field has rows padded to a multiple of 32 elements (TMA strides)
   h->pitch = row_pitch(h->prm.nx);
   const size_t fb = align256((size_t)h->pitch * h->prm.ny * h->prm.nz * h->esize);
-  const int nfield = 12 + 2 + 2 + 1 + 1 + 3;
+  const int nfield = 12 + 2 + 2 + 1 + 1 + 3 + 3;
   const size_t stage_b = align256((size_t)h->ncell * sizeof(double));
   const long long nb_blocks = (h->ncell + 255) / 256;
   h->nblk = (int)(nb_blocks < 152 * 8 ? nb_blocks : 152 * 8);
@@ -531,6 +538,7 @@ extern "C" int gpe2p_create(const gpe2p_params* p, void* stream, gpe2p_handle* o
   h->mus = c; c += fb;
   h->acc = c; c += fb;
   for (int a = 0; a < 3; ++a) { h->uh[a] = c; c += fb; }
+  for (int a = 0; a < 3; ++a) { h->usum[a] = c; c += fb; }
   h->d_stage = (double*)c; c += stage_b;
   h->d_part = (double*)c; c += part_b;
   h->d_out = (double*)c;

@@ -77,7 +77,7 @@ __device__ __forceinline__ bool ring_acquire(Ring<real, NRAW, RING, SYv>& R, con
 // One block: a TX x CH_K3_TY column of cells over the planes [kbeg, kend);
 // thread (tx, ty) takes the cells (i0 + tx, j0 + 2 ty + r), r = 0, 1, whose
 // stencils share most of their loads.
-template <typename real, int ISO, int CONS, int RING>
+template <typename real, int ISO, int CONS, int RING, bool USUM>
 __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ Maps<5> maps,
                                                     const __grid_constant__ KParams<real> P,
                                                     const CHArgs<real> A, const int kchunk, int* err) {
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
     CHPoint<real> c[2];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
-      if (act[r]) ch_point_load<real, 3>(P, A, i, ja + r, k, c[r]);
+      if (act[r]) ch_point_load<real, 3, USUM>(P, A, i, ja + r, k, c[r]);
     if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, k + 1, true, edge_tile, fix)) { R.fail(err, k + 1); return; }
     if (edge_tile || k + 1 >= P.n[2]) __syncthreads();  // out-of-domain writes seen by all
     real L[2], ph0[2];
@@ -226,16 +226,22 @@ static cudaError_t ch_go(const KParams<real>& P, const CHArgs<real>& A, int kchu
     constexpr int RING = ch_ring<real>();
     if (A.conservative) {
       const size_t sm = ring_smem_bytes<real, 5, 0, RING, CH_K3_SY>();
-      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 1, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 1, RING, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)sm);
       if (e != cudaSuccess) return e;
-      ch3d_kernel<real, ISO, 1, RING><<<grd, blk, sm, s>>>(*maps, P, A, kchunk, err);
+      ch3d_kernel<real, ISO, 1, RING, false><<<grd, blk, sm, s>>>(*maps, P, A, kchunk, err);
+    } else if (A.compute_uh && A.usum[0]) {
+      const size_t sm = ring_smem_bytes<real, 2, 0, RING, CH_K3_SY>();
+      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 0, RING, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sm);
+      if (e != cudaSuccess) return e;
+      ch3d_kernel<real, ISO, 0, RING, true><<<grd, blk, sm, s>>>(*maps, P, A, kchunk, err);
     } else {
       const size_t sm = ring_smem_bytes<real, 2, 0, RING, CH_K3_SY>();
-      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 0, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 0, RING, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)sm);
       if (e != cudaSuccess) return e;
-      ch3d_kernel<real, ISO, 0, RING><<<grd, blk, sm, s>>>(*maps, P, A, kchunk, err);
+      ch3d_kernel<real, ISO, 0, RING, false><<<grd, blk, sm, s>>>(*maps, P, A, kchunk, err);
     }
   } else {
     const size_t sm = ch2d_smem<real>();

@@ -126,12 +126,18 @@ struct CHPoint {
   real pnl;  // low part of phi^{n+1/2} (compensated accumulation)
 };
 
-template <typename real, int DIM>
+// USUM: the stage-1 uhat from the face sums u^n + u^{n+1} the last flow stage
+// left in A.usum: uhat_a = (s_a + s_a(+e_a)) / 4
+template <typename real, int DIM, bool USUM = false>
 __device__ __forceinline__ void ch_point_load(const KParams<real>& P, const CHArgs<real>& A, int i, int j, int k,
                                               CHPoint<real>& c) {
   const long long id = lin(P, i, j, k);
   if (!A.conservative) {
-    if (A.compute_uh) {
+    if (USUM) {
+      c.uh[0] = real(0.25) * (A.usum[0][id] + face_next<0>(A.usum[0], P, i, j, k, id));
+      c.uh[1] = real(0.25) * (A.usum[1][id] + face_next<1>(A.usum[1], P, i, j, k, id));
+      if (DIM == 3) c.uh[2] = real(0.25) * (A.usum[2][id] + face_next<2>(A.usum[2], P, i, j, k, id));
+    } else if (A.compute_uh) {
       c.uh[0] = real(0.25) * ((A.u0[0][id] + face_next<0>(A.u0[0], P, i, j, k, id)) +
                               (A.u1[0][id] + face_next<0>(A.u1[0], P, i, j, k, id)));
       c.uh[1] = real(0.25) * ((A.u0[1][id] + face_next<1>(A.u0[1], P, i, j, k, id)) +

@@ -181,6 +181,16 @@ __global__ void __launch_bounds__(FLOW_NTHR, FLOW_MINB) flow3d_kernel(const __gr
 #pragma unroll
         for (int f = 0; f < 4; ++f) A.out[f][id + r * P.sy] = out[r][f];
       }
+    // the last stage also leaves u^n + u^{n+1} on every face, from which the
+    // CH step forms the time-centred cell velocity with half the loads
+    if (MODE == 2 && A.usum[0]) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+        if (act[r]) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) A.usum[a][id + r * P.sy] = q0v[r][1 + a] + out[r][1 + a];
+        }
+    }
   }
 }
 

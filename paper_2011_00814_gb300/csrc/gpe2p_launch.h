@@ -58,6 +58,7 @@ struct FlowArgs {
   const real* phi;     // frozen at t^{n+1/2}
   const real* mu;
   real a, b;
+  real* usum[3];       // 3D mode 2 (last stage): if set, also u0_c + u^{n+1}_c on every face
 };
 
 // one Cahn-Hilliard stage (Eqs. che, tvd-rk2, rk4) or its rate
@@ -71,6 +72,7 @@ struct CHArgs {
   real* uh[3];         // time-centred cell velocity (written when compute_uh)
   const real* u0[3];   // face velocity at t^n      (read when compute_uh)
   const real* u1[3];   // face velocity at t^{n+1}  (read when compute_uh)
+  const real* usum[3]; // if set (3D): u0 + u1 per face, read instead of u0 and u1
   int scheme;          // 2 or 4
   int stage;           // 1..scheme; 0 = write the rate L only
   int compute_uh;      // 1: build uhat (Eq. u-center-2d) from u0, u1 and store it
