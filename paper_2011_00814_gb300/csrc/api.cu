@@ -50,6 +50,7 @@ struct gpe2p_ctx {
   Maps<6> flow_maps[3];         // stage input Q[set] (p, u, v, w), phi, mu
   Maps<5> ch_maps[3];           // (phi, mu), (phis0, mus), (phis1, mus), each with uhat
   Maps<1> mu_maps[3];           // phi, phis0, phis1
+  Maps<5> pt_maps;              // uhat x 3, phi, acc: point boxes of a CH block's cells
   int cur = 0;                  // which Q set holds q^n (0 or 1)
   long long step = 0;
   int kchunk = 8;                // z-chunk of the flow stage
@@ -361,7 +362,7 @@ static cudaError_t enqueue_step(gpe2p_ctx* h, int cur, ProfHook* hook = nullptr)
   const int iso = h->prm.iso;
   auto ch = [&](const real* phis) {
     const int mi = phis == phi ? 0 : (phis == F0 ? 1 : 2);
-    return launch_ch_stage<real, DIM>(P, C, iso, h->kchunk_ch, s, &h->ch_maps[mi], h->d_err);
+    return launch_ch_stage<real, DIM>(P, C, iso, h->kchunk_ch, s, &h->ch_maps[mi], h->d_err, &h->pt_maps);
   };
   auto mu_of = [&](const real* f, real* out) {
     const int mi = f == phi ? 0 : (f == F0 ? 1 : 2);
@@ -436,14 +437,15 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// a field as a 3D tensor (x, y, z) with padded rows; box = one staged plane of `rows` rows
-static bool encode_map(gpe2p_ctx* h, CUtensorMap* m, void* base, int rows) {
+// a field as a 3D tensor (x, y, z) with padded rows; box = one staged plane of
+// `rows` rows (width: the staged row with its halo, or bx0 elements when given)
+static bool encode_map(gpe2p_ctx* h, CUtensorMap* m, void* base, int rows, int bx0 = 0) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return false;
   const int es = h->esize;
   cuuint64_t dims[3] = {(cuuint64_t)h->prm.nx, (cuuint64_t)h->prm.ny, (cuuint64_t)h->prm.nz};
   cuuint64_t strides[2] = {(cuuint64_t)(h->pitch * es), (cuuint64_t)(h->pitch * h->prm.ny * es)};
-  const int bx = es == 4 ? RingGeom<float>::BX : RingGeom<double>::BX;
+  const int bx = bx0 > 0 ? bx0 : (es == 4 ? RingGeom<float>::BX : RingGeom<double>::BX);
   cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(m, es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base, dims,
@@ -467,6 +469,9 @@ static int build_maps(gpe2p_ctx* h) {
     for (int a = 0; a < 3; ++a) ok = ok && encode_map(h, &h->ch_maps[c].m[2 + a], h->uh[a], CH_K3_SY);
     ok = ok && encode_map(h, &h->mu_maps[c].m[0], phis[c], MU_K3_SY);
   }
+  for (int a = 0; a < 3; ++a) ok = ok && encode_map(h, &h->pt_maps.m[a], h->uh[a], CH_K3_TY, TX);
+  ok = ok && encode_map(h, &h->pt_maps.m[3], h->phi, CH_K3_TY, TX);
+  ok = ok && encode_map(h, &h->pt_maps.m[4], h->acc, CH_K3_TY, TX);
   if (!ok) return fail(h, GPE2P_ECUDA, "cuTensorMapEncodeTiled failed or is unavailable");
   return GPE2P_OK;
 }

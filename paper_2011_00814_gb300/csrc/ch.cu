@@ -77,8 +77,17 @@ __device__ __forceinline__ bool ring_acquire(Ring<real, NRAW, RING, SYv>& R, con
 // One block: a TX x CH_K3_TY column of cells over the planes [kbeg, kend);
 // thread (tx, ty) takes the cells (i0 + tx, j0 + 2 ty + r), r = 0, 1, whose
 // stencils share most of their loads.
-template <typename real, int ISO, int CONS, int RING, bool USUM>
+// PTS: an advective stage after the first takes its per-cell values (uhat,
+// phi^{n+1/2}, the accumulator) from point planes that TMA brings in one
+// plane ahead (boxes of the block's own TX x CH_K3_TY cells, no halo, two
+// slots after the ring) instead of loading them per thread; pmaps: uhat x 3,
+// phi^{n+1/2}, the accumulator.  The low part of phi stays a per-thread load.
+constexpr int CP_N = 5;                  // point fields
+constexpr int CP_PT = TX * CH_K3_TY;     // reals per field-plane
+
+template <typename real, int ISO, int CONS, int RING, bool USUM, bool PTS>
 __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ Maps<5> maps,
+                                                    const __grid_constant__ Maps<5> pmaps,
                                                     const __grid_constant__ KParams<real> P,
                                                     const CHArgs<real> A, const int kchunk, int* err) {
   constexpr int NRAW = CONS ? 5 : 2;
@@ -105,17 +114,63 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
       default: return ld_cvec<2>(A.uh[2], P, ci, cj, kk);
     }
   };
+  // point planes (PTS): two slots after the ring, their barriers after the ring's
+  const int tid = ty * TX + tx;
+  uint64_t* pbar = R.bar + 8;
+  real* pts = R.raw + (size_t)RING * NRAW * G::PE;
+  const bool need_acc = (A.scheme == 4 && A.stage >= 2) || (A.phi_lo && A.scheme == 2 && A.stage == 2);
+  int pissued = kbeg - 1;  // thread 0: last point plane issued
+  auto pissue = [&](int kk) {
+    if (kk >= kend) return;
+    uint64_t* b = &pbar[(kk - kbeg) & 1];
+    real* dst = pts + (size_t)((kk - kbeg) & 1) * CP_N * CP_PT;
+    mbar_arrive_expect_tx(b, (uint32_t)((need_acc ? 5 : 4) * CP_PT * sizeof(real)));
+#pragma unroll
+    for (int f = 0; f < 4; ++f) tma_load_3d(dst + f * CP_PT, &pmaps.m[f], i0, j0, kk, b);
+    if (need_acc) tma_load_3d(dst + 4 * CP_PT, &pmaps.m[4], i0, j0, kk, b);
+    pissued = kk;
+  };
+  // after a ring timeout: let this block's point copies in flight land
+  auto pdrain = [&](int from) {
+    if (PTS && tid == 0)
+      for (int kk = from; kk <= pissued; ++kk)
+        mbar_wait_bounded(&pbar[(kk - kbeg) & 1], ((kk - kbeg) >> 1) & 1, WAIT_CYCLES / 2);
+  };
+  if (PTS && tid == 0) {
+    mbar_init(&pbar[0], 1);
+    mbar_init(&pbar[1], 1);
+  }
   R.start(P, maps.m, kbeg, kend, i0, j0);
-  if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, kbeg - 1, false, edge_tile, fix)) { R.fail(err, kbeg - 1); return; }
-  if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, kbeg, false, edge_tile, fix)) { R.fail(err, kbeg); return; }
+  if (PTS && tid == 0) pissue(kbeg);
+  if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, kbeg - 1, false, edge_tile, fix)) { R.fail(err, kbeg - 1); pdrain(kbeg); return; }
+  if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, kbeg, false, edge_tile, fix)) { R.fail(err, kbeg); pdrain(kbeg); return; }
   const real* smr = reinterpret_cast<const real*>(smraw);
   const int raw0 = (int)(R.raw - smr), cell0 = G::at(tx + 1, 2 * ty + 1);
   for (int k = kbeg; k < kend; ++k) {
     CHPoint<real> c[2];
+    if (PTS) {
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
-      if (act[r]) ch_point_load<real, 3, USUM>(P, A, i, ja + r, k, c[r]);
-    if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, k + 1, true, edge_tile, fix)) { R.fail(err, k + 1); return; }
+      for (int r = 0; r < 2; ++r)
+        c[r].pnl = (A.phi_lo && act[r]) ? A.phi_lo[lin(P, i, ja + r, k)] : real(0);
+    } else {
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+        if (act[r]) ch_point_load<real, 3, USUM>(P, A, i, ja + r, k, c[r]);
+    }
+    if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, k + 1, true, edge_tile, fix)) { R.fail(err, k + 1); pdrain(k); return; }
+    if (PTS) {
+      // every thread is past plane k - 1: its slot takes plane k + 1
+      if (tid == 0) pissue(k + 1);
+      if (!mbar_wait_bounded(&pbar[(k - kbeg) & 1], ((k - kbeg) >> 1) & 1, WAIT_CYCLES)) atomicExch(err, ERR_TMA_TIMEOUT);
+      const real* pp = pts + (size_t)((k - kbeg) & 1) * CP_N * CP_PT + (2 * ty) * TX + tx;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) c[r].uh[a] = pp[a * CP_PT + r * TX];
+        c[r].pn = pp[3 * CP_PT + r * TX];
+        c[r].acc = pp[4 * CP_PT + r * TX];
+      }
+    }
     if (edge_tile || k + 1 >= P.n[2]) __syncthreads();  // out-of-domain writes seen by all
     real L[2], ph0[2];
 #pragma unroll
@@ -216,7 +271,7 @@ static size_t ch2d_smem() {
 
 template <typename real, int DIM, int ISO>
 static cudaError_t ch_go(const KParams<real>& P, const CHArgs<real>& A, int kchunk, cudaStream_t s,
-                         const Maps<5>* maps, int* err) {
+                         const Maps<5>* maps, int* err, const Maps<5>* pmaps) {
   dim3 blk(TX, TY, 1);
   dim3 grd((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY, DIM == 3 ? (P.n[2] + kchunk - 1) / kchunk : 1);
   cudaError_t e;
@@ -226,22 +281,28 @@ static cudaError_t ch_go(const KParams<real>& P, const CHArgs<real>& A, int kchu
     constexpr int RING = ch_ring<real>();
     if (A.conservative) {
       const size_t sm = ring_smem_bytes<real, 5, 0, RING, CH_K3_SY>();
-      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 1, RING, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)sm);
+      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 1, RING, false, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
-      ch3d_kernel<real, ISO, 1, RING, false><<<grd, blk, sm, s>>>(*maps, P, A, kchunk, err);
+      ch3d_kernel<real, ISO, 1, RING, false, false><<<grd, blk, sm, s>>>(*maps, *maps, P, A, kchunk, err);
     } else if (A.compute_uh && A.usum[0]) {
       const size_t sm = ring_smem_bytes<real, 2, 0, RING, CH_K3_SY>();
-      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 0, RING, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)sm);
+      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 0, RING, true, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
-      ch3d_kernel<real, ISO, 0, RING, true><<<grd, blk, sm, s>>>(*maps, P, A, kchunk, err);
+      ch3d_kernel<real, ISO, 0, RING, true, false><<<grd, blk, sm, s>>>(*maps, *maps, P, A, kchunk, err);
+    } else if (!A.compute_uh && A.stage != 0 && pmaps) {
+      const size_t sm = ring_smem_bytes<real, 2, 0, RING, CH_K3_SY>() + sizeof(real) * (size_t)2 * CP_N * CP_PT;
+      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 0, RING, false, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+      ch3d_kernel<real, ISO, 0, RING, false, true><<<grd, blk, sm, s>>>(*maps, *pmaps, P, A, kchunk, err);
     } else {
       const size_t sm = ring_smem_bytes<real, 2, 0, RING, CH_K3_SY>();
-      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 0, RING, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)sm);
+      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 0, RING, false, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
-      ch3d_kernel<real, ISO, 0, RING, false><<<grd, blk, sm, s>>>(*maps, P, A, kchunk, err);
+      ch3d_kernel<real, ISO, 0, RING, false, false><<<grd, blk, sm, s>>>(*maps, *maps, P, A, kchunk, err);
     }
   } else {
     const size_t sm = ch2d_smem<real>();
@@ -254,14 +315,14 @@ static cudaError_t ch_go(const KParams<real>& P, const CHArgs<real>& A, int kchu
 
 template <typename real, int DIM>
 cudaError_t launch_ch_stage(const KParams<real>& P, const CHArgs<real>& A, int iso, int kchunk,
-                            cudaStream_t s, const Maps<5>* maps, int* err) {
+                            cudaStream_t s, const Maps<5>* maps, int* err, const Maps<5>* pmaps) {
   if constexpr (DIM == 2) {
-    return ch_go<real, DIM, 9>(P, A, kchunk, s, maps, err);
+    return ch_go<real, DIM, 9>(P, A, kchunk, s, maps, err, nullptr);
   } else {
     switch (iso) {
-      case 15: return ch_go<real, DIM, 15>(P, A, kchunk, s, maps, err);
-      case 19: return ch_go<real, DIM, 19>(P, A, kchunk, s, maps, err);
-      default: return ch_go<real, DIM, 27>(P, A, kchunk, s, maps, err);
+      case 15: return ch_go<real, DIM, 15>(P, A, kchunk, s, maps, err, pmaps);
+      case 19: return ch_go<real, DIM, 19>(P, A, kchunk, s, maps, err, pmaps);
+      default: return ch_go<real, DIM, 27>(P, A, kchunk, s, maps, err, pmaps);
     }
   }
 }
@@ -313,7 +374,7 @@ cudaError_t launch_center_velocity(const KParams<real>& P, const real* const u0[
 
 #define GPE2P_CH_INST(R, D)                                                                                 \
   template cudaError_t launch_ch_stage<R, D>(const KParams<R>&, const CHArgs<R>&, int, int, cudaStream_t,   \
-                                             const Maps<5>*, int*);                                        \
+                                             const Maps<5>*, int*, const Maps<5>*);                        \
   template cudaError_t launch_mu<R, D>(const KParams<R>&, const R*, R*, int, int, cudaStream_t, const Maps<1>*, \
                                        int*);                                                              \
   template cudaError_t launch_center_velocity<R, D>(const KParams<R>&, const R* const[3], const R* const[3], \
