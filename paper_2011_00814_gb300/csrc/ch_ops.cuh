@@ -212,7 +212,7 @@ __device__ __forceinline__ void ch_finish(const KParams<real>& P, const CHArgs<r
     const real d = P.dt * L;
     double od;
     if (A.scheme == 2) od = pn + 0.5 * ((double)c.acc + (double)d);
-    else od = pn + ((double)c.acc + (double)d) / 6.0;
+    else od = fma((double)c.acc + (double)d, 1.0 / 6.0, pn);
     const real hi = (real)od;
     A.phi_lo[id] = (real)(od - (double)hi);
     A.out[id] = hi;
@@ -234,7 +234,7 @@ __device__ __forceinline__ void ch_finish(const KParams<real>& P, const CHArgs<r
     if (A.stage == 1) { A.acc[id] = d; o = pn + real(0.5) * d; }
     else if (A.stage == 2) { A.acc[id] = c.acc + real(2) * d; o = pn + real(0.5) * d; }
     else if (A.stage == 3) { A.acc[id] = c.acc + real(2) * d; o = pn + d; }
-    else { o = pn + (c.acc + d) / real(6); }
+    else { o = fma(c.acc + d, real(1.0 / 6.0), pn); }  // a multiply, not an IEEE divide
   }
   A.out[id] = o;
 }
