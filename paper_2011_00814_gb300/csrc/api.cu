@@ -51,6 +51,7 @@ struct gpe2p_ctx {
   Maps<5> ch_maps[3];           // (phi, mu), (phis0, mus), (phis1, mus), each with uhat
   Maps<1> mu_maps[3];           // phi, phis0, phis1
   Maps<5> pt_maps;              // uhat x 3, phi, acc: point boxes of a CH block's cells
+  Maps<5> us_maps;              // face sums s_x, s_y, s_z with the faces above a CH block's cells
   int cur = 0;                  // which Q set holds q^n (0 or 1)
   long long step = 0;
   int kchunk = 8;                // z-chunk of the flow stage
@@ -362,7 +363,8 @@ static cudaError_t enqueue_step(gpe2p_ctx* h, int cur, ProfHook* hook = nullptr)
   const int iso = h->prm.iso;
   auto ch = [&](const real* phis) {
     const int mi = phis == phi ? 0 : (phis == F0 ? 1 : 2);
-    return launch_ch_stage<real, DIM>(P, C, iso, h->kchunk_ch, s, &h->ch_maps[mi], h->d_err, &h->pt_maps);
+    return launch_ch_stage<real, DIM>(P, C, iso, h->kchunk_ch, s, &h->ch_maps[mi], h->d_err, &h->pt_maps,
+                                      &h->us_maps);
   };
   auto mu_of = [&](const real* f, real* out) {
     const int mi = f == phi ? 0 : (f == F0 ? 1 : 2);
@@ -470,6 +472,10 @@ static int build_maps(gpe2p_ctx* h) {
     ok = ok && encode_map(h, &h->mu_maps[c].m[0], phis[c], MU_K3_SY);
   }
   for (int a = 0; a < 3; ++a) ok = ok && encode_map(h, &h->pt_maps.m[a], h->uh[a], CH_K3_TY, TX);
+  ok = ok && encode_map(h, &h->us_maps.m[0], h->usum[0], CH_K3_TY, TX + 4);
+  ok = ok && encode_map(h, &h->us_maps.m[1], h->usum[1], CH_K3_TY + 1, TX);
+  ok = ok && encode_map(h, &h->us_maps.m[2], h->usum[2], CH_K3_TY, TX);
+  h->us_maps.m[3] = h->us_maps.m[4] = h->us_maps.m[2];
   ok = ok && encode_map(h, &h->pt_maps.m[3], h->phi, CH_K3_TY, TX);
   ok = ok && encode_map(h, &h->pt_maps.m[4], h->acc, CH_K3_TY, TX);
   if (!ok) return fail(h, GPE2P_ECUDA, "cuTensorMapEncodeTiled failed or is unavailable");

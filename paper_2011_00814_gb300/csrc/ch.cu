@@ -84,8 +84,13 @@ __device__ __forceinline__ bool ring_acquire(Ring<real, NRAW, RING, SYv>& R, con
 // phi^{n+1/2}, the accumulator.  The low part of phi stays a per-thread load.
 constexpr int CP_N = 5;                  // point fields
 constexpr int CP_PT = TX * CH_K3_TY;     // reals per field-plane
+// UPTS (with USUM): stage 1 takes the face sums the same way, each with the
+// face above the cell: s_x boxes of (TX + 4) x CH_K3_TY, s_y TX x (CH_K3_TY + 1),
+// s_z TX x CH_K3_TY of planes k and k + 1, in three slots (pmaps: s_x, s_y, s_z)
+constexpr int US_X = (TX + 4) * CH_K3_TY, US_Y = TX * (CH_K3_TY + 1), US_Z = TX * CH_K3_TY;
+constexpr int US_SLOT = US_X + US_Y + US_Z;
 
-template <typename real, int ISO, int CONS, int RING, bool USUM, bool PTS>
+template <typename real, int ISO, int CONS, int RING, bool USUM, bool PTS, bool UPTS>
 __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ Maps<5> maps,
                                                     const __grid_constant__ Maps<5> pmaps,
                                                     const __grid_constant__ KParams<real> P,
@@ -136,19 +141,44 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
       for (int kk = from; kk <= pissued; ++kk)
         mbar_wait_bounded(&pbar[(kk - kbeg) & 1], ((kk - kbeg) >> 1) & 1, WAIT_CYCLES / 2);
   };
-  if (PTS && tid == 0) {
+  // UPTS: the face-sum point planes kbeg .. klast
+  const int klast = min(kend, P.n[2] - 1);
+  int uissued = kbeg - 1;  // thread 0: last face-sum plane issued
+  auto uslot = [&](int kk) { return (kk - kbeg) % 3; };
+  auto upar = [&](int kk) { return (uint32_t)(((kk - kbeg) / 3) & 1); };
+  auto uissue = [&](int kk) {
+    if (kk > klast) return;
+    uint64_t* b = &pbar[uslot(kk)];
+    real* dst = pts + (size_t)uslot(kk) * US_SLOT;
+    mbar_arrive_expect_tx(b, (uint32_t)(US_SLOT * sizeof(real)));
+    tma_load_3d(dst, &pmaps.m[0], i0, j0, kk, b);
+    tma_load_3d(dst + US_X, &pmaps.m[1], i0, j0, kk, b);
+    tma_load_3d(dst + US_X + US_Y, &pmaps.m[2], i0, j0, kk, b);
+    uissued = kk;
+  };
+  auto udrain = [&](int from) {
+    if (UPTS && tid == 0)
+      for (int kk = from; kk <= uissued; ++kk) mbar_wait_bounded(&pbar[uslot(kk)], upar(kk), WAIT_CYCLES / 2);
+  };
+  if ((PTS || UPTS) && tid == 0) {
     mbar_init(&pbar[0], 1);
     mbar_init(&pbar[1], 1);
+    mbar_init(&pbar[2], 1);
   }
   R.start(P, maps.m, kbeg, kend, i0, j0);
   if (PTS && tid == 0) pissue(kbeg);
-  if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, kbeg - 1, false, edge_tile, fix)) { R.fail(err, kbeg - 1); pdrain(kbeg); return; }
-  if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, kbeg, false, edge_tile, fix)) { R.fail(err, kbeg); pdrain(kbeg); return; }
+  if (UPTS && tid == 0) {
+    uissue(kbeg);
+    uissue(kbeg + 1);
+  }
+  if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, kbeg - 1, false, edge_tile, fix)) { R.fail(err, kbeg - 1); pdrain(kbeg); udrain(kbeg); return; }
+  if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, kbeg, false, edge_tile, fix)) { R.fail(err, kbeg); pdrain(kbeg); udrain(kbeg); return; }
+  if (UPTS && !mbar_wait_bounded(&pbar[uslot(kbeg)], upar(kbeg), WAIT_CYCLES)) atomicExch(err, ERR_TMA_TIMEOUT);
   const real* smr = reinterpret_cast<const real*>(smraw);
   const int raw0 = (int)(R.raw - smr), cell0 = G::at(tx + 1, 2 * ty + 1);
   for (int k = kbeg; k < kend; ++k) {
     CHPoint<real> c[2];
-    if (PTS) {
+    if (PTS || UPTS) {
 #pragma unroll
       for (int r = 0; r < 2; ++r)
         c[r].pnl = (A.phi_lo && act[r]) ? A.phi_lo[lin(P, i, ja + r, k)] : real(0);
@@ -157,7 +187,35 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
       for (int r = 0; r < 2; ++r)
         if (act[r]) ch_point_load<real, 3, USUM>(P, A, i, ja + r, k, c[r]);
     }
-    if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, k + 1, true, edge_tile, fix)) { R.fail(err, k + 1); pdrain(k); return; }
+    if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, k + 1, true, edge_tile, fix)) { R.fail(err, k + 1); pdrain(k); udrain(k + 1); return; }
+    if (UPTS) {
+      // every thread is past plane k - 1: its slot takes plane k + 2
+      if (tid == 0) uissue(k + 2);
+      if (k + 1 <= klast && !mbar_wait_bounded(&pbar[uslot(k + 1)], upar(k + 1), WAIT_CYCLES))
+        atomicExch(err, ERR_TMA_TIMEOUT);
+      const real* sb = pts + (size_t)uslot(k) * US_SLOT;
+      const real* sz1p = pts + (size_t)uslot(k + 1) * US_SLOT + US_X + US_Y;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int row = 2 * ty + r, j = ja + r;
+        const real sx0 = sb[row * (TX + 4) + tx];
+        real sx1 = sb[row * (TX + 4) + tx + 1];
+        const real sy0 = sb[US_X + row * TX + tx];
+        real sy1 = sb[US_X + (row + 1) * TX + tx];
+        const real sz0 = sb[US_X + US_Y + row * TX + tx];
+        real sz1 = k + 1 <= klast ? sz1p[row * TX + tx] : real(0);
+        // the face above the cell on a periodic axis's far end is face 0 (a
+        // wall face beyond the domain reads zero, as the box fill gives it)
+        if (act[r]) {
+          if (P.bc[0] == BC_PERIODIC && i + 1 == P.n[0]) sx1 = A.usum[0][lin(P, 0, j, k)];
+          if (P.bc[1] == BC_PERIODIC && j + 1 == P.n[1]) sy1 = A.usum[1][lin(P, i, 0, k)];
+          if (P.bc[2] == BC_PERIODIC && k + 1 == P.n[2]) sz1 = A.usum[2][lin(P, i, j, 0)];
+        }
+        c[r].uh[0] = real(0.25) * (sx0 + sx1);
+        c[r].uh[1] = real(0.25) * (sy0 + sy1);
+        c[r].uh[2] = real(0.25) * (sz0 + sz1);
+      }
+    }
     if (PTS) {
       // every thread is past plane k - 1: its slot takes plane k + 1
       if (tid == 0) pissue(k + 1);
@@ -181,6 +239,7 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
       for (int dz = -1; dz <= 1; ++dz) S.r[dz + 1] = raw0 + R.slot(k + dz) * NRAW * G::PE + cell0 + r * G::BX;
       L[r] = ch_rate<real, 3, ISO>(S, P, A, c[r]);
       ph0[r] = S(C_PHI, 0, 0, 0);
+      if (USUM) c[r].pn = ph0[r];  // stage 1: phi^{n+1/2} = phi_s
     }
     // stores after both cells, so that nothing separates their shared loads
 #pragma unroll
@@ -271,7 +330,7 @@ static size_t ch2d_smem() {
 
 template <typename real, int DIM, int ISO>
 static cudaError_t ch_go(const KParams<real>& P, const CHArgs<real>& A, int kchunk, cudaStream_t s,
-                         const Maps<5>* maps, int* err, const Maps<5>* pmaps) {
+                         const Maps<5>* maps, int* err, const Maps<5>* pmaps, const Maps<5>* umaps) {
   dim3 blk(TX, TY, 1);
   dim3 grd((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY, DIM == 3 ? (P.n[2] + kchunk - 1) / kchunk : 1);
   cudaError_t e;
@@ -281,28 +340,34 @@ static cudaError_t ch_go(const KParams<real>& P, const CHArgs<real>& A, int kchu
     constexpr int RING = ch_ring<real>();
     if (A.conservative) {
       const size_t sm = ring_smem_bytes<real, 5, 0, RING, CH_K3_SY>();
-      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 1, RING, false, false>,
+      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 1, RING, false, false, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
-      ch3d_kernel<real, ISO, 1, RING, false, false><<<grd, blk, sm, s>>>(*maps, *maps, P, A, kchunk, err);
-    } else if (A.compute_uh && A.usum[0]) {
+      ch3d_kernel<real, ISO, 1, RING, false, false, false><<<grd, blk, sm, s>>>(*maps, *maps, P, A, kchunk, err);
+    } else if (A.compute_uh && A.usum[0] && A.phin == A.phis && umaps) {
+      const size_t sm = ring_smem_bytes<real, 2, 0, RING, CH_K3_SY>() + sizeof(real) * (size_t)3 * US_SLOT;
+      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 0, RING, true, false, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+      ch3d_kernel<real, ISO, 0, RING, true, false, true><<<grd, blk, sm, s>>>(*maps, *umaps, P, A, kchunk, err);
+    } else if (A.compute_uh && A.usum[0] && A.phin == A.phis) {
       const size_t sm = ring_smem_bytes<real, 2, 0, RING, CH_K3_SY>();
-      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 0, RING, true, false>,
+      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 0, RING, true, false, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
-      ch3d_kernel<real, ISO, 0, RING, true, false><<<grd, blk, sm, s>>>(*maps, *maps, P, A, kchunk, err);
+      ch3d_kernel<real, ISO, 0, RING, true, false, false><<<grd, blk, sm, s>>>(*maps, *maps, P, A, kchunk, err);
     } else if (!A.compute_uh && A.stage != 0 && pmaps) {
       const size_t sm = ring_smem_bytes<real, 2, 0, RING, CH_K3_SY>() + sizeof(real) * (size_t)2 * CP_N * CP_PT;
-      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 0, RING, false, true>,
+      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 0, RING, false, true, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
-      ch3d_kernel<real, ISO, 0, RING, false, true><<<grd, blk, sm, s>>>(*maps, *pmaps, P, A, kchunk, err);
+      ch3d_kernel<real, ISO, 0, RING, false, true, false><<<grd, blk, sm, s>>>(*maps, *pmaps, P, A, kchunk, err);
     } else {
       const size_t sm = ring_smem_bytes<real, 2, 0, RING, CH_K3_SY>();
-      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 0, RING, false, false>,
+      e = cudaFuncSetAttribute(ch3d_kernel<real, ISO, 0, RING, false, false, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       if (e != cudaSuccess) return e;
-      ch3d_kernel<real, ISO, 0, RING, false, false><<<grd, blk, sm, s>>>(*maps, *maps, P, A, kchunk, err);
+      ch3d_kernel<real, ISO, 0, RING, false, false, false><<<grd, blk, sm, s>>>(*maps, *maps, P, A, kchunk, err);
     }
   } else {
     const size_t sm = ch2d_smem<real>();
@@ -315,14 +380,15 @@ static cudaError_t ch_go(const KParams<real>& P, const CHArgs<real>& A, int kchu
 
 template <typename real, int DIM>
 cudaError_t launch_ch_stage(const KParams<real>& P, const CHArgs<real>& A, int iso, int kchunk,
-                            cudaStream_t s, const Maps<5>* maps, int* err, const Maps<5>* pmaps) {
+                            cudaStream_t s, const Maps<5>* maps, int* err, const Maps<5>* pmaps,
+                            const Maps<5>* umaps) {
   if constexpr (DIM == 2) {
-    return ch_go<real, DIM, 9>(P, A, kchunk, s, maps, err, nullptr);
+    return ch_go<real, DIM, 9>(P, A, kchunk, s, maps, err, nullptr, nullptr);
   } else {
     switch (iso) {
-      case 15: return ch_go<real, DIM, 15>(P, A, kchunk, s, maps, err, pmaps);
-      case 19: return ch_go<real, DIM, 19>(P, A, kchunk, s, maps, err, pmaps);
-      default: return ch_go<real, DIM, 27>(P, A, kchunk, s, maps, err, pmaps);
+      case 15: return ch_go<real, DIM, 15>(P, A, kchunk, s, maps, err, pmaps, umaps);
+      case 19: return ch_go<real, DIM, 19>(P, A, kchunk, s, maps, err, pmaps, umaps);
+      default: return ch_go<real, DIM, 27>(P, A, kchunk, s, maps, err, pmaps, umaps);
     }
   }
 }
@@ -374,7 +440,7 @@ cudaError_t launch_center_velocity(const KParams<real>& P, const real* const u0[
 
 #define GPE2P_CH_INST(R, D)                                                                                 \
   template cudaError_t launch_ch_stage<R, D>(const KParams<R>&, const CHArgs<R>&, int, int, cudaStream_t,   \
-                                             const Maps<5>*, int*, const Maps<5>*);                        \
+                                             const Maps<5>*, int*, const Maps<5>*, const Maps<5>*);        \
   template cudaError_t launch_mu<R, D>(const KParams<R>&, const R*, R*, int, int, cudaStream_t, const Maps<1>*, \
                                        int*);                                                              \
   template cudaError_t launch_center_velocity<R, D>(const KParams<R>&, const R* const[3], const R* const[3], \

@@ -149,7 +149,8 @@ __device__ __forceinline__ void ch_point_load(const KParams<real>& P, const CHAr
       for (int a = 0; a < DIM; ++a) c.uh[a] = A.uh[a][id];
     }
   }
-  if (A.stage != 0) c.pn = A.phin[id];
+  // (USUM: phi^{n+1/2} is phi_s itself, which the caller takes from its tile)
+  if (A.stage != 0 && !USUM) c.pn = A.phin[id];
   c.pnl = (A.phi_lo && A.stage != 0) ? A.phi_lo[id] : real(0);
   // RK4 stages 2-4 read the accumulated increments; with the compensated
   // accumulation the RK2 stage 2 reads the increment of stage 1

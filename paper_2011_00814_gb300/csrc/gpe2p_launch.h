@@ -93,8 +93,11 @@ template <typename real, int DIM>
 // pmaps (3D advective stages after the first, else nullptr): uhat x 3,
 // phi^{n+1/2} and the accumulator as boxes of a block's own cells, which the
 // kernel then brings in by TMA instead of loading them per cell
+// umaps (3D advective stage 1 with A.usum, else nullptr): the face sums
+// s_x, s_y, s_z as boxes of a block's cells and the faces above them
 cudaError_t launch_ch_stage(const KParams<real>& P, const CHArgs<real>& A, int iso, int kchunk,
-                            cudaStream_t s, const Maps<5>* maps, int* err, const Maps<5>* pmaps = nullptr);
+                            cudaStream_t s, const Maps<5>* maps, int* err, const Maps<5>* pmaps = nullptr,
+                            const Maps<5>* umaps = nullptr);
 
 // mu = 4 a phi (phi^2 - 1) - kappa lap_iso phi   (Eq. chem-pot)
 template <typename real, int DIM>
