@@ -176,9 +176,13 @@ def test_bubble3d_full_size_sampled():
 @pytest.mark.parametrize("shape,bc", [((1, 8, 1), ("periodic",) * 3), ((3, 3, 1), ("noslip", "noslip", "periodic")),
                                       ((2, 5, 1), ("freeslip", "periodic", "periodic")),
                                       ((2, 3, 4), ("periodic", "noslip", "periodic")),
-                                      ((1, 1, 6), ("noslip", "periodic", "noslip"))])
+                                      ((1, 1, 6), ("noslip", "periodic", "noslip")),
+                                      # 3D with a single plane, walls and a periodic z
+                                      ((5, 3, 1, 3), ("noslip", "freeslip", "periodic")),
+                                      ((4, 2, 1, 3), ("periodic", "noslip", "noslip"))])
 def test_degenerate_grids(shape, bc):
-    dim = 3 if shape[2] > 1 else 2
+    dim = shape[3] if len(shape) > 3 else (3 if shape[2] > 1 else 2)
+    shape = shape[:3]
     prm = inputs.base_params(dim, *shape, dx=1.0, dt=0.05, cs=1.0, bc=bc, sigma=0.02, M=0.02, W=2.0,
                              g=(0.0, 0.01, -0.01), rho_ref=0.5)
     f = inputs.random_fields(prm, seed=3)
