@@ -265,20 +265,22 @@ __global__ void __launch_bounds__(MU_NTHR) mu3d_kernel(const __grid_constant__ M
   const int kend = min(kbeg + kchunk, P.n[2]);
   const int nx = P.n[0], ny = P.n[1];
   const bool edge_tile = i0 == 0 || i0 + TX + 1 > nx || j0 == 0 || j0 + MU_K3_TY + 1 > ny;
-  const int i = i0 + tx, ja = j0 + 2 * ty;
-  const bool act[2] = {i < nx && ja < ny, i < nx && ja + 1 < ny};
+  const int i = i0 + tx, ja = j0 + MU_CPT * ty;
+  bool act[MU_CPT];
+#pragma unroll
+  for (int r = 0; r < MU_CPT; ++r) act[r] = i < nx && ja + r < ny;
   auto fix = [&](int, int ci, int cj, int kk) -> real { return ld_cen(phi, P, ci, cj, kk); };
   R.start(P, maps.m, kbeg, kend, i0, j0);
   if (!ring_acquire<real, 1, RING, MU_K3_SY, MU_NTHR>(R, P, maps.m, kbeg - 1, false, edge_tile, fix)) { R.fail(err, kbeg - 1); return; }
   if (!ring_acquire<real, 1, RING, MU_K3_SY, MU_NTHR>(R, P, maps.m, kbeg, false, edge_tile, fix)) { R.fail(err, kbeg); return; }
   const real* smr = reinterpret_cast<const real*>(smraw);
-  const int raw0 = (int)(R.raw - smr), cell0 = G::at(tx + 1, 2 * ty + 1);
+  const int raw0 = (int)(R.raw - smr), cell0 = G::at(tx + 1, MU_CPT * ty + 1);
   for (int k = kbeg; k < kend; ++k) {
     if (!ring_acquire<real, 1, RING, MU_K3_SY, MU_NTHR>(R, P, maps.m, k + 1, true, edge_tile, fix)) { R.fail(err, k + 1); return; }
     if (edge_tile || k + 1 >= P.n[2]) __syncthreads();  // out-of-domain writes seen by all
-    real m[2];
+    real m[MU_CPT];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
+    for (int r = 0; r < MU_CPT; ++r) {
       RawTile<real, 1, MU_K3_SY> S;
       S.sm = smr;
 #pragma unroll
@@ -289,7 +291,7 @@ __global__ void __launch_bounds__(MU_NTHR) mu3d_kernel(const __grid_constant__ M
       m[r] = fma(P.a4 * f, fma(f, f, real(-1)), -(P.kappa * lap_iso_shells<real, 3, ISO>(S, P, 0)));
     }
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
+    for (int r = 0; r < MU_CPT; ++r)
       if (act[r]) mu[lin(P, i, ja + r, k)] = m[r];
   }
 }

@@ -27,25 +27,32 @@ constexpr int FLOW_K3_TY = 2 * FLOW_TY;
 constexpr int FLOW_K3_SY = FLOW_K3_TY + 2;
 constexpr int FLOW_MINB = 16 / FLOW_TY;
 
-// the blocks of the 3D CH stage and of mu, likewise (2 CH_TY and 2 MU_TY rows
-// of cells), and the blocks of each that fit on an SM: the FP32 CH stage is
-// held by registers (48 a thread) to 40 warps, mu by threads to 64.  Four
+// the blocks of the 3D CH stage and of mu, likewise (2 CH_TY and MU_CPT MU_TY
+// rows of cells), and the blocks of each that fit on an SM: the FP32 CH stage
+// is held by shared memory (its ring and point planes) to nine blocks of four
+// warps, mu by threads to 64 warps.  Four
 // warps per CH block measured 0.552 against 0.576 ms for stage 1 (the other
-// stages unchanged); mu keeps eight (four measured 1.5 % slower).
+// stages unchanged).  A mu thread takes MU_CPT = 4 cells in y, so that its
+// plane wait, barrier and addressing serve four cells: 0.094 against 0.114
+// ms per sweep with two.
 #ifndef GPE2P_CH_TY
 #define GPE2P_CH_TY 4
 #endif
 #ifndef GPE2P_MU_TY
-#define GPE2P_MU_TY 8
+#define GPE2P_MU_TY 4
 #endif
 constexpr int CH_TY = GPE2P_CH_TY;
 constexpr int CH_NTHR = TX * CH_TY;
 constexpr int CH_K3_TY = 2 * CH_TY;
 constexpr int CH_K3_SY = CH_K3_TY + 2;
-constexpr int CH_RESIDENT = 40 / CH_TY;
+constexpr int CH_RESIDENT = CH_TY == 4 ? 9 : 40 / CH_TY;
+#ifndef GPE2P_MU_CPT
+#define GPE2P_MU_CPT 4
+#endif
 constexpr int MU_TY = GPE2P_MU_TY;
+constexpr int MU_CPT = GPE2P_MU_CPT;   // cells per mu thread, adjacent in y
 constexpr int MU_NTHR = TX * MU_TY;
-constexpr int MU_K3_TY = 2 * MU_TY;
+constexpr int MU_K3_TY = MU_CPT * MU_TY;
 constexpr int MU_K3_SY = MU_K3_TY + 2;
 constexpr int MU_RESIDENT = 64 / MU_TY;
 
