@@ -108,8 +108,10 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
   const int kend = min(kbeg + kchunk, P.n[2]);
   const int nx = P.n[0], ny = P.n[1];
   const bool edge_tile = i0 == 0 || i0 + TX + 1 > nx || j0 == 0 || j0 + CH_K3_TY + 1 > ny;
-  const int i = i0 + tx, ja = j0 + 2 * ty;
-  const bool act[2] = {i < nx && ja < ny, i < nx && ja + 1 < ny};
+  const int i = i0 + tx, ja = j0 + CH_CPT * ty;
+  bool act[CH_CPT];
+#pragma unroll
+  for (int r = 0; r < CH_CPT; ++r) act[r] = i < nx && ja + r < ny;
   auto fix = [&](int f, int ci, int cj, int kk) -> real {
     switch (f) {
       case C_PHI: return ld_cen(A.phis, P, ci, cj, kk);
@@ -175,16 +177,16 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
   if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, kbeg, false, edge_tile, fix)) { R.fail(err, kbeg); pdrain(kbeg); udrain(kbeg); return; }
   if (UPTS && !mbar_wait_bounded(&pbar[uslot(kbeg)], upar(kbeg), WAIT_CYCLES)) atomicExch(err, ERR_TMA_TIMEOUT);
   const real* smr = reinterpret_cast<const real*>(smraw);
-  const int raw0 = (int)(R.raw - smr), cell0 = G::at(tx + 1, 2 * ty + 1);
+  const int raw0 = (int)(R.raw - smr), cell0 = G::at(tx + 1, CH_CPT * ty + 1);
   for (int k = kbeg; k < kend; ++k) {
-    CHPoint<real> c[2];
+    CHPoint<real> c[CH_CPT];
     if (PTS || UPTS) {
 #pragma unroll
-      for (int r = 0; r < 2; ++r)
+      for (int r = 0; r < CH_CPT; ++r)
         c[r].pnl = (A.phi_lo && act[r]) ? A.phi_lo[lin(P, i, ja + r, k)] : real(0);
     } else {
 #pragma unroll
-      for (int r = 0; r < 2; ++r)
+      for (int r = 0; r < CH_CPT; ++r)
         if (act[r]) ch_point_load<real, 3, USUM>(P, A, i, ja + r, k, c[r]);
     }
     if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, k + 1, true, edge_tile, fix)) { R.fail(err, k + 1); pdrain(k); udrain(k + 1); return; }
@@ -196,8 +198,8 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
       const real* sb = pts + (size_t)uslot(k) * US_SLOT;
       const real* sz1p = pts + (size_t)uslot(k + 1) * US_SLOT + US_X + US_Y;
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int row = 2 * ty + r, j = ja + r;
+      for (int r = 0; r < CH_CPT; ++r) {
+        const int row = CH_CPT * ty + r, j = ja + r;
         const real sx0 = sb[row * (TX + 4) + tx];
         real sx1 = sb[row * (TX + 4) + tx + 1];
         const real sy0 = sb[US_X + row * TX + tx];
@@ -220,9 +222,9 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
       // every thread is past plane k - 1: its slot takes plane k + 1
       if (tid == 0) pissue(k + 1);
       if (!mbar_wait_bounded(&pbar[(k - kbeg) & 1], ((k - kbeg) >> 1) & 1, WAIT_CYCLES)) atomicExch(err, ERR_TMA_TIMEOUT);
-      const real* pp = pts + (size_t)((k - kbeg) & 1) * CP_N * CP_PT + (2 * ty) * TX + tx;
+      const real* pp = pts + (size_t)((k - kbeg) & 1) * CP_N * CP_PT + (CH_CPT * ty) * TX + tx;
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
+      for (int r = 0; r < CH_CPT; ++r) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) c[r].uh[a] = pp[a * CP_PT + r * TX];
         c[r].pn = pp[3 * CP_PT + r * TX];
@@ -230,9 +232,9 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
       }
     }
     if (edge_tile || k + 1 >= P.n[2]) __syncthreads();  // out-of-domain writes seen by all
-    real L[2], ph0[2];
+    real L[CH_CPT], ph0[CH_CPT];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
+    for (int r = 0; r < CH_CPT; ++r) {
       RawTile<real, NRAW, CH_K3_SY> S;
       S.sm = smr;
 #pragma unroll
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
     }
     // stores after both cells, so that nothing separates their shared loads
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
+    for (int r = 0; r < CH_CPT; ++r)
       if (act[r]) ch_finish<real, 3>(P, A, lin(P, i, ja + r, k), c[r], L[r], ph0[r]);
   }
 }

@@ -34,18 +34,23 @@ constexpr int FLOW_MINB = 16 / FLOW_TY;
 // warps per CH block measured 0.552 against 0.576 ms for stage 1 (the other
 // stages unchanged).  A mu thread takes MU_CPT = 4 cells in y, so that its
 // plane wait, barrier and addressing serve four cells: 0.094 against 0.114
-// ms per sweep with two.
+// ms per sweep with two.  Four cells per CH thread measured no faster (the
+// larger tile halves the resident blocks).
 #ifndef GPE2P_CH_TY
 #define GPE2P_CH_TY 4
 #endif
 #ifndef GPE2P_MU_TY
 #define GPE2P_MU_TY 4
 #endif
+#ifndef GPE2P_CH_CPT
+#define GPE2P_CH_CPT 2
+#endif
 constexpr int CH_TY = GPE2P_CH_TY;
+constexpr int CH_CPT = GPE2P_CH_CPT;   // cells per CH thread, adjacent in y
 constexpr int CH_NTHR = TX * CH_TY;
-constexpr int CH_K3_TY = 2 * CH_TY;
+constexpr int CH_K3_TY = CH_CPT * CH_TY;
 constexpr int CH_K3_SY = CH_K3_TY + 2;
-constexpr int CH_RESIDENT = CH_TY == 4 ? 9 : 40 / CH_TY;
+constexpr int CH_RESIDENT = CH_CPT == 2 && CH_TY == 4 ? 9 : 40 / CH_TY;
 #ifndef GPE2P_MU_CPT
 #define GPE2P_MU_CPT 4
 #endif
