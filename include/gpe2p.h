@@ -116,6 +116,10 @@ int gpe2p_create(const gpe2p_params *p, void *stream, gpe2p_handle *out);
 
 /* Sets the state from host arrays (nx*ny*nz doubles each, layout above):
  * phi, u, v and p are required, w is required in 3D and ignored in 2D.
+ * Arrays in pinned host memory (cudaHostAlloc, cudaHostRegister) are read in
+ * place by the device through their mapped address; pageable arrays are
+ * copied through a staging buffer.  Either way the call returns after the
+ * last read.
  * Wall faces of the normal velocity are set to zero.  mu is computed from
  * phi (Eq. chem-pot); phi is taken as phi^{1/2} of the time-staggered scheme
  * (Sec. 3).  Resets the step counter.  Synchronises the handle's stream. */
@@ -134,7 +138,9 @@ int gpe2p_step(gpe2p_handle h);
 int gpe2p_advance(gpe2p_handle h, long long nsteps, gpe2p_diag *last);
 
 /* Copies the state to host arrays (nx*ny*nz doubles each).  Any pointer
- * may be NULL to skip that field; w is ignored in 2D.  Synchronises. */
+ * may be NULL to skip that field; w is ignored in 2D.  Pinned host arrays
+ * are written in place by the device (FP32 states: the conversion to FP64
+ * writes them directly).  Synchronises. */
 int gpe2p_read_fields(gpe2p_handle h, double *phi, double *u, double *v, double *w, double *p,
                       double *mu);
 
