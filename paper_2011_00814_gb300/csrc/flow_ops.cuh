@@ -54,9 +54,23 @@ struct FlowOps {
   __device__ __forceinline__ static void edge_eta4(const T& S, int t, real& e4p, real& e4m) {
     const int cx = C == 0, cy = C == 1, cz = C == 2;
     const int tx = t == 0, ty = t == 1, tz = t == 2;
-    e4p = (S(F_ETA, 0, 0, 0) + S(F_ETA, tx, ty, tz)) + (S(F_ETA, -cx, -cy, -cz) + S(F_ETA, tx - cx, ty - cy, tz - cz));
-    e4m = (S(F_ETA, 0, 0, 0) + S(F_ETA, -tx, -ty, -tz)) +
-          (S(F_ETA, -cx, -cy, -cz) + S(F_ETA, -tx - cx, -ty - cy, -tz - cz));
+    if constexpr (DIM == 3) {
+      // summed in one order per edge whichever face asks (pairs along the
+      // lower axis first), so that the rates of the two components and the
+      // two cells that share an edge share its sum
+      const int a = C < t ? C : t, b = C < t ? t : C;
+      auto e4 = [&](int ox, int oy, int oz) {
+        const int ax = a == 0, ay = a == 1, az = a == 2, bx = b == 0, by = b == 1, bz = b == 2;
+        return (S(F_ETA, ox, oy, oz) + S(F_ETA, ox + ax, oy + ay, oz + az)) +
+               (S(F_ETA, ox + bx, oy + by, oz + bz) + S(F_ETA, ox + ax + bx, oy + ay + by, oz + az + bz));
+      };
+      e4p = e4(-cx, -cy, -cz);
+      e4m = e4(-cx - tx, -cy - ty, -cz - tz);
+    } else {
+      e4p = (S(F_ETA, 0, 0, 0) + S(F_ETA, tx, ty, tz)) + (S(F_ETA, -cx, -cy, -cz) + S(F_ETA, tx - cx, ty - cy, tz - cz));
+      e4m = (S(F_ETA, 0, 0, 0) + S(F_ETA, -tx, -ty, -tz)) +
+            (S(F_ETA, -cx, -cy, -cz) + S(F_ETA, -tx - cx, -ty - cy, -tz - cz));
+    }
   }
 
   // whether the pressure gradient averages transversally (Eq. gradp-u-p-ave-3d)
