@@ -99,7 +99,7 @@ def test_barrier_timeout_is_reported_and_recovers():
         assert d["nan_flag"] == 0
 
 
-def test_config4_workload_steps_without_divergence():
+def test_uneven_batch_workload_steps_without_divergence():
     prms, fields = inputs.batch_instances(n=12, seed=3)
     with gpe2p.Batch(prms) as b:
         for k, f in enumerate(fields):

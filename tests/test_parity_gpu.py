@@ -1,9 +1,9 @@
 """Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
 
 Tolerances (max relative field error, floors as in tests/fields.py):
-  FP64: operator rates 1e-12, states after many steps 1e-11 (the north-star
-  bar for the static drop after 2000 steps); FP32: rates 2e-5 of the largest
-  rate, the static drop after 2000 steps 1e-4.
+  FP64: operator rates 1e-12, states after many steps 1e-11 (the bar for the
+  static drop after 2000 steps); FP32: rates 2e-5 of the largest rate, the
+  static drop after 2000 steps 1e-4.
 """
 from __future__ import annotations
 
