@@ -329,6 +329,24 @@ def measure_surrogate(cases=(0, 1, 2, 3), calls=64):
     return out
 
 
+def max_over_ranks(ms, dist, device):
+    """The timed region of the job: the slowest rank's milliseconds (every
+    rank gets the same number), then a barrier."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_value(world, ncell, steps, ms):
+    """Whole-job cell-updates/s: every rank steps its own replica of ncell
+    cells, so the job processes world * ncell * steps cell-updates in ms."""
+    return world * ncell * steps / (ms / 1e3)
+
+
 def dist_setup(n_gpus):
     if n_gpus <= 1 and "WORLD_SIZE" not in os.environ:
         return 0, 1, None
@@ -436,14 +454,9 @@ def main():
             solver.step()
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     d = solver.diagnostics()
-    value = world * ncell * args.steps / (ms / 1e3)
+    value = job_value(world, ncell, args.steps, ms)
 
     # end to end through the public API: pinned host inputs in, state out, every step
     pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy() for k, v in f.items()}

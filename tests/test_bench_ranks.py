@@ -1,0 +1,63 @@
+"""The multi-rank logic of bench.py on CPU: two gloo ranks agree on the
+slowest rank's time, the job value counts every rank's replica, and the
+reference arm runs on rank 0 only."""
+from __future__ import annotations
+
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+import bench  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms = bench.max_over_ranks(10.0 + 5.0 * rank, dist, "cpu")
+        q.put((rank, ms, bench.job_value(world, 1000, 4, ms)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(world))
+    for rank, ms, value in got:
+        assert ms == 15.0
+        assert value == pytest.approx(2 * 1000 * 4 / 0.015)
+
+
+def test_single_rank_is_unchanged():
+    assert bench.max_over_ranks(12.5, None, "cpu") == 12.5
+    assert bench.job_value(1, 10, 2, 1000.0) == pytest.approx(20.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+
+    class Args:
+        steps, warmup, gpus = 1, 1, 2
+
+    assert bench.run_reference(Args()) == 0
+    assert capsys.readouterr().out == ""
