@@ -175,7 +175,11 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
   }
   if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, kbeg - 1, false, edge_tile, fix)) { R.fail(err, kbeg - 1); pdrain(kbeg); udrain(kbeg); return; }
   if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, kbeg, false, edge_tile, fix)) { R.fail(err, kbeg); pdrain(kbeg); udrain(kbeg); return; }
-  if (UPTS && !mbar_wait_bounded(&pbar[uslot(kbeg)], upar(kbeg), WAIT_CYCLES)) atomicExch(err, ERR_TMA_TIMEOUT);
+  bool pfail = false;  // a point-plane wait of this thread gave up
+  if (UPTS && !mbar_wait_bounded(&pbar[uslot(kbeg)], upar(kbeg), WAIT_CYCLES)) {
+    atomicExch(err, ERR_TMA_TIMEOUT);
+    pfail = true;
+  }
   const real* smr = reinterpret_cast<const real*>(smraw);
   const int raw0 = (int)(R.raw - smr), cell0 = G::at(tx + 1, CH_CPT * ty + 1);
   for (int k = kbeg; k < kend; ++k) {
@@ -193,8 +197,10 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
     if (UPTS) {
       // every thread is past plane k - 1: its slot takes plane k + 2
       if (tid == 0) uissue(k + 2);
-      if (k + 1 <= klast && !mbar_wait_bounded(&pbar[uslot(k + 1)], upar(k + 1), WAIT_CYCLES))
+      if (k + 1 <= klast && !mbar_wait_bounded(&pbar[uslot(k + 1)], upar(k + 1), WAIT_CYCLES)) {
         atomicExch(err, ERR_TMA_TIMEOUT);
+        pfail = true;
+      }
       const real* sb = pts + (size_t)uslot(k) * US_SLOT;
       const real* sz1p = pts + (size_t)uslot(k + 1) * US_SLOT + US_X + US_Y;
 #pragma unroll
@@ -221,7 +227,10 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
     if (PTS) {
       // every thread is past plane k - 1: its slot takes plane k + 1
       if (tid == 0) pissue(k + 1);
-      if (!mbar_wait_bounded(&pbar[(k - kbeg) & 1], ((k - kbeg) >> 1) & 1, WAIT_CYCLES)) atomicExch(err, ERR_TMA_TIMEOUT);
+      if (!mbar_wait_bounded(&pbar[(k - kbeg) & 1], ((k - kbeg) >> 1) & 1, WAIT_CYCLES)) {
+        atomicExch(err, ERR_TMA_TIMEOUT);
+        pfail = true;
+      }
       const real* pp = pts + (size_t)((k - kbeg) & 1) * CP_N * CP_PT + (CH_CPT * ty) * TX + tx;
 #pragma unroll
       for (int r = 0; r < CH_CPT; ++r) {
@@ -247,6 +256,17 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
 #pragma unroll
     for (int r = 0; r < CH_CPT; ++r)
       if (act[r]) ch_finish<real, 3>(P, A, lin(P, i, ja + r, k), c[r], L[r], ph0[r]);
+  }
+  // a point-plane wait of thread 0 gave up (the error word is set): let the
+  // last copies into each slot land before the block exits; a phase that
+  // never completed also holds the bytes of the copies issued after it
+  if ((PTS || UPTS) && tid == 0 && pfail) {
+    if (PTS)
+      for (int kk = pissued; kk >= kbeg && kk > pissued - 2; --kk)
+        mbar_wait_bounded(&pbar[(kk - kbeg) & 1], ((kk - kbeg) >> 1) & 1, WAIT_CYCLES / 2);
+    if (UPTS)
+      for (int kk = uissued; kk >= kbeg && kk > uissued - 3; --kk)
+        mbar_wait_bounded(&pbar[uslot(kk)], upar(kk), WAIT_CYCLES / 2);
   }
 }
 
