@@ -74,3 +74,41 @@ def test_capillary_wave_numbers(case):
     assert abs(prm["amplitude"] - g["A_p"]) < 1e-15
     assert g["N_t"] / g["N_L"] == g["c"]
     _check_discretisation(prm, g, g["N_t"])
+
+
+def test_bubble3d_numbers():
+    """The 3D buoyant bubble of the bench (a reading of the paper's 3D setting
+    in lattice units): Eo = 10, Mo = 1e-4, r_rho = 10, r_eta = 10, D = 64."""
+    prm, f = inputs.bubble3d()
+    R, D = 32.0, 64.0
+    g = -prm["g"][2]
+    drho = prm["rhoL"] - prm["rhoG"]
+    assert abs(g * drho * D * D / prm["sigma"] - 10.0) < 1e-9
+    assert abs(g * prm["etaL"] ** 4 * drho / (prm["rhoL"] ** 2 * prm["sigma"] ** 3) - 1e-4) < 1e-15
+    assert abs(prm["rhoL"] / prm["rhoG"] - 10.0) < 1e-12 and abs(prm["etaL"] / prm["etaG"] - 10.0) < 1e-12
+    assert prm["dx"] == 1.0 and prm["dt"] == 1.0 and abs(prm["cs"] - 1.0 / math.sqrt(3.0)) < 1e-15
+    assert prm["rho_ref"] == prm["rhoL"] and prm["iso"] == 15 and prm["ch_scheme"] == 4
+    assert prm["bc"] == ("noslip", "noslip", "noslip")
+    assert (prm["nx"], prm["ny"], prm["nz"]) == (256, 256, 512)
+    # gas (phi < 0) inside the bubble centred 64 + 32 cells above the bottom wall
+    x, y, z = inputs.cell_centres(prm)
+    r = np.sqrt((x - 128.0) ** 2 + (y - 128.0) ** 2 + (z - 96.0) ** 2)
+    assert np.all(f["phi"][r < R - 3 * prm["W"]] < -0.99) and np.all(f["phi"][r > R + 3 * prm["W"]] > 0.99)
+
+
+def test_two_drops_recipe():
+    """Two drops on the periodic 256^2 box: radii in [20, 50] scaled to the box,
+    the second centre R1 + R2 + gap away with the gap in [2, 8] cells,
+    r_rho log-uniform in [2, 20] and r_eta = r_rho (a reading of the surrogate
+    workload), seeded and reproducible."""
+    for seed in range(8):
+        prm, f = inputs.two_drops(seed)
+        assert (prm["nx"], prm["ny"]) == (256, 256) and prm["bc"][:2] == ("periodic", "periodic")
+        r_rho = prm["rhoL"] / prm["rhoG"]
+        assert 2.0 - 1e-12 <= r_rho <= 20.0 + 1e-12
+        assert abs(prm["etaL"] / prm["etaG"] - r_rho) < 1e-9
+        assert np.all(np.abs(f["phi"]) <= 1.0)
+        # two drops of radius 20-50 cover pi (R1^2 + R2^2) / 256^2 of the box
+        assert 2 * math.pi * 20 ** 2 / 65536 * 0.9 < np.mean(f["phi"] > 0) < 2 * math.pi * 50 ** 2 / 65536
+        prm2, f2 = inputs.two_drops(seed)
+        assert np.array_equal(f["phi"], f2["phi"])
