@@ -43,10 +43,14 @@ METRIC = "cell-updates/s (RK3 step)"
 UNIT = "cell-updates/s"
 WORKLOAD = "3D buoyant bubble 256x256x512 FP32 (no-slip walls, D3Q15, RK4 CH)"
 
-# algorithmic words per cell of each launch kind in the 3D FP32 step
-# (reads + writes of one pass; see the measurement section of the design doc)
-# (flow stage 3 also writes u^n + u^{n+1} on the three faces; CH stage 1 forms
-# uhat from those sums)
+# algorithmic words per cell of each launch kind in the 3D FP32 step, reads +
+# writes of one pass: flow stage 1 reads p, u, v, w, phi and mu and writes
+# p, u, v, w (6 + 4); stages 2 and 3 also read the four fields of q^n (10 + 4),
+# and stage 3 writes u^n + u^{n+1} on the three faces (10 + 7); CH stage 1
+# reads the three face sums, phi^n and mu and writes uhat, acc and phi_1
+# (5 + 5), stages 2 and 3 read uhat, phi^n, acc, the stage phi and mu and write
+# acc and phi (7 + 2), stage 4 writes phi only (7 + 1); the mu sweep reads phi
+# and writes mu (1 + 1)
 WORDS = {"flow_stage1": 10, "flow_stage2": 14, "flow_stage3": 17, "ch_stage": None, "mu": 2}
 CH_WORDS_RK4 = [10, 9, 9, 8]  # CH stage 1 (builds uhat from the face sums), 2, 3, 4
 

@@ -1,4 +1,4 @@
-"""Learned surrogate of the 2D two-phase step, with the solver as judge and fallback.
+"""Learned surrogate of the 2D two-phase step, with the solver as referee and fallback.
 
 A convolutional U-Net (the library's ``gpe2p_net_*``) advances the state
 (phi, u, v, p) of a periodic 2D problem over K solver steps in one call.  Its
@@ -9,7 +9,7 @@ the state K steps later, formed as the input plus a scaled learned increment
 which also recomputes mu from phi.  Every step of that path runs in the
 library's kernels; this module only sequences the calls.
 
-The controller keeps the solver as the judge: every ``check_every``-th call
+The controller keeps the solver as the referee: every ``check_every``-th call
 also runs the K solver steps from the same start and measures the relative
 phi L2 distance between the two results (``gpe2p_state_distance``).  The
 solver's result is kept.  If the distance exceeds ``tol``, the window of calls
@@ -286,7 +286,7 @@ class Controller:
             self.s.unpack(self.y[0])
             return
         self._window = 0
-        self.s.advance(K)                                    # the judge, from the same start
+        self.s.advance(K)                                    # the referee, from the same start
         st.solver_calls += 1
         st.checks += 1
         d = self.s.distance(self.y[0])
