@@ -319,6 +319,91 @@ def test_ch_step_fourier_closed_form(dim, iso, scheme, shape, modes, phi0):
 
 
 # ----------------------------------------------------------------------------
+# the coupling: a phase-field mode drives the flow through surface tension and
+# buoyancy (uniform phi0, rho_ref = rho(phi0), fluid at rest)
+# ----------------------------------------------------------------------------
+
+def forcing_symbol(prm, theta, phi0):
+    """Velocity rates per unit phi mode, linearised about uniform phi0 at rest,
+    by hand from Eqs. st-u-discretization and gpe-momentum-two-phase-const-bf:
+    on the low-c face, -sigma phi_face (mu_i - mu_{i-1}) / dx / rho_face gives
+    -sigma phi0 s_c (f'' - kappa lam) / (dx rho0), and (rho_face - rho_ref) g_c
+    / rho_face with rho_face the mean of the two cells and rho linear in phi
+    gives (rho_L - rho_G)/2 cos(theta_c / 2) g_c / rho0.  The pressure rate
+    has no phi term at rest (its phi enters through rho c^2 div u and nu grad p,
+    both zero at rest)."""
+    d = prm["dim"]
+    rho0, _, _ = _material(prm, phi0)
+    a_ = 3.0 / (4.0 * prm["W"])
+    kappa = 3.0 * prm["W"] / 8.0
+    fpp = 4.0 * a_ * (3.0 * phi0 * phi0 - 1.0)
+    lam = iso_laplacian_symbol(d, prm["iso"], theta, prm["dx"])
+    b = np.zeros(d + 1, dtype=complex)
+    for c in range(d):
+        s_c = 2j * math.sin(theta[c] / 2.0)
+        b[1 + c] = (-prm["sigma"] * phi0 * s_c * (fpp - kappa * lam) / prm["dx"]
+                    + 0.5 * (prm["rhoL"] - prm["rhoG"]) * math.cos(theta[c] / 2.0) * prm["g"][c]) / rho0
+    z = prm["dt"] * prm["M"] * lam * (fpp - kappa * lam)
+    return b, ch_polynomial(z, prm["ch_scheme"])
+
+
+def tvd_rk3_forced(q, hA, hb):
+    """One step of Eq. tvd-rk3 for dq/dt = A q + b with b frozen over the stages."""
+    q1 = q + hA @ q + hb
+    q2 = 0.75 * q + 0.25 * (q1 + hA @ q1 + hb)
+    return q / 3.0 + 2.0 / 3.0 * (q2 + hA @ q2 + hb)
+
+
+COUPLING_CASES = [
+    # dim, shape, phi0, g, theta-index triples
+    (2, (8, 8, 1), 0.3, (0.3, -0.5, 0.0), [(1, 0), (2, 1), (0, 3)]),
+    (2, (8, 6, 1), -0.5, (0.0, -0.4, 0.0), [(1, 1), (3, 2)]),
+    (3, (8, 6, 4), 0.4, (0.3, -0.5, 0.4), [(1, 1, 1), (2, 0, 1), (0, 3, 2)]),
+]
+
+
+@pytest.mark.parametrize("dim,shape,phi0,g,modes", COUPLING_CASES)
+def test_phase_field_mode_drives_the_flow(dim, shape, phi0, g, modes):
+    """A phi mode on a uniform phi0 at rest: phi evolves by the CH amplification
+    alone (u.grad phi is second order), and step n of the flow is forced by
+    phi^{n+1/2} (phi^{1/2} = phi^0), frozen over its three stages.  Run with
+    the mode added and subtracted; half the difference is the linear
+    response, compared with the recursion q <- RK3(q; A, b g_ch^n)."""
+    nx, ny, nz = shape
+    prm = inputs.base_params(dim, nx, ny, nz, dx=0.5, dt=0.05, cs=1.3, rhoL=1.7, rhoG=0.4, etaL=0.05,
+                             etaG=0.02, sigma=0.02, M=0.01, W=3.0, g=g)
+    prm["rho_ref"] = _material(prm, phi0)[0]
+    n = [nx, ny, nz][:dim]
+    names = "uvw"[:dim]
+    eps = 1e-6
+    nsteps = 30
+    amp = 0.8 + 0.3j
+    for m in modes:
+        theta = [2.0 * math.pi * m[a] / n[a] for a in range(dim)]
+        res = []
+        for sgn in (1.0, -1.0):
+            f = inputs.zero_fields(prm)
+            f["phi"] = phi0 + _mode_field(prm, "c", sgn * eps * amp, theta)
+            st = oracle.init_state(prm, f["phi"], f["p"], f["u"], f["v"], f.get("w"))
+            res.append(oracle.step(prm, st, nsteps))
+        b, gch = forcing_symbol(prm, theta, phi0)
+        hA = prm["dt"] * flow_symbol(prm, theta, phi0)
+        q = np.zeros(dim + 1, dtype=complex)
+        phi_hat = amp
+        for _ in range(nsteps):
+            q = tvd_rk3_forced(q, hA, prm["dt"] * b * phi_hat)
+            phi_hat = phi_hat * gch
+        scale = eps * max(np.max(np.abs(q)), 1e-3)
+        lin = {k: 0.5 * (res[0][k] - res[1][k]) for k in ["phi", "p", *names]}
+        assert np.max(np.abs(lin["phi"] - _mode_field(prm, "c", eps * phi_hat, theta))) < 1e-8 * eps
+        err = np.max(np.abs(lin["p"] - _mode_field(prm, "c", eps * q[0], theta))) / scale
+        for a, nm in enumerate(names):
+            err = max(err, np.max(np.abs(lin[nm] - _mode_field(prm, nm, eps * q[1 + a], theta))) / scale)
+        assert err < 1e-7, (m, err)
+        assert np.max(np.abs(q)) > 1e-3  # the forcing moved the fluid
+
+
+# ----------------------------------------------------------------------------
 # time-centred advection velocity: uniformly accelerated, density-matched flow
 # ----------------------------------------------------------------------------
 
