@@ -404,6 +404,48 @@ def test_phase_field_mode_drives_the_flow(dim, shape, phi0, g, modes):
 
 
 # ----------------------------------------------------------------------------
+# the diagnostics, summed by hand on tiny grids
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_diagnostics_by_hand(dim):
+    """phi alternates between 0.5 and -1 along x, so every x face sits between
+    one cell of each kind and every other face between two cells of the same
+    kind; u = 1 on even x faces and -2 on odd ones, the other components
+    uniform.  int phi = sum phi dx^d, the kinetic energy = 1/2 sum over faces
+    of the mean density of the two cells times u^2 dx^d, umax the largest
+    |component|; a single Inf sets the flag."""
+    nx, ny, nz = 6, 4, (2 if dim == 3 else 1)
+    prm = inputs.base_params(dim, nx, ny, nz, dx=0.5, rhoL=1.7, rhoG=0.4)
+    f = inputs.zero_fields(prm)
+    even = (np.arange(nx) % 2 == 0)
+    f["phi"][...] = np.where(even, 0.5, -1.0)
+    f["u"][...] = np.where(even, 1.0, -2.0)
+    f["v"][...] = 0.25
+    if dim == 3:
+        f["w"][...] = -0.75
+    st = oracle.init_state(prm, f["phi"], f["p"], f["u"], f["v"], f.get("w"))
+    rho = lambda ph: 0.5 * (1.7 * (1.0 + ph) + 0.4 * (1.0 - ph))
+    r_hi, r_lo = rho(0.5), rho(-1.0)
+    vol = 0.5 ** dim
+    rows = ny * nz
+    int_phi = rows * (nx // 2) * (0.5 - 1.0) * vol
+    # x faces: the mean of one cell of each kind; y and z faces: the cell's own density
+    ke_x = 0.5 * 0.5 * (r_hi + r_lo) * rows * (nx // 2) * (1.0 + 4.0)
+    ke_y = 0.5 * rows * (nx // 2) * (r_hi + r_lo) * 0.25 ** 2
+    ke_z = 0.5 * rows * (nx // 2) * (r_hi + r_lo) * 0.75 ** 2 if dim == 3 else 0.0
+    got = oracle.diag(prm, st)
+    assert abs(got[0] - int_phi) < 1e-14
+    assert abs(got[1] - (ke_x + ke_y + ke_z) * vol) < 1e-13
+    assert got[2] == 2.0 and got[3] is False
+    st["p"][(0,) * dim] = np.inf
+    assert oracle.diag(prm, st)[3] is True
+    st["p"][(0,) * dim] = 0.0
+    st["phi"][(1,) * dim] = np.nan
+    assert oracle.diag(prm, st)[3] is True
+
+
+# ----------------------------------------------------------------------------
 # time-centred advection velocity: uniformly accelerated, density-matched flow
 # ----------------------------------------------------------------------------
 
