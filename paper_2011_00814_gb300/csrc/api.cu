@@ -206,13 +206,15 @@ extern "C" int gpe2p_stability_limits(const gpe2p_params* p, double out[3]) {
       }
   const double omega = p->cs * 2.0 / dx * std::sqrt(amax);
   out[0] = std::sqrt(3.0) / omega;
-  // viscous: the largest kinematic viscosity of the two phases against
-  // 4/dx^2 times (2 + bulk + (d - 1)) for momentum and d for pressure diffusion
+  // viscous: the stress operator of a uniform state has the symbol
+  // nu [sum_t s_t^2 I + (1 + bulk) s s^T], s_t = 2 i sin(t_t/2) / dx, whose
+  // largest eigenvalue magnitude, (2 + bulk) nu sum_t |s_t|^2 on longitudinal
+  // modes, peaks at (2 + bulk) nu 4 d / dx^2 for t = (pi, ..., pi); the
+  // pressure diffusion's nu 4 d / dx^2 lies below it.  nu = eta / rho is
+  // largest in one of the two phases (a ratio of linear laws is monotone).
   const double nuL = p->etaL / p->rhoL, nuG = p->etaG / p->rhoG;
   const double nu = nuL > nuG ? nuL : nuG;
-  double fac = 2.0 + (p->bulk_visc ? 1.0 : 0.0) + (d - 1);
-  if (fac < d) fac = d;
-  const double lv = nu * 4.0 * fac / (dx * dx);
+  const double lv = nu * (2.0 + (p->bulk_visc ? 1.0 : 0.0)) * 4.0 * d / (dx * dx);
   out[1] = lv > 0.0 ? 2.5127 / lv : INFINITY;  // RK3 real-axis limit
   // Cahn-Hilliard: |z| = dt M lam (8a + kappa lam) with f'' <= 8a on |phi| <= 1
   const double a = 3.0 / (4.0 * p->W), kappa = 3.0 * p->W / 8.0;

@@ -199,8 +199,9 @@ def batch_instances(n: int = 96, seed: int = 0, sides=(64, 128, 192, 256, 384, 5
     inside, |g| uniform in [0, 1e-5] along -y, rho_ref the mean density of
     the initial state, so that the periodic box does not accelerate).  The
     sound speed is U_c / Ma with U_c = sigma / eta_L and Ma = 0.1; dt is the
-    acoustic CFL 0.3 step, reduced where needed to 0.4 of the explicit
-    viscous bound 2.5 dx^2 / (16 nu_max) and the CH bound 2 / (M lam (8a + kappa lam)),
+    acoustic CFL 0.3 step, reduced where needed to dx^2 / (16 nu_max) (0.6 of
+    the RK3 viscous limit 2.51 dx^2 / (24 nu_max) of a 2D grid with bulk
+    viscosity) and to 0.4 of the CH bound 2 / (M lam (8a + kappa lam)),
     lam = 16/3 dx^-2.  Returns (list of params, list of field dicts)."""
     rng = np.random.default_rng(seed)
     prms, fields = [], []
