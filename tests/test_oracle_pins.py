@@ -238,6 +238,34 @@ def test_flow_operator_about_a_uniform_velocity(dim, shape, phi0, ubg, modes):
             assert np.max(np.abs(even - ubg[a])) < 1e-9
 
 
+@pytest.mark.parametrize("dim,comp", [(2, "v"), (3, "w"), (3, "v")])
+def test_finite_amplitude_shear_wave(dim, comp):
+    """A shear wave across x at finite amplitude, phi = 1 (mu = 0 exactly),
+    u = p = 0 and the one velocity component a function of x alone: the
+    convection of Eq. conv-u-discretization and the divergence vanish
+    identically, so each Fourier mode decays by P3(-dt nu 4 sin^2(theta/2) /
+    dx^2) per step at any amplitude."""
+    n = 16
+    prm = inputs.base_params(dim, n, 4, 4, dx=0.5, dt=0.05, cs=1.3, rhoL=1.7, rhoG=0.4, etaL=0.05,
+                             etaG=0.02, sigma=0.02, M=0.01, W=3.0)
+    nu = prm["etaL"] / prm["rhoL"]
+    X = positions(prm, comp)[0]
+    f = inputs.zero_fields(prm)
+    f["phi"][...] = 1.0
+    amps = {1: 0.5, 3: -0.3, 8: 0.2}
+    f[comp] = sum(A * np.sin(2.0 * math.pi * m * X / n) for m, A in amps.items())
+    st = oracle.init_state(prm, f["phi"], f["p"], f["u"], f["v"], f.get("w"))
+    nsteps = 50
+    out = oracle.step(prm, st, nsteps)
+    expect = 0.0
+    for m, A in amps.items():
+        z = -prm["dt"] * nu * 4.0 * math.sin(math.pi * m / n) ** 2 / prm["dx"] ** 2
+        expect = expect + A * (1 + z + z * z / 2 + z ** 3 / 6) ** nsteps * np.sin(2.0 * math.pi * m * X / n)
+    assert np.max(np.abs(out[comp] - expect)) < 1e-13
+    for other in ["p", *[c for c in "uvw"[:dim] if c != comp]]:
+        assert np.max(np.abs(out[other])) == 0.0
+
+
 # ----------------------------------------------------------------------------
 # Fourier symbol of the linearised Cahn-Hilliard step (u = 0, sigma = 0)
 # ----------------------------------------------------------------------------
@@ -552,8 +580,17 @@ def test_flat_interface_equilibrium_is_stationary():
     n, W = 64, 4.0
     prof = _flat_equilibrium(n, W)
     # the discrete profile approaches tanh(2d/W) (Eq. chem-pot with a, kappa)
-    d = np.arange(n // 4, n // 2) + 0.5 - n // 4
-    assert np.max(np.abs(prof[n // 4:n // 2] - np.tanh(2.0 * d / W))) < 0.02
+    # at second order in dx / W, and the oracle's mu vanishes on each
+    devs = []
+    for k in (1, 2, 4):
+        nk, Wk = n * k, W * k
+        pk = prof if k == 1 else _flat_equilibrium(nk, Wk)
+        d = np.arange(nk // 4, nk // 2) + 0.5 - nk // 4
+        devs.append(np.max(np.abs(pk[nk // 4:nk // 2] - np.tanh(2.0 * d / Wk))))
+        pw = inputs.base_params(2, nk, 2, dx=1.0, W=Wk)
+        assert np.max(np.abs(oracle.mu(pw, np.tile(pk, (2, 1))))) < 1e-12
+    assert devs[0] < 0.015
+    assert devs[0] / devs[1] > 3.5 and devs[1] / devs[2] > 3.5, devs
     prm = inputs.base_params(2, n, 6, dx=1.0, dt=0.3, cs=1.0, W=W, sigma=0.05, M=0.05)
     phi = np.tile(prof, (6, 1))
     st = oracle.init_state(prm, phi)
