@@ -475,8 +475,8 @@ def main():
         solver.step()
         solver._check(lib.gpe2p_read_fields(solver.h, dptr(outb["phi"]), dptr(outb["u"]), dptr(outb["v"]),
                                             dptr(outb["w"]), dptr(outb["p"]), None))
-    e2e_s = time.perf_counter() - t0
-    e2e_val = world * ncell * args.e2e_steps / e2e_s
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, dist, "cuda")
+    e2e_val = job_value(world, ncell, args.e2e_steps, e2e_ms)
     solver.close()
 
     if rank != 0:
