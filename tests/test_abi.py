@@ -136,3 +136,42 @@ def test_null_arguments_do_not_crash(lib):
     h = ctypes.c_void_p()
     assert lib.gpe2p_create(None, None, ctypes.byref(h)) == gpe2p.EINVAL
     assert b"NULL" in lib.gpe2p_last_error(None)
+
+
+def test_create_refuses_unstable_dt_before_touching_the_device(lib):
+    """With check_stability = 1, gpe2p_create and gpe2p_create_batch compare dt
+    with each explicit limit and refuse on the host (no device is needed to
+    reach the refusal), naming the limit or the instance."""
+    prm = dict(inputs.base_params(2, 16, 16), precision=64, check_stability=1)
+    lim = gpe2p.stability_limits(prm)
+    names = ("acoustic", "viscous", "Cahn-Hilliard")
+    for which in range(3):
+        # make limit `which` the binding one and step just past it
+        q = dict(prm)
+        if which == 0:
+            q.update(cs=50.0)
+        elif which == 1:
+            q.update(etaL=5.0, etaG=0.5)
+        else:
+            q.update(M=5.0)
+        lims = gpe2p.stability_limits(q)
+        assert min(range(3), key=lambda t: lims[t]) == which
+        q["dt"] = 1.01 * lims[which]
+        with pytest.raises(gpe2p.GPE2PError) as e:
+            gpe2p.Solver(q)
+        assert e.value.code == gpe2p.EUNSTABLE and names[which] in str(e.value)
+        with pytest.raises(gpe2p.GPE2PError) as e:
+            gpe2p.Batch([prm, q])
+        assert e.value.code == gpe2p.EUNSTABLE and "instance 1" in str(e.value)
+    assert prm["dt"] < min(lim)
+
+
+def test_create_batch_validates_every_instance(lib):
+    good = dict(inputs.base_params(2, 16, 16), precision=32)
+    with pytest.raises(gpe2p.GPE2PError) as e:
+        gpe2p.Batch([good, good, dict(good, W=-1.0)])
+    assert e.value.code == gpe2p.EINVAL and "instance 2" in str(e.value)
+    h = ctypes.c_void_p()
+    arr = (gpe2p.Params * 1)(gpe2p.params(good))
+    assert lib.gpe2p_create_batch(arr, 0, None, ctypes.byref(h)) == gpe2p.EINVAL
+    assert lib.gpe2p_create_batch(None, 1, None, ctypes.byref(h)) == gpe2p.EINVAL
