@@ -175,3 +175,39 @@ def test_create_batch_validates_every_instance(lib):
     arr = (gpe2p.Params * 1)(gpe2p.params(good))
     assert lib.gpe2p_create_batch(arr, 0, None, ctypes.byref(h)) == gpe2p.EINVAL
     assert lib.gpe2p_create_batch(None, 1, None, ctypes.byref(h)) == gpe2p.EINVAL
+
+
+def test_noalloc_diagnostics_validate_on_the_host(lib):
+    """gpe2p_diagnostics_noalloc checks its arguments before it looks up its
+    scratch or launches anything.  Run only where no GPU is visible, so that
+    the one well-formed call below ends at the device lookup (GPE2P_ECUDA)
+    and its stand-in pointers are never read."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("needs a machine without a visible GPU")
+    f = lib.gpe2p_diagnostics_noalloc
+    fake = ctypes.c_void_p(4096)
+    out = ctypes.cast(ctypes.c_void_p(8192), ctypes.POINTER(ctypes.c_double))
+
+    def call(prm, pitch=None, w=fake, outp=out, p=fake):
+        q = gpe2p.params(prm)
+        pitch = prm["nx"] if pitch is None else pitch
+        return f(ctypes.byref(q), p, fake, fake, w, fake, pitch, outp, None)
+
+    good3 = dict(inputs.base_params(3, 8, 6, 4), precision=32)
+    good2 = dict(inputs.base_params(2, 8, 6), precision=64)
+    assert call(good3, w=None) == gpe2p.EINVAL              # 3D needs w
+    assert call(good2, p=None) == gpe2p.EINVAL
+    assert call(good2, outp=None) == gpe2p.EINVAL
+    assert call(good2, pitch=7) == gpe2p.EINVAL              # row pitch below nx
+    assert call(dict(good2, precision=16)) == gpe2p.EINVAL
+    assert call(dict(good2, dx=0.0)) == gpe2p.EINVAL
+    assert call(dict(good2, dim=4)) == gpe2p.EINVAL
+    big = dict(inputs.base_params(3, 1024, 1024, 65), precision=32)  # 68.2M cells
+    assert call(big) == gpe2p.EINVAL
+    q = gpe2p.params(good2)
+    q.bc[1] = 5
+    assert f(ctypes.byref(q), fake, fake, fake, None, fake, 8, out, None) == gpe2p.EINVAL
+    # well formed: it gets as far as the device lookup
+    assert call(good2, w=None) == gpe2p.ECUDA
+    assert call(good3) == gpe2p.ECUDA
