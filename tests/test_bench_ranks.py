@@ -1,6 +1,7 @@
-"""The multi-rank logic of bench.py on CPU: two gloo ranks agree on the
-slowest rank's time, the job value counts every rank's replica, and the
-reference arm runs on rank 0 only."""
+"""Host logic of bench.py on CPU: two gloo ranks agree on the
+slowest rank's time, the job value counts every rank's replica, the
+reference arm runs on rank 0 only, and the clock record of the timed region
+is read from nvidia-smi's lines."""
 from __future__ import annotations
 
 import os
@@ -61,3 +62,24 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
 
     assert bench.run_reference(Args()) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_clock_summary_reads_nvidia_smi_lines():
+    """The clock record of the timed region: the median SM clock under load,
+    the maximum, and every throttle reason seen Active at least once
+    (nvidia-smi --format=csv,noheader,nounits lines of the bench's query)."""
+    c = bench.ClockSampler(None)
+    c.out = "\n".join([
+        "2070, 2070, 910.50, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "2055, 2070, 1390.20, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "1980, 2070, 1401.00, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "[N/A], 2070, 0.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage",
+    ])
+    s = c.summary()
+    assert s["sm_mhz"] == 2055.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    c.out = "1200, 2070, 700.0, 0x0000000000000008, Not Active, Active, Not Active, Not Active\n"
+    assert c.summary()["reasons"] == ["hw_thermal_slowdown"]
+    c.out = ""
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
