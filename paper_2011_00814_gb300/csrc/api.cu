@@ -992,12 +992,13 @@ extern "C" void gpe2p_destroy(gpe2p_handle h) {
     return;
   }
   cudaSetDevice(h->dev);
+  // let the handle's work in flight finish before its memory goes
+  if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->d_dist) cudaFree(h->d_dist);
   if (h->h_dist) cudaFreeHost(h->h_dist);
   if (h->phi_lo) cudaFree(h->phi_lo);
   for (int c = 0; c < 2; ++c)
     if (h->gexec[c]) cudaGraphExecDestroy(h->gexec[c]);
-  if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->base) cudaFree(h->base);
   if (h->h_out) cudaFreeHost(h->h_out);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
