@@ -473,6 +473,86 @@ def test_diagnostics_by_hand(dim):
     assert oracle.diag(prm, st)[3] is True
 
 
+def _iso_gradient_symbol(dim, iso, theta, dx, a):
+    """Component a of the isotropic gradient symbol: the x formula with axis a
+    taken first (every lattice is symmetric in the two other axes)."""
+    order = [a] + [t for t in range(dim) if t != a]
+    return iso_gradient_symbol_x(dim, iso, [theta[t] for t in order], dx)
+
+
+def _rk_forced(y, hl, hb, scheme):
+    """One step of Eq. tvd-rk2 or Eq. rk4 for dy/dt = l y + b, b frozen."""
+    f = lambda v: hl * v + hb
+    if scheme == 2:
+        y1 = y + f(y)
+        return 0.5 * y + 0.5 * (y1 + f(y1))
+    k1 = f(y)
+    k2 = f(y + 0.5 * k1)
+    k3 = f(y + 0.5 * k2)
+    k4 = f(y + k3)
+    return y + (k1 + 2.0 * k2 + 2.0 * k3 + k4) / 6.0
+
+
+@pytest.mark.parametrize("dim,iso,scheme,modes", [(2, 9, 2, [(1, 0), (2, 3), (3, 1)]),
+                                                   (3, 15, 4, [(1, 1, 1), (2, 0, 1)]),
+                                                   (3, 19, 2, [(1, 2, 1)]),
+                                                   (3, 27, 4, [(2, 1, 1)])])
+def test_velocity_mode_moves_phi_only_in_the_conservative_form(dim, iso, scheme, modes):
+    """A velocity mode on a uniform phi0 (sigma = 0, g = 0, so phi does not act
+    back on the flow at linear order): the flow evolves it by P3(dt A); the CH
+    step of step n sees the cell velocity of Eq. u-center-2d, whose symbol is
+    cos(theta_a / 2) (U^n_a + U^{n+1}_a) / 2.  The conservative form
+    -div_iso(uhat phi) then adds -phi0 sum_a g_a uhat_a to the rate of the phi
+    mode, g_a the isotropic gradient symbol, frozen over the CH stages; the
+    advective form u.grad phi adds nothing at linear order."""
+    n = [8, 6, 8][:dim]
+    phi0 = 0.4
+    amp_phi = 0.3 - 0.6j
+    eps = 1e-6
+    nsteps = 20
+    for cons in (1, 0):
+        prm = inputs.base_params(dim, *([8, 6, 8][:dim] + [1] * (3 - dim)), dx=0.5, dt=0.05, cs=1.3,
+                                 rhoL=1.7, rhoG=0.4, etaL=0.05, etaG=0.02, sigma=0.0, M=0.01, W=3.0, iso=iso,
+                                 ch_scheme=scheme, ch_advection=cons)
+        rng = np.random.default_rng(5)
+        a_, kappa = 3.0 / (4.0 * prm["W"]), 3.0 * prm["W"] / 8.0
+        fpp = 4.0 * a_ * (3.0 * phi0 * phi0 - 1.0)
+        names = "uvw"[:dim]
+        for m in modes:
+            theta = [2.0 * math.pi * m[a] / n[a] for a in range(dim)]
+            q0 = rng.normal(size=dim + 1) + 1j * rng.normal(size=dim + 1)
+            res = []
+            for sgn in (1.0, -1.0):
+                f = inputs.zero_fields(prm)
+                f["phi"] = phi0 + _mode_field(prm, "c", sgn * eps * amp_phi, theta)
+                f["p"] = _mode_field(prm, "c", sgn * eps * q0[0], theta)
+                for a, nm in enumerate(names):
+                    f[nm] = _mode_field(prm, nm, sgn * eps * q0[1 + a], theta)
+                st = oracle.init_state(prm, f["phi"], f["p"], f["u"], f["v"], f.get("w"))
+                res.append(oracle.step(prm, st, nsteps))
+            G = rk3_amplification(prm["dt"] * flow_symbol(prm, theta, phi0))
+            lam = iso_laplacian_symbol(dim, iso, theta, prm["dx"])
+            hl = prm["dt"] * prm["M"] * lam * (fpp - kappa * lam)
+            g = [_iso_gradient_symbol(dim, iso, theta, prm["dx"], a) for a in range(dim)]
+            q, ph = q0.astype(complex), complex(amp_phi)
+            for _ in range(nsteps):
+                q1 = G @ q
+                uhat = [math.cos(theta[a] / 2.0) * 0.5 * (q[1 + a] + q1[1 + a]) for a in range(dim)]
+                b = -phi0 * sum(g[a] * uhat[a] for a in range(dim)) if cons else 0.0
+                ph = _rk_forced(ph, hl, prm["dt"] * b, scheme)
+                q = q1
+            lin = 0.5 * (res[0]["phi"] - res[1]["phi"])
+            want = _mode_field(prm, "c", eps * ph, theta)
+            scale = eps * max(abs(ph), 1e-2)
+            assert np.max(np.abs(lin - want)) / scale < 1e-7, (cons, m)
+            if cons:
+                # the velocity's share is visible: without it the comparison fails
+                ph0 = complex(amp_phi)
+                for _ in range(nsteps):
+                    ph0 = _rk_forced(ph0, hl, 0.0, scheme)
+                assert abs(ph0 - ph) > 0.05 * abs(ph), m
+
+
 # ----------------------------------------------------------------------------
 # time-centred advection velocity: uniformly accelerated, density-matched flow
 # ----------------------------------------------------------------------------
