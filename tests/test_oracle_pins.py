@@ -168,6 +168,66 @@ def test_flow_operator_fourier_closed_form(dim, shape, phi0, bulk, pavg, modes):
         assert np.max(np.abs(out["phi"] - phi0)) < 1e-14
 
 
+WALL_CASES = [
+    # dim, shape, free-slip axes, phi0, bulk, pavg, mode indices (pi m / n on a wall axis, 2 pi m / n else)
+    (2, (8, 6, 1), (0,), 1.0, 1, 1, [(1, 1), (3, 2), (7, 0)]),
+    (2, (6, 8, 1), (0, 1), 0.3, 1, 1, [(1, 1), (2, 5)]),
+    (3, (6, 4, 6), (0, 2), 1.0, 1, 1, [(1, 1, 1), (2, 0, 3), (5, 1, 1)]),
+    (3, (4, 6, 4), (0, 1, 2), -1.0, 0, 1, [(1, 2, 3), (3, 1, 1)]),
+]
+
+
+@pytest.mark.parametrize("dim,shape,walls,phi0,bulk,pavg,modes", WALL_CASES)
+def test_flow_operator_between_free_slip_walls(dim, shape, walls, phi0, bulk, pavg, modes):
+    """Between free-slip walls the cosine-sine modes are exact eigenmodes of
+    the discrete operator when the ghost rules are the mirror images the wall
+    implies: p, phi and the tangential velocities even about the wall, the
+    normal velocity odd (zero on the wall face).  Such a mode is the sum of
+    the complex modes with theta mirrored on the wall axes, each carrying the
+    amplitude vector with the mirrored normal components negated; all of them
+    evolve by P3(dt A(theta)), so the fields after n steps follow in closed
+    form.  This pins the ghost rules, including the corner ghosts of two
+    walls that the edge viscosities and the averaged pressure read."""
+    nx, ny, nz = shape
+    bc = tuple("freeslip" if a in walls else "periodic" for a in range(3))
+    prm = inputs.base_params(dim, nx, ny, nz, dx=0.5, dt=0.05, cs=1.3, rhoL=1.7, rhoG=0.4, etaL=0.05,
+                             etaG=0.02, sigma=0.02, M=0.01, W=3.0, bulk_visc=bulk, p_average=pavg, bc=bc)
+    n = [nx, ny, nz][:dim]
+    names = "uvw"[:dim]
+    rng = np.random.default_rng(17)
+    eps, nsteps = 1e-30, 40
+
+    def fields_of(q, theta):
+        out = {k: 0.0 for k in ["p", *names]}
+        for signs in np.ndindex(*([2] * len(walls))):
+            th = list(theta)
+            qs = q.astype(complex).copy()
+            for w, s in zip(walls, signs):
+                if s:
+                    th[w] = -th[w]
+                    qs[1 + w] = -qs[1 + w]
+            out["p"] = out["p"] + _mode_field(prm, "c", eps * qs[0], th)
+            for a, nm in enumerate(names):
+                out[nm] = out[nm] + _mode_field(prm, nm, eps * qs[1 + a], th)
+        return out
+
+    for m in modes:
+        theta = [(math.pi if a in walls else 2.0 * math.pi) * m[a] / n[a] for a in range(dim)]
+        q0 = rng.normal(size=dim + 1) + 1j * rng.normal(size=dim + 1)
+        f0 = fields_of(q0, theta)
+        for w in walls:
+            assert np.max(np.abs(np.take(f0["uvw"[w]], 0, axis=dim - 1 - w))) < 1e-12 * eps
+        f = inputs.zero_fields(prm)
+        f["phi"][...] = phi0
+        st = oracle.init_state(prm, f["phi"], f0["p"], f0["u"], f0["v"], f0.get("w"))
+        out = oracle.step(prm, st, nsteps)
+        qN = np.linalg.matrix_power(rk3_amplification(prm["dt"] * flow_symbol(prm, theta, phi0)), nsteps) @ q0
+        want = fields_of(qN, theta)
+        scale = max(np.max(np.abs(want[k])) for k in want)
+        err = max(np.max(np.abs(out[k] - want[k])) for k in want) / scale
+        assert err < 1e-11, (m, err)
+
+
 def convection_symbol(prm, theta, ubg):
     """Centred convection of Eq. conv-u-discretization linearised about a
     uniform velocity U, by hand: every velocity component is carried by
