@@ -775,6 +775,44 @@ def test_variable_viscosity_shear_closed_form():
     assert np.max(np.abs(out["phi"] - phi)) < 1e-12
 
 
+@pytest.mark.parametrize("dim,wall,flow", [(2, 1, 0), (3, 2, 0), (3, 0, 1)])
+def test_body_force_channel_between_no_slip_walls(dim, wall, flow):
+    """A body force along a periodic axis between two no-slip walls, one phase
+    (phi = 1, rho_ref = 0): the flow is u(y) with nu u'' = -g.  With the
+    tangential ghost odd about the wall (the wall value, the mean of the
+    ghost and the first cell, is zero) the discrete steady state of the
+    3-point operator is exactly u_j = a y_j (H - y_j) + a dx^2 / 4,
+    a = g / (2 nu), at the cell-centre heights y_j = (j + 1/2) dx (the 3-point
+    second difference of a parabola is exact, and the constant makes the
+    wall mean vanish).  The oracle keeps that profile stationary, and p and
+    the other components at zero."""
+    shape = [4, 4, 4]
+    shape[wall] = 16
+    bc = ["periodic"] * 3
+    bc[wall] = "noslip"
+    g = [0.0, 0.0, 0.0]
+    g[flow] = 0.01
+    prm = inputs.base_params(dim, *shape, dx=0.5, dt=0.05, cs=1.3, rhoL=1.7, rhoG=0.4, etaL=0.05, etaG=0.02,
+                             sigma=0.02, M=0.01, W=3.0, g=tuple(g), bc=tuple(bc), rho_ref=0.0)
+    nu = prm["etaL"] / prm["rhoL"]
+    a_ = g[flow] / (2.0 * nu)
+    H = shape[wall] * prm["dx"]
+    y = positions(prm, "uvw"[flow])[wall] * prm["dx"]
+    ustar = a_ * y * (H - y) + a_ * prm["dx"] ** 2 / 4.0
+    # the closed form is the discrete steady state: nu D2 u + g = 0 with odd ghosts
+    line = np.take(np.moveaxis(ustar, dim - 1 - wall, -1).reshape(-1, shape[wall]), 0, axis=0)
+    ext = np.concatenate([[-line[0]], line, [-line[-1]]])
+    assert np.max(np.abs(nu * (ext[2:] - 2 * ext[1:-1] + ext[:-2]) / prm["dx"] ** 2 + g[flow])) < 1e-15
+    f = inputs.zero_fields(prm)
+    f["phi"][...] = 1.0
+    f["uvw"[flow]] = ustar
+    st = oracle.init_state(prm, f["phi"], f["p"], f["u"], f["v"], f.get("w"))
+    out = oracle.step(prm, st, 100)
+    assert np.max(np.abs(out["uvw"[flow]] - ustar)) < 1e-13 * np.max(ustar)
+    for k in ["p", *[c for c in "uvw"[:dim] if c != "uvw"[flow]]]:
+        assert np.max(np.abs(out[k])) < 1e-15, k
+
+
 # ----------------------------------------------------------------------------
 # invariants
 # ----------------------------------------------------------------------------
