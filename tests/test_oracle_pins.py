@@ -613,6 +613,54 @@ def test_velocity_mode_moves_phi_only_in_the_conservative_form(dim, iso, scheme,
                 assert abs(ph0 - ph) > 0.05 * abs(ph), m
 
 
+@pytest.mark.parametrize("dim,iso,scheme,shape,walls,bcname", [
+    (2, 9, 2, (8, 6, 1), (0, 1), "noslip"),
+    (3, 15, 4, (6, 4, 6), (0, 2), "freeslip"),
+    (3, 19, 2, (4, 6, 4), (0, 1, 2), "noslip"),
+    (3, 27, 4, (6, 4, 4), (1,), "freeslip"),
+])
+def test_ch_step_between_walls(dim, iso, scheme, shape, walls, bcname):
+    """Walls give phi and mu even ghosts (no flux through the wall), on either
+    kind of wall.  A cosine mode across the wall axes is then an exact
+    eigenfunction of the isotropic stencils, diagonal neighbours across a
+    corner included, and decays or grows by the periodic CH amplification
+    with theta = pi m / n on those axes."""
+    nx, ny, nz = shape
+    bc = tuple(bcname if a in walls else "periodic" for a in range(3))
+    prm = inputs.base_params(dim, nx, ny, nz, dx=1.0, dt=0.4, sigma=0.0, M=0.05, W=4.0, iso=iso,
+                             ch_scheme=scheme, bc=bc)
+    n = [nx, ny, nz][:dim]
+    phi0 = 0.6
+    a_, kappa = 3.0 / (4.0 * prm["W"]), 3.0 * prm["W"] / 8.0
+    fpp = 4.0 * a_ * (3.0 * phi0 * phi0 - 1.0)
+    eps, nsteps = 1e-6, 30
+    for m in [tuple(1 + (k + a) % (n[a] - 1) for a in range(dim)) for k in range(3)]:
+        theta = [(math.pi if a in walls else 2.0 * math.pi) * m[a] / n[a] for a in range(dim)]
+
+        def mode(amp):
+            tot = 0.0
+            for signs in np.ndindex(*([2] * len(walls))):
+                th = list(theta)
+                for w, sg in zip(walls, signs):
+                    if sg:
+                        th[w] = -th[w]
+                tot = tot + _mode_field(prm, "c", amp, th)
+            return tot
+
+        res = []
+        for sgn in (1.0, -1.0):
+            f = inputs.zero_fields(prm)
+            f["phi"] = phi0 + mode(sgn * eps * (0.8 + 0.3j))
+            out = oracle.step(prm, oracle.init_state(prm, f["phi"]), nsteps)
+            assert np.max(np.abs(out["u"])) == 0.0
+            res.append(out["phi"] - phi0)
+        lam = iso_laplacian_symbol(dim, iso, theta, prm["dx"])
+        gN = ch_polynomial(prm["dt"] * prm["M"] * lam * (fpp - kappa * lam), scheme) ** nsteps
+        want = mode(eps * (0.8 + 0.3j) * gN)
+        scale = eps * max(abs(gN), 1.0)
+        assert np.max(np.abs(0.5 * (res[0] - res[1]) - want)) / scale < 1e-8, m
+
+
 # ----------------------------------------------------------------------------
 # time-centred advection velocity: uniformly accelerated, density-matched flow
 # ----------------------------------------------------------------------------
