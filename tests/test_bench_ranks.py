@@ -1,7 +1,7 @@
 """Host logic of bench.py on CPU: two gloo ranks agree on the
 slowest rank's time, the job value counts every rank's replica, the
-reference arm runs on rank 0 only, and the clock record of the timed region
-is read from nvidia-smi's lines."""
+reference arm runs on rank 0 only and prints the contract's JSON line, and
+the clock record of the timed region is read from nvidia-smi's lines."""
 from __future__ import annotations
 
 import os
