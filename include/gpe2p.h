@@ -83,8 +83,9 @@ typedef struct {
                             * (u_r = 0, every other ghost even) whatever bc[0] says; bc[0] is
                             * the outer wall (NOSLIP or FREESLIP; PERIODIC is refused).  Needs
                             * ch_advection = 0 and g[0] = 0.  The stability limits and the
-                            * diagnostics stay those of the planar (x, y) grid: int_phi and
-                            * kinetic sum over the (r, z) plane, not over the volume. */
+                            * diagnostics stay those of the planar (x, y) grid (the limits
+                            * remain safe for the axisymmetric operator); int_phi and kinetic
+                            * sum over the (r, z) plane, not over the volume. */
 } gpe2p_params;
 
 typedef struct gpe2p_ctx *gpe2p_handle;
