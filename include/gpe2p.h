@@ -83,8 +83,9 @@ typedef struct {
                             * (u_r = 0, every other ghost even) whatever bc[0] says; bc[0] is
                             * the outer wall (NOSLIP or FREESLIP; PERIODIC is refused).  Needs
                             * ch_advection = 0 and g[0] = 0.  The stability limits and the
-                            * diagnostics stay those of the planar (x, y) grid (the limits
-                            * remain safe for the axisymmetric operator); int_phi and kinetic
+                            * diagnostics stay those of the planar (x, y) grid (on small test
+                            * grids the limits held for the axisymmetric operator's spectrum
+                            * too); int_phi and kinetic
                             * sum over the (r, z) plane, not over the volume. */
 } gpe2p_params;
 
