@@ -85,8 +85,8 @@ typedef struct {
                             * ch_advection = 0 and g[0] = 0.  The stability limits and the
                             * diagnostics stay those of the planar (x, y) grid (on small test
                             * grids the limits held for the axisymmetric operator's spectrum
-                            * too); int_phi and kinetic
-                            * sum over the (r, z) plane, not over the volume. */
+                            * too); int_phi and kinetic sum over the (r, z) plane, not over
+                            * the volume. */
 } gpe2p_params;
 
 typedef struct gpe2p_ctx *gpe2p_handle;
