@@ -11,7 +11,10 @@
 //
 // Set-up: the first call on a device, with that device current, looks up the
 // device address of the array (cudaGetSymbolAddress) and keeps it; that first
-// call should therefore come before any stream capture.  All calls share the
+// call should therefore come before any stream capture.  Later calls that are
+// not made while their stream is capturing look the address up again, so
+// that a device reset (which reloads the library's device code, possibly at
+// another address) does not leave a stale one behind.  All calls share the
 // array: each call overwrites the slots it uses before reading them, and two
 // calls whose kernels overlap on the GPU race on it.
 #include <cuda_runtime.h>
@@ -54,7 +57,8 @@ __device__ __forceinline__ double na_warp_max(double v) {
 template <typename real, int DIM>
 __global__ void __launch_bounds__(NA_THREADS) na_partial_kernel(const KParams<real> P, const real* p, const real* u0,
                                                                 const real* u1, const real* u2, const real* phi,
-                                                                double* slots, long long ncell) {
+                                                                const real* phi_lo, double* slots,
+                                                                long long ncell) {
   const real* U[3] = {u0, u1, u2};
   double sphi = 0.0, ke = 0.0, umax = 0.0, bad = 0.0;
   const long long base = (long long)blockIdx.x * NA_CELLS_PER_BLOCK;
@@ -65,7 +69,10 @@ __global__ void __launch_bounds__(NA_THREADS) na_partial_kernel(const KParams<re
     const int j = (int)((id / P.n[0]) % P.n[1]);
     const int k = (int)(id / ((long long)P.n[0] * P.n[1]));
     const long long q = gpe2p::lin(P, i, j, k);
-    const double f = (double)phi[q];
+    // phi of the cell: the stored value plus, under the compensated
+    // accumulation, its low part; the lower neighbour's phi in the face
+    // density is the stored value alone, as in gpe2p_diagnostics
+    const double f = (double)phi[q] + (phi_lo ? (double)phi_lo[q] : 0.0);
     sphi += f;
     if (!isfinite(f) || !isfinite((double)p[q])) bad = 1.0;
     const double rho0 = 0.5 * ((double)P.rhoL * (1.0 + f) + (double)P.rhoG * (1.0 - f));
@@ -140,15 +147,19 @@ __global__ void __launch_bounds__(NA_THREADS) na_final_kernel(const double* slot
   }
 }
 
-// the device address of the scratch array on the current device, looked up
-// once per device
-cudaError_t scratch_on_current_device(double** ptr) {
+// the device address of the scratch array on the current device: looked up on
+// the first call on a device, and again on every call whose stream is not
+// capturing (a capture keeps the address found before it)
+cudaError_t scratch_on_current_device(cudaStream_t s, double** ptr) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= NA_MAX_DEVICES) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const bool capturing = cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+  if (capturing) cudaGetLastError();  // a query refused during a capture leaves no sticky error
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev] || !capturing) {
     double* p = nullptr;
     e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
@@ -160,10 +171,11 @@ cudaError_t scratch_on_current_device(double** ptr) {
 
 template <typename real, int DIM>
 cudaError_t launch(const KParams<real>& P, const void* p, const void* u, const void* v, const void* w,
-                   const void* phi, double* slots, long long ncell, int nblocks, double vol, double* out,
-                   cudaStream_t s) {
+                   const void* phi, const void* phi_lo, double* slots, long long ncell, int nblocks, double vol,
+                   double* out, cudaStream_t s) {
   na_partial_kernel<real, DIM><<<nblocks, NA_THREADS, 0, s>>>(P, (const real*)p, (const real*)u, (const real*)v,
-                                                              (const real*)w, (const real*)phi, slots, ncell);
+                                                              (const real*)w, (const real*)phi,
+                                                              (const real*)phi_lo, slots, ncell);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   na_final_kernel<<<1, NA_THREADS, 0, s>>>(slots, nblocks, vol, out);
@@ -188,8 +200,8 @@ KParams<real> na_params(const gpe2p_params& q, long long row_pitch) {
 }  // namespace
 
 extern "C" int gpe2p_diagnostics_noalloc(const gpe2p_params* q, const void* p, const void* u, const void* v,
-                                         const void* w, const void* phi, long long row_pitch, double* out,
-                                         void* stream) {
+                                         const void* w, const void* phi, const void* phi_lo,
+                                         long long row_pitch, double* out, void* stream) {
   if (!q || !p || !u || !v || !phi || !out) return GPE2P_EINVAL;
   if (q->dim != 2 && q->dim != 3) return GPE2P_EINVAL;
   if (q->dim == 3 && !w) return GPE2P_EINVAL;
@@ -201,20 +213,20 @@ extern "C" int gpe2p_diagnostics_noalloc(const gpe2p_params* q, const void* p, c
     if (q->bc[a] < 0 || q->bc[a] > 2) return GPE2P_EINVAL;
   const long long ncell = (long long)q->nx * q->ny * nz;
   if (ncell > GPE2P_NOALLOC_MAX_CELLS) return GPE2P_EINVAL;  // more cells than the scratch slots cover
+  cudaStream_t s = (cudaStream_t)stream;
   double* slots = nullptr;
-  if (scratch_on_current_device(&slots) != cudaSuccess) return GPE2P_ECUDA;
+  if (scratch_on_current_device(s, &slots) != cudaSuccess) return GPE2P_ECUDA;
   const int nblocks = (int)((ncell + NA_CELLS_PER_BLOCK - 1) / NA_CELLS_PER_BLOCK);
   const double vol = q->dim == 3 ? q->dx * q->dx * q->dx : q->dx * q->dx;
-  cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
   if (q->precision == 32) {
     const KParams<float> P = na_params<float>(*q, row_pitch);
-    e = q->dim == 2 ? launch<float, 2>(P, p, u, v, w, phi, slots, ncell, nblocks, vol, out, s)
-                    : launch<float, 3>(P, p, u, v, w, phi, slots, ncell, nblocks, vol, out, s);
+    e = q->dim == 2 ? launch<float, 2>(P, p, u, v, w, phi, phi_lo, slots, ncell, nblocks, vol, out, s)
+                    : launch<float, 3>(P, p, u, v, w, phi, phi_lo, slots, ncell, nblocks, vol, out, s);
   } else {
     const KParams<double> P = na_params<double>(*q, row_pitch);
-    e = q->dim == 2 ? launch<double, 2>(P, p, u, v, w, phi, slots, ncell, nblocks, vol, out, s)
-                    : launch<double, 3>(P, p, u, v, w, phi, slots, ncell, nblocks, vol, out, s);
+    e = q->dim == 2 ? launch<double, 2>(P, p, u, v, w, phi, phi_lo, slots, ncell, nblocks, vol, out, s)
+                    : launch<double, 3>(P, p, u, v, w, phi, phi_lo, slots, ncell, nblocks, vol, out, s);
   }
   return e == cudaSuccess ? GPE2P_OK : GPE2P_ECUDA;
 }
