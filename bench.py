@@ -245,6 +245,72 @@ def measure_axisym(stream, steps=400, warmup=5):
     return out
 
 
+def measure_static_drop(stream, steps=2000, settled=8000):
+    """The 64 x 64 static drop (R = 16, density and viscosity ratio 10, FP64 on
+    the GPU): after `steps` steps, the pressure jump of the stored p and of
+    P = p + sigma phi mu (the pressure of the equivalent mu grad phi form,
+    which carries the Laplace jump) between the inner disc r < R/2 and the
+    outer band r > R + 8, against sigma / R_eff with R_eff the radius of the
+    phi > 0 area; the relative drift of the phi integral, in the paper's
+    advective CH form and in the conservative variant; and the largest
+    spurious velocity, also as a fraction of the capillary velocity
+    sigma / eta_L.  The same jump after `settled` steps, once the slow
+    transient has decayed."""
+    import torch
+    from paper_2011_00814_gb300 import gpe2p
+    prm, f = inputs.static_drop()
+    n = prm["nx"]
+    x, y = inputs.cell_centres(prm)
+    r = np.hypot(x - n / 2.0, y - n / 2.0)
+    inner, outer = r < 8.0, r > 24.0
+    abs0 = float(np.sum(np.abs(f["phi"]))) * prm["dx"] ** 2
+    Uc = prm["sigma"] / prm["etaL"]
+
+    def jump(out):
+        R_eff = math.sqrt(float(np.sum(out["phi"] > 0)) / math.pi)
+        P = out["p"] + prm["sigma"] * out["phi"] * out["mu"]
+        dp = float(np.mean(out["p"][inner]) - np.mean(out["p"][outer]))
+        dP = float(np.mean(P[inner]) - np.mean(P[outer]))
+        lap = prm["sigma"] / R_eff
+        return {"R_eff": R_eff, "sigma_over_R_eff": lap, "dp": dp, "dP": dP, "dP_over_laplace": dP / lap,
+                "dp_over_laplace": dp / lap, "within_2pct": abs(dP / lap - 1.0) <= 0.02}
+
+    res = {"workload": "static drop 64x64 periodic, R=16, FP64, density/viscosity ratio 10, 2000 steps",
+           "U_c": Uc}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for form in (0, 1):
+        with gpe2p.Solver(dict(prm, precision=64, ch_advection=form), stream=stream.cuda_stream) as s:
+            s.init_fields(f)
+            d0 = s.diagnostics()
+            e0.record(stream)
+            s.advance(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out = s.read_fields()
+            d = s.diagnostics()
+            row = {"int_phi_drift": abs(d["int_phi"] - d0["int_phi"]) / abs0,
+                   "max_spurious_u": float(max(np.max(np.abs(out["u"])), np.max(np.abs(out["v"])))),
+                   "ms_per_step": e0.elapsed_time(e1) / steps}
+            row["max_spurious_u_over_Uc"] = row["max_spurious_u"] / Uc
+            if form == 0:
+                row.update(jump(out))
+                s.advance(settled - steps)
+                row["settled"] = dict(jump(s.read_fields()), steps=settled)
+            res["advective" if form == 0 else "conservative"] = row
+    return res
+
+
+def measure_fp_rates():
+    """The measured multiply-add rates of the device in FP64 and FP32
+    (gpe2p_fma_rate), the bound of the FP64 path."""
+    from paper_2011_00814_gb300 import gpe2p
+    out = {}
+    for prec in (64, 32):
+        r = gpe2p.fma_rate(prec)
+        out[f"fp{prec}_tflops"] = r["flops_per_s"] / 1e12
+    return out
+
+
 def cpu_baseline_axisym(steps=2):
     """The CPU oracle on a two-step sample of the axisymmetric falling drop."""
     import oracle
@@ -518,6 +584,9 @@ def main():
         "clocks": clk.summary(),
         "diag": {"int_phi": d["int_phi"], "umax": d["umax"], "nan": d["nan_flag"]},
     }
+    if world == 1:
+        line["fp_rates"] = measure_fp_rates()
+        line["static_drop"] = measure_static_drop(stream)
     if not args.no_batch:
         line["batch2d"] = measure_batch2d(stream)
     if not args.no_axisym and world == 1:

@@ -157,18 +157,36 @@ int gpe2p_diagnostics(gpe2p_handle h, gpe2p_diag *out);
  * NULL; Lw is ignored in 2D.  Synchronises. */
 int gpe2p_eval_rates(gpe2p_handle h, double *Lp, double *Lu, double *Lv, double *Lw, double *Lphi);
 
-/* Measurement aid: advances nsteps full steps launched eagerly (not from
- * the graphs), timing every kernel launch of a step with CUDA events on the
- * handle's stream.  ms[i] receives the mean duration in milliseconds of the
- * i-th launch of a step (i < max_launches), *nlaunches the launches per step,
- * names (if not NULL) a comma-separated list of their kernel names, truncated
- * to names_len bytes.  The state advances exactly as with gpe2p_advance.
- * Synchronises. */
+/* Measurement aid: advances nsteps + 1 full steps (1 <= nsteps <= 64)
+ * launched eagerly (not from the graphs) and back to back, timing every
+ * kernel launch of the last nsteps with CUDA events on the handle's stream
+ * (the first step only fills the queue, so that no launch is charged with
+ * the time the host takes to issue it).  ms[i] receives the mean duration in
+ * milliseconds of the i-th launch of a step (i < max_launches), *nlaunches
+ * the launches per step, names (if not NULL) a comma-separated list of their
+ * kernel names, truncated to names_len bytes.  The state advances exactly as
+ * with gpe2p_advance.  Synchronises. */
 int gpe2p_profile_steps(gpe2p_handle h, int nsteps, double *ms, int max_launches, int *nlaunches,
                         char *names, int names_len);
 
+/* Measurement aid (the paper has no counterpart): the rate of fused
+ * multiply-adds of the current device in the given precision (32 or 64),
+ * in floating-point operations per second (two per multiply-add), written to
+ * *flops_per_s; *ms (may be NULL) receives the duration of the timed launch.
+ * Independent chains of multiply-adds in every thread of a grid of eight
+ * 256-thread blocks per SM, sized to run about 50 ms, the best of three
+ * launches after a calibration launch, timed with CUDA events on stream (a
+ * cudaStream_t, NULL for the legacy default stream).  The FP64 path of the
+ * step is bound by this FP64 rate rather than by memory bandwidth.
+ * Allocates nothing; synchronises the stream.  GPE2P_EINVAL for a NULL
+ * pointer or another precision, GPE2P_ECUDA if a launch fails. */
+int gpe2p_fma_rate(int precision, double *flops_per_s, double *ms, void *stream);
+
 /* Device pointer of a field of the current state, in the handle's precision
- * (float or double): which = 0 p, 1 u, 2 v, 3 w, 4 phi, 5 mu.  On the device
+ * (float or double): which = 0 p, 1 u, 2 v, 3 w, 4 phi, 5 mu, 6 the low part
+ * of phi under the compensated accumulation (phi = field 4 + field 6; see
+ * gpe2p_set_phi_accumulation), for which *dptr is NULL while that
+ * accumulation is not active.  On the device
  * every field is stored x-fastest with rows padded to *row_pitch elements
  * (a multiple of 32; row (j, k) starts at element (k ny + j) row_pitch);
  * row_pitch may be NULL.  Valid until the next call that advances,
@@ -208,15 +226,27 @@ int gpe2p_diagnostics_instance(gpe2p_handle h, int inst, gpe2p_diag *out);
  * persistent form (0: one launch per sweep), and its measured ms per step. */
 int gpe2p_batch_config(gpe2p_handle h, int *tile_x, int *tile_y, int *persistent, double *ms_per_step);
 
-/* Host-side fault injection and test switches of a batch (rebuilds its step
- * graphs): GPE2P_FAULT_SKIP_BARRIER (value = block index that never arrives
- * at the grid barrier; -1 none), GPE2P_FAULT_WAIT_LIMIT (barrier wait limit
- * in SM clock cycles), GPE2P_FAULT_FORCE_PERSISTENT (1: persistent form,
- * 0: one launch per sweep), GPE2P_FAULT_CLEAR (defaults, and clears the
- * error word).  A barrier wait that runs out makes every block return and
- * the next diagnostics report GPE2P_ETIMEOUT; the state is then undefined. */
+/* Host-side fault injection and test switches (rebuilds the step graphs).
+ * A batch takes GPE2P_FAULT_SKIP_BARRIER (value = block index that never
+ * arrives at the grid barrier; -1 none), GPE2P_FAULT_WAIT_LIMIT (barrier wait
+ * limit in SM clock cycles), GPE2P_FAULT_FORCE_PERSISTENT (1: persistent
+ * form, 0: one launch per sweep) and GPE2P_FAULT_CLEAR (defaults, and clears
+ * the error word).  A barrier wait that runs out makes every block return and
+ * the next diagnostics report GPE2P_ETIMEOUT; the state is then undefined.
+ * A single 3D problem takes GPE2P_FAULT_LOSE_COPY, value a mask of
+ * GPE2P_LOSE_* bits: in every block of the chosen kernels the first wait of
+ * that kind for a plane copy (which still completes, so that no copy is left
+ * in flight) is reported as timed out, as if the copy had been lost; the
+ * block then records the error, waits for its other copies and returns, and
+ * the next diagnostics report GPE2P_ETIMEOUT.  GPE2P_FAULT_CLEAR (value
+ * ignored) turns it off and clears the error word; gpe2p_init_fields also
+ * clears the error word.  No fault reaches the GPU: only the kernels' own
+ * bounded-wait bookkeeping is exercised. */
 enum { GPE2P_FAULT_SKIP_BARRIER = 1, GPE2P_FAULT_WAIT_LIMIT = 2, GPE2P_FAULT_FORCE_PERSISTENT = 3,
-       GPE2P_FAULT_CLEAR = 4 };
+       GPE2P_FAULT_CLEAR = 4, GPE2P_FAULT_LOSE_COPY = 5 };
+/* bits of GPE2P_FAULT_LOSE_COPY: the plane rings of the flow stage, of the CH
+ * stages and of mu, and the CH stages' point planes */
+enum { GPE2P_LOSE_FLOW_RING = 1, GPE2P_LOSE_CH_RING = 2, GPE2P_LOSE_MU_RING = 4, GPE2P_LOSE_CH_POINTS = 8 };
 int gpe2p_set_fault_injection(gpe2p_handle h, int what, long long value);
 
 /* ---- precision policy of the phi accumulation --------------------------
@@ -342,18 +372,25 @@ int gpe2p_state_distance(gpe2p_handle h, int inst, const float *tensor, int nch,
  *   64: double), in the layout of gpe2p_field_ptr with rows of row_pitch
  *   elements (>= nx); w may be NULL in 2D.  Only the dim, nx, ny, nz, dx,
  *   rhoL, rhoG, bc and precision members of *p are used.
+ *   phi_lo: the low part of phi in the same layout and precision (field 6 of
+ *   gpe2p_field_ptr, while the compensated accumulation is active), or NULL
+ *   for none.  With it, the phi integral and each cell's density take
+ *   phi + phi_lo, as gpe2p_diagnostics does.
  *   stream: a cudaStream_t, or NULL for the legacy default stream.  The call
  *   is asynchronous; out is valid once the stream has reached it.
  * It allocates nothing: its scratch is a fixed device array of 512 KiB in the
  * library, held by every GPU that loads the library until the process
  * exits.  The first call on a device (with that device current) looks up
- * that array's device address, so it should come before any stream capture.
- * All calls share the array: calls whose work overlaps on the GPU race.
+ * that array's device address, so it should come before any stream capture;
+ * calls made while their stream is not capturing look it up again, so the
+ * call stays valid after a device reset.  All calls share the array: calls
+ * whose work overlaps on the GPU race.
  * Returns GPE2P_EINVAL for a NULL pointer, bad parameters or more than
  * GPE2P_NOALLOC_MAX_CELLS cells, GPE2P_ECUDA if a launch fails; it records
  * no error text. */
 int gpe2p_diagnostics_noalloc(const gpe2p_params *p, const void *pfield, const void *u, const void *v,
-                              const void *w, const void *phi, long long row_pitch, double *out, void *stream);
+                              const void *w, const void *phi, const void *phi_lo, long long row_pitch,
+                              double *out, void *stream);
 
 /* Text of the handle's last error ("" if none); with h == NULL, the last
  * error of a failed gpe2p_create on this thread. */

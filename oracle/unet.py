@@ -14,6 +14,19 @@ b; decoder L-2..0 up, a, b) weights [cout][tap][cin] with
 tap = 3(dy+1) + (dx+1), then bias [cout]; then head weights [out][c0] and
 bias [out].  Everything is written out with numpy primitives and explicit
 loops over the nine taps; backward passes are the adjoints, derived by hand.
+
+With bf16=True the FP64 arithmetic is kept but every tensor the network
+stores in BF16 is rounded to BF16 (nearest, ties to even, through FP32) where
+it is stored: the padded input, each convolution's pre-activation z (kept for
+the backward pass) and its output SiLU(z) (SiLU of the unrounded z), the
+pooled tensors, and in the backward pass the gradient of every stored
+activation: the head's input gradient, dz = dy SiLU'(z) of each convolution,
+each convolution's input gradient, the sum of the four children of an
+upsampled pixel and the encoder gradient after the pooled gradient is added.
+Weights and biases are given already rounded by the caller.  What remains
+between this and a BF16/FP32 implementation is the accumulation (FP64 here)
+and the rounding of a stored value whose FP32 and FP64 sums fall on the two
+sides of a BF16 rounding boundary.
 """
 from __future__ import annotations
 
@@ -60,6 +73,18 @@ def pack(grads, levels, channels, in_ch, out_ch):
         parts += [grads[name + ".w"].ravel(), grads[name + ".b"].ravel()]
     parts += [grads["head.w"].ravel(), grads["head.b"].ravel()]
     return np.concatenate(parts)
+
+
+def round_bf16(a):
+    """Round to the nearest BF16 value (8 significant bits, ties to even),
+    through FP32 as a BF16/FP32 implementation holds the value first."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _same(a):
+    return a
 
 
 def shift(x, dy, dx):
@@ -111,59 +136,64 @@ def upsample_backward(dy):
     return dy.reshape(B, H // 2, 2, W // 2, 2, C).sum(axis=(2, 4))
 
 
-def forward(params, x, levels, channels, in_ch, out_ch, keep=False):
+def forward(params, x, levels, channels, in_ch, out_ch, keep=False, bf16=False):
     """Network output for x [B, H, W, in_ch]; with keep=True also the saved
-    tensors the backward pass needs."""
+    tensors the backward pass needs; bf16=True rounds the stored tensors to
+    BF16 (module docstring)."""
+    r = round_bf16 if bf16 else _same
     p = unpack(params, levels, channels, in_ch, out_ch)
     B, H, W, _ = x.shape
     x16 = np.zeros((B, H, W, 16))
-    x16[..., :in_ch] = x
+    x16[..., :in_ch] = r(x)
     saved = {"x16": x16}
     cur = x16
     enc = []
     for l in range(levels):
         if l > 0:
-            cur = pool(enc[l - 1])
+            cur = r(pool(enc[l - 1]))
             saved[f"pool{l - 1}"] = cur
         za = conv3x3(cur, p[f"enc{l}a.w"], p[f"enc{l}a.b"])
-        a = silu(za)
+        a = r(silu(za))
         zb = conv3x3(a, p[f"enc{l}b.w"], p[f"enc{l}b.b"])
-        e = silu(zb)
-        saved.update({f"enc{l}a.in": cur, f"enc{l}a.z": za, f"enc{l}b.in": a, f"enc{l}b.z": zb})
+        e = r(silu(zb))
+        saved.update({f"enc{l}a.in": cur, f"enc{l}a.z": r(za), f"enc{l}b.in": a, f"enc{l}b.z": r(zb)})
         enc.append(e)
     d = enc[-1]
     for l in range(levels - 2, -1, -1):
         u = upsample(d)
         zu = conv3x3(u, p[f"up{l}.w"], p[f"up{l}.b"])
-        cat = np.concatenate([silu(zu), enc[l]], axis=-1)
+        cat = np.concatenate([r(silu(zu)), enc[l]], axis=-1)
         za = conv3x3(cat, p[f"dec{l}a.w"], p[f"dec{l}a.b"])
-        a = silu(za)
+        a = r(silu(za))
         zb = conv3x3(a, p[f"dec{l}b.w"], p[f"dec{l}b.b"])
-        d = silu(zb)
-        saved.update({f"up{l}.in": u, f"up{l}.z": zu, f"dec{l}a.in": cat, f"dec{l}a.z": za, f"dec{l}b.in": a,
-                      f"dec{l}b.z": zb})
+        d = r(silu(zb))
+        saved.update({f"up{l}.in": u, f"up{l}.z": r(zu), f"dec{l}a.in": cat, f"dec{l}a.z": r(za),
+                      f"dec{l}b.in": a, f"dec{l}b.z": r(zb)})
     y = np.einsum("bhwc,oc->bhwo", d, p["head.w"]) + p["head.b"]
     saved["head.in"] = d
     return (y, saved) if keep else y
 
 
-def loss_and_gradient(params, x, t, levels, channels, in_ch, out_ch):
-    """Mean squared error of net(x) against t and its gradient (flat layout)."""
+def loss_and_gradient(params, x, t, levels, channels, in_ch, out_ch, bf16=False):
+    """Mean squared error of net(x) against t and its gradient (flat layout);
+    bf16=True rounds the stored tensors and gradients to BF16 (module
+    docstring)."""
+    r = round_bf16 if bf16 else _same
     p = unpack(params, levels, channels, in_ch, out_ch)
-    y, s = forward(params, x, levels, channels, in_ch, out_ch, keep=True)
+    y, s = forward(params, x, levels, channels, in_ch, out_ch, keep=True, bf16=bf16)
     n = y.size
     loss = float(np.sum((y - t) ** 2) / n)
     dy = 2.0 * (y - t) / n
     g = {}
     g["head.w"] = np.einsum("bhwc,bhwo->oc", s["head.in"], dy)
     g["head.b"] = dy.sum(axis=(0, 1, 2))
-    dd = np.einsum("bhwo,oc->bhwc", dy, p["head.w"])
+    dd = r(np.einsum("bhwo,oc->bhwc", dy, p["head.w"]))
 
     def layer_back(name, dout):
-        dz = dout * dsilu(s[name + ".z"])
+        dz = r(dout * dsilu(s[name + ".z"]))
         dx, dw, db = conv3x3_backward(s[name + ".in"], p[name + ".w"], dz)
         g[name + ".w"], g[name + ".b"] = dw, db
-        return dx
+        return r(dx)
 
     denc = [None] * levels
     dpool_to_enc = None
@@ -174,10 +204,10 @@ def loss_and_gradient(params, x, t, levels, channels, in_ch, out_ch):
         c = channels[l]
         denc[l] = dcat[..., c:]
         du = layer_back(f"up{l}", dcat[..., :c])
-        dd = upsample_backward(du)
+        dd = r(upsample_backward(du))
     denc_last = dd
     for l in range(levels - 1, -1, -1):
-        de = denc_last if l == levels - 1 else denc[l] + dpool_to_enc
+        de = denc_last if l == levels - 1 else r(denc[l] + dpool_to_enc)
         da = layer_back(f"enc{l}b", de)
         dinp = layer_back(f"enc{l}a", da)
         if l > 0:

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgpe2p.so")
-SOURCES = ["flow.cu", "ch.cu", "diag.cu", "api.cu", "noalloc.cu", "batch.cu", "nn.cu", "net.cu", "pack.cu", "conv_tc.cu"]
+SOURCES = ["flow.cu", "ch.cu", "diag.cu", "api.cu", "noalloc.cu", "batch.cu", "nn.cu", "net.cu", "pack.cu", "conv_tc.cu", "rate.cu"]
 HEADERS = ["gpe2p_dev.cuh", "gpe2p_launch.h", "flow_ops.cuh", "ch_ops.cuh", "ring3d.cuh", "tma.cuh", "batch.h", "nn.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

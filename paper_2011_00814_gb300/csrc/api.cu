@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include <cudaTypedefs.h>
 
@@ -71,6 +72,7 @@ struct gpe2p_ctx {
   double drift_thr = 1e-10;
   double int_phi0 = 0.0, abs_phi0 = 0.0, last_drift = 0.0;
   long long switched_at = -1;
+  int wait_fault = 0;           // test switch of the 3D kernels' timeout paths (WF_* bits)
   std::string err;
 };
 
@@ -293,7 +295,8 @@ struct ProfHook {
 
 template <typename real, int DIM>
 static cudaError_t enqueue_step(gpe2p_ctx* h, int cur, ProfHook* hook = nullptr) {
-  const KParams<real> P = kparams<real>(h->prm);
+  KParams<real> P = kparams<real>(h->prm);
+  P.wait_fault = h->wait_fault;
   cudaStream_t s = h->stream;
   auto mark = [&](const char* name) -> cudaError_t {
     if (!hook) return cudaSuccess;
@@ -703,6 +706,8 @@ extern "C" int gpe2p_init_fields(gpe2p_handle h, const double* phi, const double
   if (!phi || !u || !v || !p || (h->prm.dim == 3 && !w)) return fail(h, GPE2P_EINVAL, "a required field is NULL");
   CK(h, cudaSetDevice(h->dev), "set device");
   h->cur = 0;
+  // a new state starts with a clear error word (a wait that timed out on the old one)
+  CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream), "init_fields");
   cudaError_t e = h->esize == 4 ? init_impl<float>(h, phi, u, v, w, p) : init_impl<double>(h, phi, u, v, w, p);
   if (e != cudaSuccess) return cuda_fail(h, e, "init_fields");
   if (h->phi_lo) CK(h, cudaMemsetAsync(h->phi_lo, 0, field_bytes(h), h->stream), "init_fields");
@@ -935,36 +940,53 @@ extern "C" int gpe2p_profile_steps(gpe2p_handle h, int nsteps, double* ms, int m
   if (!h || !ms || !nlaunches || nsteps < 1 || max_launches < 1) return fail(h, GPE2P_EINVAL, "bad argument");
   if (h->batch) return fail(h, GPE2P_EINVAL, "a batch handle has no per-launch profile");
   if (!h->initialized) return fail(h, GPE2P_ESTATE, "profile_steps before gpe2p_init_fields");
+  if (nsteps > 64) return fail(h, GPE2P_EINVAL, "at most 64 profiled steps");
   CK(h, cudaSetDevice(h->dev), "set device");
+  // One untimed step, then the timed ones, all enqueued back to back with
+  // their own events: each step's first event then waits on the GPU for the
+  // previous step's last kernel, so no launch is charged with the host's
+  // enqueue time (a wait for the GPU between steps would leave it idle while
+  // the next step's first launch is being issued).
   const int cap = 32;
-  cudaEvent_t ev[cap + 1];
+  const int nst = nsteps + 1;
+  std::vector<cudaEvent_t> ev((size_t)nst * (cap + 1), nullptr);
   const char* nm[cap];
-  for (int i = 0; i <= cap; ++i) CK(h, cudaEventCreate(&ev[i]), "event create");
-  ProfHook hook;
-  hook.ev = ev;
-  hook.max = cap;
-  hook.names = nm;
-  for (int i = 0; i < max_launches; ++i) ms[i] = 0.0;
   int rc = GPE2P_OK;
-  for (int s = 0; s < nsteps && rc == GPE2P_OK; ++s) {
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) { rc = cuda_fail(h, cudaGetLastError(), "event create"); break; }
+  for (int i = 0; i < max_launches; ++i) ms[i] = 0.0;
+  int n = 0;
+  for (int s = 0; s < nst && rc == GPE2P_OK; ++s) {
+    ProfHook hook;
+    hook.ev = &ev[(size_t)s * (cap + 1)];
+    hook.max = cap;
+    hook.names = nm;
     cudaError_t e = enqueue(h, h->cur, &hook);
-    if (e == cudaSuccess) e = cudaEventSynchronize(ev[hook.n]);
     if (e != cudaSuccess) { rc = cuda_fail(h, e, "profile step"); break; }
     h->cur = 1 - h->cur;
     h->step += 1;
-    for (int i = 0; i < hook.n && i < max_launches; ++i) {
+    n = hook.n;
+  }
+  if (rc == GPE2P_OK) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) rc = cuda_fail(h, e, "profile step");
+  }
+  for (int s = 1; s < nst && rc == GPE2P_OK; ++s) {
+    const cudaEvent_t* se = &ev[(size_t)s * (cap + 1)];
+    for (int i = 0; i < n && i < max_launches; ++i) {
       float t = 0.f;
-      cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+      cudaEventElapsedTime(&t, se[i], se[i + 1]);
       ms[i] += (double)t / nsteps;
     }
   }
-  *nlaunches = hook.n;
+  *nlaunches = n;
   if (names && names_len > 0) {
     std::string all;
-    for (int i = 0; i < hook.n; ++i) { if (i) all += ","; all += nm[i]; }
+    for (int i = 0; i < n; ++i) { if (i) all += ","; all += nm[i]; }
     std::snprintf(names, (size_t)names_len, "%s", all.c_str());
   }
-  for (int i = 0; i <= cap; ++i) cudaEventDestroy(ev[i]);
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
   return rc;
 }
 
@@ -972,8 +994,8 @@ extern "C" int gpe2p_field_ptr(gpe2p_handle h, int which, void** dptr, long long
   if (!h || !dptr) return fail(h, GPE2P_EINVAL, "NULL argument");
   if (h->batch) return fail(h, GPE2P_EINVAL, "a batch handle: use the per-instance calls");
   if (row_pitch) *row_pitch = h->pitch;
-  if (which < 0 || which > 5 || (which == 3 && h->prm.dim == 2)) return fail(h, GPE2P_EINVAL, "bad field index");
-  void* src[6] = {h->Q[h->cur][0], h->Q[h->cur][1], h->Q[h->cur][2], h->Q[h->cur][3], h->phi, h->mu};
+  if (which < 0 || which > 6 || (which == 3 && h->prm.dim == 2)) return fail(h, GPE2P_EINVAL, "bad field index");
+  void* src[7] = {h->Q[h->cur][0], h->Q[h->cur][1], h->Q[h->cur][2], h->Q[h->cur][3], h->phi, h->mu, h->phi_lo};
   *dptr = src[which];
   return GPE2P_OK;
 }
@@ -1068,8 +1090,32 @@ extern "C" int gpe2p_batch_config(gpe2p_handle h, int* tile_x, int* tile_y, int*
   return batch_config(h->batch, tile_x, tile_y, persistent, ms_per_step);
 }
 
+static_assert(GPE2P_LOSE_FLOW_RING == WF_FLOW_RING && GPE2P_LOSE_CH_RING == WF_CH_RING &&
+                  GPE2P_LOSE_MU_RING == WF_MU_RING && GPE2P_LOSE_CH_POINTS == WF_CH_POINTS,
+              "the header's bits are the kernels' bits");
+
 extern "C" int gpe2p_set_fault_injection(gpe2p_handle h, int what, long long value) {
-  if (!h || !h->batch) return fail(h, GPE2P_EINVAL, "fault injection applies to batch handles");
+  if (!h) return fail(nullptr, GPE2P_EINVAL, "handle is NULL");
+  if (!h->batch) {
+    // a single problem: the switch of the 3D kernels' timeout paths
+    if (what == GPE2P_FAULT_LOSE_COPY) {
+      if (h->prm.dim != 3) return fail(h, GPE2P_EINVAL, "GPE2P_FAULT_LOSE_COPY applies to 3D problems");
+      if (value < 0 || value > 15) return fail(h, GPE2P_EINVAL, "GPE2P_FAULT_LOSE_COPY takes bits 1, 2, 4, 8");
+      h->wait_fault = (int)value;
+    } else if (what == GPE2P_FAULT_CLEAR) {
+      h->wait_fault = 0;
+      CK(h, cudaSetDevice(h->dev), "set device");
+      CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream), "clear error word");
+      CK(h, cudaStreamSynchronize(h->stream), "clear error word");
+    } else {
+      return fail(h, GPE2P_EINVAL, "a single problem takes GPE2P_FAULT_LOSE_COPY or GPE2P_FAULT_CLEAR");
+    }
+    for (int c = 0; c < 2; ++c)
+      if (h->gexec[c]) { cudaGraphExecDestroy(h->gexec[c]); h->gexec[c] = nullptr; }
+    h->have_graph = false;
+    return GPE2P_OK;
+  }
+  if (what == GPE2P_FAULT_LOSE_COPY) return fail(h, GPE2P_EINVAL, "GPE2P_FAULT_LOSE_COPY applies to 3D problems");
   std::string why;
   const int rc = batch_fault(h->batch, what, value, why);
   return rc == GPE2P_OK ? rc : fail(h, rc, why);

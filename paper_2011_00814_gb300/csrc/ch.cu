@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
     mbar_init(&pbar[1], 1);
     mbar_init(&pbar[2], 1);
   }
-  R.start(P, maps.m, kbeg, kend, i0, j0);
+  R.start(P, maps.m, kbeg, kend, i0, j0, (P.wait_fault & WF_CH_RING) != 0);
   if (PTS && tid == 0) pissue(kbeg);
   if (UPTS && tid == 0) {
     uissue(kbeg);
@@ -176,7 +176,9 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
   if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, kbeg - 1, false, edge_tile, fix)) { R.fail(err, kbeg - 1); pdrain(kbeg); udrain(kbeg); return; }
   if (!ring_acquire<real, NRAW, RING, CH_K3_SY, CH_NTHR>(R, P, maps.m, kbeg, false, edge_tile, fix)) { R.fail(err, kbeg); pdrain(kbeg); udrain(kbeg); return; }
   bool pfail = false;  // a point-plane wait of this thread gave up
-  if (UPTS && !mbar_wait_bounded(&pbar[uslot(kbeg)], upar(kbeg), WAIT_CYCLES)) {
+  // test switch: the first point-plane wait completes, then reports a timeout
+  const bool plose = (P.wait_fault & WF_CH_POINTS) != 0;
+  if (UPTS && (!mbar_wait_bounded(&pbar[uslot(kbeg)], upar(kbeg), WAIT_CYCLES) || plose)) {
     atomicExch(err, ERR_TMA_TIMEOUT);
     pfail = true;
   }
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(CH_NTHR) ch3d_kernel(const __grid_constant__ M
     if (PTS) {
       // every thread is past plane k - 1: its slot takes plane k + 1
       if (tid == 0) pissue(k + 1);
-      if (!mbar_wait_bounded(&pbar[(k - kbeg) & 1], ((k - kbeg) >> 1) & 1, WAIT_CYCLES)) {
+      if (!mbar_wait_bounded(&pbar[(k - kbeg) & 1], ((k - kbeg) >> 1) & 1, WAIT_CYCLES) || (plose && k == kbeg)) {
         atomicExch(err, ERR_TMA_TIMEOUT);
         pfail = true;
       }
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(MU_NTHR) mu3d_kernel(const __grid_constant__ M
 #pragma unroll
   for (int r = 0; r < MU_CPT; ++r) act[r] = i < nx && ja + r < ny;
   auto fix = [&](int, int ci, int cj, int kk) -> real { return ld_cen(phi, P, ci, cj, kk); };
-  R.start(P, maps.m, kbeg, kend, i0, j0);
+  R.start(P, maps.m, kbeg, kend, i0, j0, (P.wait_fault & WF_MU_RING) != 0);
   if (!ring_acquire<real, 1, RING, MU_K3_SY, MU_NTHR>(R, P, maps.m, kbeg - 1, false, edge_tile, fix)) { R.fail(err, kbeg - 1); return; }
   if (!ring_acquire<real, 1, RING, MU_K3_SY, MU_NTHR>(R, P, maps.m, kbeg, false, edge_tile, fix)) { R.fail(err, kbeg); return; }
   const real* smr = reinterpret_cast<const real*>(smraw);

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(FLOW_NTHR, FLOW_MINB) flow3d_kernel(const __gr
   const int i = i0 + tx, ja = j0 + 2 * ty;
   const bool act[2] = {i < nx && ja < ny, i < nx && ja + 1 < ny};
 
-  R.start(P, maps.m, kbeg, kend, i0, j0);
+  R.start(P, maps.m, kbeg, kend, i0, j0, (P.wait_fault & WF_FLOW_RING) != 0);
 
   // wait for plane kk and overwrite its out-of-domain cells (all cells of a
   // ghost plane or of a tile overhanging the domain end, else the perimeter

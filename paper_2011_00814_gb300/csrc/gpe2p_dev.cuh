@@ -38,7 +38,13 @@ struct KParams {
   // isotropic stencils (Eqs. 1st-der-iso, laplacian-iso)
   real w1, w2, w3;     // weights of the shells |e|^2 = 1, 2, 3 (0 if absent)
   real lap_c, grad_c;  // 6/dx^2 and 3/dx
+  // host-set test switch of the 3D kernels' timeout paths (bits WF_*): the
+  // first wait of the chosen kind completes, then is treated as timed out
+  int wait_fault;
 };
+
+// bits of KParams::wait_fault
+enum { WF_FLOW_RING = 1, WF_CH_RING = 2, WF_MU_RING = 4, WF_CH_POINTS = 8 };
 
 // ---------------------------------------------------------------------------
 // boundary maps (ghost layer of one cell); arguments in [-1, n]

@@ -63,6 +63,7 @@ struct Ring {
   int first, last;  // planes kbeg-1 .. kend (inclusive)
   int i0, j0;
   int issued;       // last plane issued
+  bool lose_first;  // test switch: report the wait for the first plane as timed out
   __device__ __forceinline__ int slot(int kk) const { return (int)((unsigned)(kk - first) & (RING - 1)); }
   __device__ __forceinline__ uint32_t parity(int kk) const { return ((unsigned)(kk - first) >> LOG2) & 1u; }
   __device__ __forceinline__ real* plane(int kk, int f) const { return raw + ((size_t)slot(kk) * NRAW + f) * G::PE; }
@@ -80,8 +81,11 @@ struct Ring {
     issued = kk;
   }
 
+  // lose: the test switch of the timeout path (the wait for the first plane
+  // still completes, so no copy is left in flight, and then reports a timeout)
   __device__ __forceinline__ void start(const KParams<real>& P, const CUtensorMap* maps, int kbeg, int kend,
-                                        int i0_, int j0_) {
+                                        int i0_, int j0_, bool lose = false) {
+    lose_first = lose;
     first = kbeg - 1;
     last = kend;
     i0 = i0_;
@@ -101,7 +105,7 @@ struct Ring {
 
   // all threads: wait for plane kk; false (block-uniform) on timeout
   __device__ __forceinline__ bool wait(int kk) {
-    const bool ok = mbar_wait_bounded(&bar[slot(kk)], parity(kk), WAIT_CYCLES);
+    const bool ok = mbar_wait_bounded(&bar[slot(kk)], parity(kk), WAIT_CYCLES) && !(lose_first && kk == first);
     return !__syncthreads_or(!ok);
   }
 

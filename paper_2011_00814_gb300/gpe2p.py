@@ -23,7 +23,7 @@ OK, EINVAL, EUNSTABLE, ENOMEM, ECUDA, EDIVERGED, ETIMEOUT, ESTATE = range(8)
 STATUS = {0: "OK", 1: "EINVAL", 2: "EUNSTABLE", 3: "ENOMEM", 4: "ECUDA", 5: "EDIVERGED", 6: "ETIMEOUT",
           7: "ESTATE"}
 BC = {"periodic": 0, "noslip": 1, "freeslip": 2}
-FIELD = {"p": 0, "u": 1, "v": 2, "w": 3, "phi": 4, "mu": 5}
+FIELD = {"p": 0, "u": 1, "v": 2, "w": 3, "phi": 4, "mu": 5, "phi_lo": 6}
 
 
 class Params(ctypes.Structure):
@@ -78,8 +78,8 @@ def lib():
         L.gpe2p_field_ptr.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_longlong)]
         L.gpe2p_profile_steps.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                           ctypes.c_char_p, ctypes.c_int]
-        L.gpe2p_diagnostics_noalloc.argtypes = [ctypes.POINTER(Params), vp, vp, vp, vp, vp, ctypes.c_longlong,
-                                                vp, vp]
+        L.gpe2p_diagnostics_noalloc.argtypes = [ctypes.POINTER(Params), vp, vp, vp, vp, vp, vp,
+                                                ctypes.c_longlong, vp, vp]
         L.gpe2p_diagnostics_noalloc.restype = ctypes.c_int
         L.gpe2p_create_batch.argtypes = [ctypes.POINTER(Params), ctypes.c_int, vp, ctypes.POINTER(vp)]
         L.gpe2p_init_instance.argtypes = [vp, ctypes.c_int] + [dp] * 5
@@ -123,6 +123,9 @@ def lib():
         L.gpe2p_set_phi_accumulation.argtypes = [vp, ctypes.c_int, ctypes.c_double]
         L.gpe2p_phi_accumulation.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+        L.gpe2p_fma_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                     vp]
+        L.gpe2p_fma_rate.restype = ctypes.c_int
         L.gpe2p_last_error.argtypes = [vp]
         L.gpe2p_last_error.restype = ctypes.c_char_p
         L.gpe2p_destroy.argtypes = [vp]
@@ -133,6 +136,17 @@ def lib():
             getattr(L, nm).restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+def fma_rate(precision: int, stream: int | None = None) -> dict:
+    """Measured multiply-add rate of the current device (gpe2p_fma_rate):
+    {"flops_per_s": ..., "ms": ...} in the given precision (32 or 64)."""
+    f = ctypes.c_double()
+    ms = ctypes.c_double()
+    rc = lib().gpe2p_fma_rate(int(precision), ctypes.byref(f), ctypes.byref(ms), stream)
+    if rc != OK:
+        raise GPE2PError(rc, "gpe2p_fma_rate failed")
+    return {"flops_per_s": f.value, "ms": ms.value}
 
 
 def params(prm: dict) -> Params:
@@ -296,6 +310,10 @@ class Solver:
         """[sum (f_c - t_c)^2, sum f_c^2] for c = phi, u, v, p (8 floats)."""
         return _tensor_call(self, "distance", 0, tensor, mean, scale)
 
+    def fault(self, what: int, value: int = 0):
+        """Host-side test switch of the kernels' timeout paths (gpe2p_set_fault_injection)."""
+        self._check(lib().gpe2p_set_fault_injection(self.h, int(what), int(value)))
+
     def field_ptr(self, name: str):
         """(device pointer, row pitch in elements) of a field of the current state."""
         p = ctypes.c_void_p()
@@ -321,7 +339,8 @@ class Solver:
             pass
 
 
-FAULT_SKIP_BARRIER, FAULT_WAIT_LIMIT, FAULT_FORCE_PERSISTENT, FAULT_CLEAR = 1, 2, 3, 4
+FAULT_SKIP_BARRIER, FAULT_WAIT_LIMIT, FAULT_FORCE_PERSISTENT, FAULT_CLEAR, FAULT_LOSE_COPY = 1, 2, 3, 4, 5
+LOSE_FLOW_RING, LOSE_CH_RING, LOSE_MU_RING, LOSE_CH_POINTS = 1, 2, 4, 8
 
 
 class Batch:

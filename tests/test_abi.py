@@ -192,7 +192,7 @@ def test_noalloc_diagnostics_validate_on_the_host(lib):
     def call(prm, pitch=None, w=fake, outp=out, p=fake):
         q = gpe2p.params(prm)
         pitch = prm["nx"] if pitch is None else pitch
-        return f(ctypes.byref(q), p, fake, fake, w, fake, pitch, outp, None)
+        return f(ctypes.byref(q), p, fake, fake, w, fake, None, pitch, outp, None)
 
     good3 = dict(inputs.base_params(3, 8, 6, 4), precision=32)
     good2 = dict(inputs.base_params(2, 8, 6), precision=64)
@@ -207,7 +207,7 @@ def test_noalloc_diagnostics_validate_on_the_host(lib):
     assert call(big) == gpe2p.EINVAL
     q = gpe2p.params(good2)
     q.bc[1] = 5
-    assert f(ctypes.byref(q), fake, fake, fake, None, fake, 8, out, None) == gpe2p.EINVAL
+    assert f(ctypes.byref(q), fake, fake, fake, None, fake, None, 8, out, None) == gpe2p.EINVAL
     # well formed: it gets as far as the device lookup
     assert call(good2, w=None) == gpe2p.ECUDA
     assert call(good3) == gpe2p.ECUDA

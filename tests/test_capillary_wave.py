@@ -18,7 +18,7 @@ import oracle
 from oracle import capillary as C
 from paper_2011_00814_gb300 import inputs
 
-from capillary_probe import h_tilde
+from interface_position import h_tilde
 
 pytest.importorskip("scipy")
 

@@ -13,7 +13,7 @@ import oracle
 from oracle import capillary as C
 from paper_2011_00814_gb300 import build, gpe2p, inputs
 
-from capillary_probe import h_tilde
+from interface_position import h_tilde
 
 pytestmark = pytest.mark.gpu
 

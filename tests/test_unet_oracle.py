@@ -91,3 +91,44 @@ def test_adam_first_steps_closed_form():
         w_prev = w
         w, m, v = unet.adam_step(w, g, m, v, t, lr, eps=eps)
         assert np.allclose(w - w_prev, -lr * g / (np.abs(g) + eps), rtol=1e-12, atol=1e-15)
+
+
+def test_round_bf16_matches_the_library_conversion():
+    """The oracle's BF16 rounding (nearest, ties to even, through FP32) agrees
+    with torch's float32 -> bfloat16 conversion, a library routine, on random
+    values, exact halfway cases, signed zeros and powers of two."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    x = np.concatenate([rng.normal(size=4000) * 10.0 ** rng.integers(-8, 8, size=4000),
+                        [0.0, -0.0, 1.0, -2.0, 2.0 ** -20, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8,
+                         -(1.0 + 2.0 ** -8), 1.0 + 2.0 ** -8 + 2.0 ** -20]])
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    got = unet.round_bf16(x)
+    assert np.array_equal(got, ref)
+    # ties to even: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7
+    assert unet.round_bf16(np.array([1.0 + 2.0 ** -8]))[0] == 1.0
+    assert unet.round_bf16(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
+
+
+def test_bf16_mode_rounds_only_what_is_stored():
+    """With bf16=True every saved tensor is a BF16 value, and the output and
+    gradient stay within the BF16 rounding of the FP64 network (about 2^-9 per
+    stored tensor over the few layers of this net), so the mode rounds where
+    values are stored and nowhere else."""
+    L, ch, IN, OUT = 2, [16, 32], 3, 2
+    rng = np.random.default_rng(12)
+    convs, _ = unet.layer_shapes(L, ch, IN, OUT)
+    n = sum(co * t * ci + co for _, ci, co, t in convs) + OUT * ch[0] + OUT
+    p = unet.round_bf16(rng.normal(size=n) * 0.2)
+    x = rng.normal(size=(2, 8, 8, IN))
+    t = rng.normal(size=(2, 8, 8, OUT))
+    y64 = unet.forward(p, x, L, ch, IN, OUT)
+    y16, saved = unet.forward(p, x, L, ch, IN, OUT, keep=True, bf16=True)
+    for k, v in saved.items():
+        assert np.array_equal(unet.round_bf16(v), v), k
+    rel = np.linalg.norm(y16 - y64) / np.linalg.norm(y64)
+    assert 1e-5 < rel < 2e-2, rel
+    _, g64 = unet.loss_and_gradient(p, x, t, L, ch, IN, OUT)
+    _, g16 = unet.loss_and_gradient(p, x, t, L, ch, IN, OUT, bf16=True)
+    relg = np.linalg.norm(g16 - g64) / np.linalg.norm(g64)
+    assert 1e-5 < relg < 5e-2, relg
