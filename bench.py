@@ -329,28 +329,34 @@ SURROGATE_WEIGHTS = os.path.join(ROOT, "paper_2011_00814_gb300", "data", "unet_t
 def measure_surrogate(cases=(0, 1, 2, 3), calls=64):
     """The learned surrogate on held-out two-drop problems (256 x 256, K = 64
     steps per call, 64 calls = 4096 steps): time to solution of the
-    controller (network calls with a solver check every 4th call) against the
-    plain FP32 solver on the same stream, the final phase errors against the
+    controller (network calls with a solver check every 4th call: phi L2 of
+    the call <= 2e-2 and its interface displacement within the tolerance
+    calibrated on other held-out problems) against the plain
+    FP32 solver on the same stream, the final phase errors against the
     solver, the same with the network replaced by persistence (the method
-    without the network), the network with a stricter check tolerance, and
-    the network's forward throughput against the BF16 tensor peak."""
+    without the network), and the network's forward throughput against the
+    BF16 tensor peak."""
     import torch
     from paper_2011_00814_gb300 import surrogate as S
     if not os.path.exists(SURROGATE_WEIGHTS):
         return {"unavailable": "no trained weights file"}
     sur = S.Surrogate.load(SURROGATE_WEIGHTS, max_batch=8)
+    cal = sur.calibration or {}
     out = {"workload": "two drops, periodic 256x256, FP32, K=64 steps per call, 64 calls (4096 steps), "
-                       "check every 4th call at phi L2 <= 2e-2",
+                       "check every 4th call",
+           "check_tol": sur.check_tol,
+           "check_tol_disp_cells": sur.check_tol_disp,
+           "check_tol_source": (f"phi L2 tolerance {sur.check_tol} as configured; interface-displacement "
+                                f"tolerance calibrated on {cal.get('cases')} held-out problems (seeds "
+                                f"{cal.get('seeds')}), margin {cal.get('margin')}") if cal else "defaults",
+           "bars": {"phi_l2": S.BAR_PHI_L2, "interface_cells": S.BAR_INTERFACE},
            "cases": []}
-    strict = 1e-3
     for c in cases:
         prm, f = inputs.two_drops(50000 + c)
         row = {"case": c, "r_rho": prm["r_rho"]}
-        for key, pers, tol in (("network", False, 2e-2), ("persistence", True, 2e-2),
-                               ("network_strict", False, strict)):
-            r = S.compare_to_solver(sur, prm, f, calls=calls, repeats=2, persistence=pers, tol=tol)
+        for key, pers in (("network", False), ("persistence", True)):
+            r = S.compare_to_solver(sur, prm, f, calls=calls, repeats=2, persistence=pers)
             r["stats"].pop("check_l2", None)
-            r["check_tol"] = tol
             row[key] = r
         out["cases"].append(row)
 
@@ -361,40 +367,37 @@ def measure_surrogate(cases=(0, 1, 2, 3), calls=64):
                 "interface_max_cells": max(r["interface_max"] for r in rs),
                 "interface_mean_cells": max(r["interface_mean"] for r in rs),
                 "phi_l2_of_change": statistics.mean(r["phi_l2_of_change"] for r in rs),
-                "check_failures": sum(r["stats"]["failures"] for r in rs)}
+                "check_failures": sum(r["stats"]["failures"] for r in rs),
+                "meets_bars_every_case": all(r["meets_bars"] for r in rs)}
     out["network"] = summary("network")
     out["persistence"] = summary("persistence")
-    out["network_strict"] = dict(summary("network_strict"), check_tol=strict)
-    # the speedup of the configuration that meets both tolerances (phi L2 <= 2e-2 and the
-    # interface within one cell) on every case
-    ok = [k for k in ("network", "network_strict")
-          if out[k]["phi_l2_max"] <= 2e-2 and out[k]["interface_max_cells"] <= 1.0]
-    out["speedup_at_tolerance"] = max((out[k]["speedup"] for k in ok), default=None)
-    out["configuration_at_tolerance"] = max(ok, key=lambda k: out[k]["speedup"]) if ok else None
-    # network forward, batch 8, inference (BF16 tensor cores)
-    B = 8
-    x = torch.randn(B, sur.n, sur.n, S.NCH, device="cuda")
-    y = torch.empty_like(x)
-    for _ in range(3):
-        sur.forward(x, y, B)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n = 20
-    e0.record(sur.torch_stream)
-    for _ in range(n):
-        sur.forward(x, y, B)
-    e1.record(sur.torch_stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / n
-    tf = sur.flops(B) / (ms / 1e3) / 1e12
+    # the speedup of the default (calibrated) configuration, if it meets both bars on every case
+    out["speedup_at_tolerance"] = out["network"]["speedup"] if out["network"]["meets_bars_every_case"] else None
+    # network forward, batch 8 and 1, inference (BF16 tensor cores)
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             peak, kind = float(json.load(fh)["bf16_tflops"]), "measured"
     except Exception:
         peak, kind = 1900.0, "fallback"
-    out["forward"] = {"batch": B, "ms": ms, "gflop": sur.flops(B) / 1e9,
-                      "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
-                                   "frac": tf / peak, "peak_kind": kind}}
+    for B in (8, 1):
+        x = torch.randn(B, sur.n, sur.n, S.NCH, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            sur.forward(x, y, B)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = 20
+        e0.record(sur.torch_stream)
+        for _ in range(n):
+            sur.forward(x, y, B)
+        e1.record(sur.torch_stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        tf = sur.flops(B) / (ms / 1e3) / 1e12
+        out["forward" if B == 8 else "forward_batch1"] = {
+            "batch": B, "ms": ms, "gflop": sur.flops(B) / 1e9,
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                         "peak_kind": kind}}
     sur.close()
     return out
 

@@ -357,6 +357,21 @@ int gpe2p_unpack_state(gpe2p_handle h, int inst, const float *tensor, int nch, c
 int gpe2p_state_distance(gpe2p_handle h, int inst, const float *tensor, int nch, const float *mean,
                          const float *scale, double *out);
 
+/* The displacement of the phi = 0 interface, in cells, between the state's
+ * phi (the reference phi_b; instance inst of a batch) and the phi channel of
+ * a network tensor, phi_a = mean[0] + scale[0] tensor[j][i][0]:
+ * out[0] = max over the cells with |phi_b| < 1/2 of |phi_a - phi_b| /
+ * |grad phi_b|, out[1] = sum |phi_a - phi_b| / sum |grad phi_b| over all
+ * cells (for the equilibrium profile tanh(2d/W) the mean normal
+ * displacement), out[2] = the number of cells with |phi_b| < 1/2 (host
+ * array of 3 doubles).  grad phi_b by central differences in cell units, with
+ * the boundaries' ghost rules.  The paper has no counterpart: the learned
+ * surrogate's check compares one network call with the solver by it.  FP64
+ * sums in a fixed order (deterministic); shares the scratch of
+ * gpe2p_state_distance.  Synchronises. */
+int gpe2p_interface_distance(gpe2p_handle h, int inst, const float *tensor, int nch, const float *mean,
+                             const float *scale, double *out);
+
 /* Largest number of cells gpe2p_diagnostics_noalloc accepts. */
 #define GPE2P_NOALLOC_MAX_CELLS 67108864LL
 

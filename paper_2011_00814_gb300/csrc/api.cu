@@ -1144,7 +1144,7 @@ static int state_of(gpe2p_ctx* h, int inst, KParams<real>* P, real* f[5], int* i
   return GPE2P_OK;
 }
 
-enum PackOp { OP_PACK, OP_UNPACK, OP_DISTANCE };
+enum PackOp { OP_PACK, OP_UNPACK, OP_DISTANCE, OP_IFACE };
 
 template <typename real>
 static cudaError_t pack_op(gpe2p_ctx* h, int inst, PackOp op, float* t, int nch, const float* mean,
@@ -1157,6 +1157,8 @@ static cudaError_t pack_op(gpe2p_ctx* h, int inst, PackOp op, float* t, int nch,
   if (*rc != GPE2P_OK) return cudaSuccess;
   if (op == OP_PACK) return launch_pack<real>(P, f, t, nch, mean, scale, s);
   if (op == OP_DISTANCE) return launch_distance<real>(P, f, t, nch, mean, scale, h->d_dist, h->d_dist + 8 * kDistanceBlocks, s);
+  if (op == OP_IFACE)
+    return launch_interface_distance<real>(P, f[0], t, nch, mean, scale, h->d_dist, h->d_dist + 8 * kDistanceBlocks, s);
   cudaError_t e = launch_unpack<real>(P, f, t, nch, mean, scale, s);
   if (e != cudaSuccess) return e;
   return launch_mu<real, 2>(P, f[0], f[4], iso, 1, s, nullptr, err);
@@ -1176,7 +1178,7 @@ static int pack_any(gpe2p_handle h, int inst, PackOp op, float* t, int nch, cons
   const int esize = h->batch ? batch_esize(h->batch) : h->esize;
   cudaStream_t s = h->batch ? batch_stream(h->batch) : h->stream;
   CK(h, cudaSetDevice(dev), "set device");
-  if (op == OP_DISTANCE && !h->d_dist) {
+  if ((op == OP_DISTANCE || op == OP_IFACE) && !h->d_dist) {
     CK(h, cudaMalloc((void**)&h->d_dist, (8 * kDistanceBlocks + 8) * sizeof(double)), "distance scratch");
     CK(h, cudaMallocHost((void**)&h->h_dist, 8 * sizeof(double)), "distance scratch");
   }
@@ -1184,17 +1186,20 @@ static int pack_any(gpe2p_handle h, int inst, PackOp op, float* t, int nch, cons
   cudaError_t e = esize == 4 ? pack_op<float>(h, inst, op, t, nch, mean, scale, s, &rc)
                              : pack_op<double>(h, inst, op, t, nch, mean, scale, s, &rc);
   if (rc != GPE2P_OK) return fail(h, rc, "instance index out of range");
-  if (e != cudaSuccess) return cuda_fail(h, e, op == OP_PACK ? "pack" : op == OP_UNPACK ? "unpack" : "distance");
+  if (e != cudaSuccess)
+    return cuda_fail(h, e, op == OP_PACK ? "pack" : op == OP_UNPACK ? "unpack" : op == OP_IFACE ? "interface distance"
+                                                                                              : "distance");
   if (op == OP_UNPACK) {
     if (h->batch) batch_mark_initialized(h->batch);
     else h->initialized = true;
     if (!h->batch && h->phi_lo) CK(h, cudaMemsetAsync(h->phi_lo, 0, field_bytes(h), s), "unpack");
   }
-  if (op == OP_DISTANCE) {
-    CK(h, cudaMemcpyAsync(h->h_dist, h->d_dist + 8 * kDistanceBlocks, 8 * sizeof(double), cudaMemcpyDeviceToHost, s),
+  if (op == OP_DISTANCE || op == OP_IFACE) {
+    const int nout = op == OP_DISTANCE ? 8 : 3;
+    CK(h, cudaMemcpyAsync(h->h_dist, h->d_dist + 8 * kDistanceBlocks, nout * sizeof(double), cudaMemcpyDeviceToHost, s),
        "distance");
     CK(h, cudaStreamSynchronize(s), "distance");
-    std::memcpy(dist, h->h_dist, 8 * sizeof(double));
+    std::memcpy(dist, h->h_dist, nout * sizeof(double));
   }
   return GPE2P_OK;
 }
@@ -1213,4 +1218,10 @@ extern "C" int gpe2p_state_distance(gpe2p_handle h, int inst, const float* tenso
                                     const float* scale, double* out) {
   if (!out) return fail(h, GPE2P_EINVAL, "NULL argument");
   return pack_any(h, inst, OP_DISTANCE, const_cast<float*>(tensor), nch, mean, scale, out);
+}
+
+extern "C" int gpe2p_interface_distance(gpe2p_handle h, int inst, const float* tensor, int nch, const float* mean,
+                                        const float* scale, double* out) {
+  if (!out) return fail(h, GPE2P_EINVAL, "NULL argument");
+  return pack_any(h, inst, OP_IFACE, const_cast<float*>(tensor), nch, mean, scale, out);
 }

@@ -150,6 +150,12 @@ cudaError_t launch_pack(const KParams<real>& P, const real* const f[4], float* o
 template <typename real>
 cudaError_t launch_unpack(const KParams<real>& P, real* const f[4], const float* in, int nch, const float* mean,
                           const float* scale, cudaStream_t s);
+// the interface displacement between the state's phi and the tensor's phi
+// channel (see pack.cu); part: kDistanceBlocks * 4 doubles; out: 3 doubles (device)
+template <typename real>
+cudaError_t launch_interface_distance(const KParams<real>& P, const real* phi, const float* in, int nch,
+                                      const float* mean, const float* scale, double* part, double* out,
+                                      cudaStream_t s);
 // part: kDistanceBlocks * 8 doubles; out: 8 doubles (device)
 template <typename real>
 cudaError_t launch_distance(const KParams<real>& P, const real* const f[4], const float* in, int nch, const float* mean,

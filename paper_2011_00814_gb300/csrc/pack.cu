@@ -92,6 +92,69 @@ __global__ void distance_final_kernel(const double* __restrict__ part, int nblk,
   }
 }
 
+// per block: the displacement of the phi = 0 interface between the state's
+// phi (the reference phi_b) and the tensor's phi channel (phi_a), in cells:
+// sum |phi_a - phi_b|, sum |grad phi_b| (central differences with the
+// boundaries' ghost rules), and over the cells with |phi_b| < 1/2 the max of
+// |phi_a - phi_b| / |grad phi_b| and their count (FP64)
+template <typename real>
+__global__ void iface_kernel(const KParams<real> P, const real* __restrict__ phi, const float* __restrict__ in,
+                             int nch, const Affine A, double* __restrict__ part) {
+  double sd = 0.0, sg = 0.0, mx = 0.0, cnt = 0.0;
+  const long long n = (long long)P.n[0] * P.n[1];
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n; id += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(id % P.n[0]), j = (int)(id / P.n[0]);
+    const double fb = (double)phi[lin(P, i, j, 0)];
+    const double fa = (double)A.mean[0] + (double)A.scale[0] * (double)in[id * nch];
+    const double gx = 0.5 * ((double)ld_cen(phi, P, i + 1, j, 0) - (double)ld_cen(phi, P, i - 1, j, 0));
+    const double gy = 0.5 * ((double)ld_cen(phi, P, i, j + 1, 0) - (double)ld_cen(phi, P, i, j - 1, 0));
+    const double g = sqrt(gx * gx + gy * gy);
+    const double d = fabs(fa - fb);
+    sd += d;
+    sg += g;
+    if (fabs(fb) < 0.5) {
+      mx = fmax(mx, d / fmax(g, 1e-12));
+      cnt += 1.0;
+    }
+  }
+  __shared__ double red[4][8];  // [value][warp]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double v[4] = {sd, sg, mx, cnt};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, x, o);
+      x = k == 2 ? fmax(x, y) : x + y;
+    }
+    if (lane == 0) red[k][w] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double x = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k)
+      x = threadIdx.x == 2 ? fmax(x, red[threadIdx.x][k]) : x + red[threadIdx.x][k];
+    part[blockIdx.x * 4 + threadIdx.x] = x;
+  }
+}
+
+// fixed-order combination of the block partials: out[0] max displacement,
+// out[1] mean displacement, out[2] band cells
+__global__ void iface_final_kernel(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+  if (threadIdx.x == 0) {
+    double sd = 0.0, sg = 0.0, mx = 0.0, cnt = 0.0;
+    for (int b = 0; b < nblk; ++b) {
+      sd += part[b * 4 + 0];
+      sg += part[b * 4 + 1];
+      mx = fmax(mx, part[b * 4 + 2]);
+      cnt += part[b * 4 + 3];
+    }
+    out[0] = mx;
+    out[1] = sd / fmax(sg, 1e-300);
+    out[2] = cnt;
+  }
+}
+
 static Affine affine(const float* mean, const float* scale, int nch) {
   Affine A;
   for (int c = 0; c < 5; ++c) {
@@ -133,13 +196,26 @@ cudaError_t launch_distance(const KParams<real>& P, const real* const f[4], cons
   return cudaGetLastError();
 }
 
+template <typename real>
+cudaError_t launch_interface_distance(const KParams<real>& P, const real* phi, const float* in, int nch,
+                                      const float* mean, const float* scale, double* part, double* out,
+                                      cudaStream_t s) {
+  iface_kernel<real><<<kDistanceBlocks, 256, 0, s>>>(P, phi, in, nch, affine(mean, scale, nch), part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  iface_final_kernel<<<1, 32, 0, s>>>(part, kDistanceBlocks, out);
+  return cudaGetLastError();
+}
+
 #define GPE2P_PACK_INST(real)                                                                                       \
   template cudaError_t launch_pack<real>(const KParams<real>&, const real* const[4], float*, int, const float*,     \
                                          const float*, cudaStream_t);                                               \
   template cudaError_t launch_unpack<real>(const KParams<real>&, real* const[4], const float*, int, const float*,   \
                                            const float*, cudaStream_t);                                             \
   template cudaError_t launch_distance<real>(const KParams<real>&, const real* const[4], const float*, int,         \
-                                             const float*, const float*, double*, double*, cudaStream_t);
+                                             const float*, const float*, double*, double*, cudaStream_t);   \
+  template cudaError_t launch_interface_distance<real>(const KParams<real>&, const real*, const float*, int,       \
+                                                       const float*, const float*, double*, double*, cudaStream_t);
 GPE2P_PACK_INST(float)
 GPE2P_PACK_INST(double)
 

@@ -120,6 +120,9 @@ def lib():
         L.gpe2p_state_distance.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, fp, fp,
                                            ctypes.POINTER(ctypes.c_double)]
         L.gpe2p_state_distance.restype = ctypes.c_int
+        L.gpe2p_interface_distance.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, fp, fp,
+                                               ctypes.POINTER(ctypes.c_double)]
+        L.gpe2p_interface_distance.restype = ctypes.c_int
         L.gpe2p_set_phi_accumulation.argtypes = [vp, ctypes.c_int, ctypes.c_double]
         L.gpe2p_phi_accumulation.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
@@ -205,6 +208,10 @@ def _tensor_call(obj, op, inst, tensor, mean, scale):
         obj._check(L.gpe2p_pack_state(obj.h, int(inst), ctypes.c_void_p(ptr), nch, m, s))
     elif op == "unpack":
         obj._check(L.gpe2p_unpack_state(obj.h, int(inst), ctypes.c_void_p(ptr), nch, m, s))
+    elif op == "interface":
+        out = (ctypes.c_double * 3)()
+        obj._check(L.gpe2p_interface_distance(obj.h, int(inst), ctypes.c_void_p(ptr), nch, m, s, out))
+        return list(out)
     else:
         out = (ctypes.c_double * 8)()
         obj._check(L.gpe2p_state_distance(obj.h, int(inst), ctypes.c_void_p(ptr), nch, m, s, out))
@@ -310,6 +317,11 @@ class Solver:
         """[sum (f_c - t_c)^2, sum f_c^2] for c = phi, u, v, p (8 floats)."""
         return _tensor_call(self, "distance", 0, tensor, mean, scale)
 
+    def interface_distance(self, tensor, mean=None, scale=None):
+        """[max, mean] displacement in cells of the tensor's phi = 0 interface
+        from the state's, and the cells of the interface band."""
+        return _tensor_call(self, "interface", 0, tensor, mean, scale)
+
     def fault(self, what: int, value: int = 0):
         """Host-side test switch of the kernels' timeout paths (gpe2p_set_fault_injection)."""
         self._check(lib().gpe2p_set_fault_injection(self.h, int(what), int(value)))
@@ -400,6 +412,9 @@ class Batch:
 
     def distance(self, k: int, tensor, mean=None, scale=None):
         return _tensor_call(self, "distance", k, tensor, mean, scale)
+
+    def interface_distance(self, k: int, tensor, mean=None, scale=None):
+        return _tensor_call(self, "interface", k, tensor, mean, scale)
 
     def config(self) -> dict:
         tx, ty, pers = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

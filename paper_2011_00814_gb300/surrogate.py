@@ -10,12 +10,25 @@ which also recomputes mu from phi.  Every step of that path runs in the
 library's kernels; this module only sequences the calls.
 
 The controller keeps the solver as the referee: every ``check_every``-th call
-also runs the K solver steps from the same start and measures the relative
-phi L2 distance between the two results (``gpe2p_state_distance``).  The
-solver's result is kept.  If the distance exceeds ``tol``, the window of calls
-since the last check is discarded, the state at that check is restored and
-the window is recomputed by the solver, and the next ``cooldown`` windows run
-on the solver alone.  Training data are trajectories of the solver itself
+also runs the K solver steps from the same start and measures two errors of
+that one network call against the solver's result: the relative phi L2
+distance (``gpe2p_state_distance``), held to ``tol`` = 2e-2, and the largest
+local displacement of the phi = 0 interface in cells
+(``gpe2p_interface_distance``), held to ``tol_disp``.  The solver's result is
+kept.  If either error exceeds its tolerance, the window of calls since the
+last check is discarded, the state at that check is restored and the window
+is recomputed by the solver, and the next ``cooldown`` windows run on the
+solver alone.
+
+The one-call errors of a run accumulate into its error at the end.  A
+network that moves a piece of the interface by a fraction of a cell per call,
+in the same direction call after call (the neck of two coalescing drops),
+leaves the global phi L2 error of each call far below 2e-2 while the
+interface ends cells away from the solver's; the local displacement sees it.
+``calibrate_tolerance`` finds the largest ``tol_disp`` at which held-out
+problems end within both end-of-run bars (phi L2 <= 2e-2, interface within
+one cell of the solver's), and a saved calibration next to the weights makes
+it the default.  Training data are trajectories of the solver itself
 (the batched engine), and training runs on the library's forward, backward
 and Adam kernels.  The paper has no learned component; this is an extension
 around its method.
@@ -23,7 +36,9 @@ around its method.
 from __future__ import annotations
 
 import dataclasses
+import json
 import math
+import os
 import time
 
 import numpy as np
@@ -33,6 +48,12 @@ from . import gpe2p, inputs
 NCH = 5                    # phi, u, v, p, rho(phi)/rho_L
 LEVELS = 4
 CHANNELS = (32, 64, 128, 256)
+# the end-of-run bars of the surrogate (phi L2 against the solver, interface
+# displacement in cells) and the check tolerance used when no calibration is saved
+BAR_PHI_L2 = 2e-2
+BAR_INTERFACE = 1.0
+DEFAULT_TOL = 2e-2
+DEFAULT_TOL_DISP = 0.05  # cells per call, used when no calibration is saved
 
 
 def _torch():
@@ -55,6 +76,10 @@ class Surrogate:
         self.torch_stream = torch.cuda.Stream()
         self.stream = self.torch_stream.cuda_stream
         self.net = gpe2p.Net(levels, list(channels), NCH, NCH, n, n, max_batch, seed=seed, stream=self.stream)
+        # the controller's default check tolerance (set from a saved calibration by load())
+        self.check_tol = DEFAULT_TOL
+        self.check_tol_disp = DEFAULT_TOL_DISP
+        self.calibration = None
         self.in_mean = np.zeros(NCH, np.float32)
         self.in_scale = np.ones(NCH, np.float32)
         self.out_scale = np.ones(NCH, np.float32)
@@ -111,15 +136,31 @@ class Surrogate:
 
     @classmethod
     def load(cls, path: str, max_batch: int = 8) -> "Surrogate":
+        """Weights and normalisation from ``path``; the check tolerance from the
+        calibration file beside it (``calibration_path``), if there is one."""
         z = np.load(path)
         n, K, levels, *ch = [int(v) for v in z["shape"]]
         s = cls(n=n, K=K, levels=levels, channels=ch, max_batch=max_batch)
         s.net.set_params(z["params"])
         s.set_stats(z["in_mean"], z["in_scale"], z["out_scale"])
+        cp = calibration_path(path)
+        if os.path.exists(cp):
+            with open(cp) as fh:
+                s.calibration = json.load(fh)
+            if s.calibration.get("tol") is not None:
+                s.check_tol = float(s.calibration["tol"])
+            if s.calibration.get("tol_disp") is not None:
+                s.check_tol_disp = float(s.calibration["tol_disp"])
         return s
 
     def close(self):
         self.net.close()
+
+
+def calibration_path(weights_path: str) -> str:
+    """The calibration file that belongs to a weights file."""
+    root, _ = os.path.splitext(weights_path)
+    return root + ".calibration.json"
 
 
 # ---------------------------------------------------------------------------
@@ -236,20 +277,25 @@ class Stats:
     checks: int = 0
     failures: int = 0
     max_check_l2: float = 0.0
+    max_check_disp: float = 0.0
     check_l2: list = dataclasses.field(default_factory=list)
+    check_disp: list = dataclasses.field(default_factory=list)
 
 
 class Controller:
     """Advances one 2D problem (a ``gpe2p.Solver`` of the surrogate's size) by
     K steps per call, with the network and the solver's periodic check."""
 
-    def __init__(self, sur: Surrogate, solver: gpe2p.Solver, check_every: int = 4, tol: float = 2e-2,
-                 cooldown: int = 1, persistence: bool = False):
+    def __init__(self, sur: Surrogate, solver: gpe2p.Solver, check_every: int = 4, tol: float | None = None,
+                 cooldown: int = 1, persistence: bool = False, tol_disp: float | None = None):
         torch = _torch()
         self.sur, self.s = sur, solver
         # persistence: the baseline without the network (the state is left unchanged by a call)
         self.persistence = bool(persistence)
+        tol = sur.check_tol if tol is None else tol
+        tol_disp = sur.check_tol_disp if tol_disp is None else tol_disp
         self.check_every, self.tol, self.cooldown = int(check_every), float(tol), int(cooldown)
+        self.tol_disp = float(tol_disp)
         n = sur.n
         self.x = torch.empty((1, n, n, NCH), dtype=torch.float32, device="cuda")
         self.y = torch.empty_like(self.x)
@@ -291,9 +337,12 @@ class Controller:
         st.checks += 1
         d = self.s.distance(self.y[0])
         e = math.sqrt(d[0] / max(d[1], 1e-300))
+        disp = self.s.interface_distance(self.y[0])[0]
         st.check_l2.append(e)
+        st.check_disp.append(disp)
         st.max_check_l2 = max(st.max_check_l2, e)
-        if not (e <= self.tol):
+        st.max_check_disp = max(st.max_check_disp, disp)
+        if not (e <= self.tol and disp <= self.tol_disp):
             st.failures += 1
             self.s.unpack(self.ckpt[0])                      # back to the last verified state
             self.s.advance(K * self.check_every)
@@ -371,12 +420,15 @@ def interface_error(phi, phi_ref):
     return mean, mx
 
 
-def compare_to_solver(sur: Surrogate, prm, fields, calls: int, check_every: int = 4, tol: float = 2e-2,
-                      repeats: int = 1, persistence: bool = False):
+def compare_to_solver(sur: Surrogate, prm, fields, calls: int, check_every: int = 4, tol: float | None = None,
+                      repeats: int = 1, persistence: bool = False, tol_disp: float | None = None):
     """Time-to-solution of the controller against the plain solver over
     ``calls`` * K steps from the same initial state, and the final errors.
     Both run on the surrogate's stream; times are CUDA-event times of the
-    whole run on that stream (best of ``repeats``), host waits included."""
+    whole run on that stream (best of ``repeats``), host waits included.
+    ``tol``, ``tol_disp``: the check tolerances (None: the surrogate's defaults)."""
+    tol = sur.check_tol if tol is None else tol
+    tol_disp = sur.check_tol_disp if tol_disp is None else tol_disp
     torch = _torch()
     stream = sur.torch_stream
     K = sur.K
@@ -410,7 +462,7 @@ def compare_to_solver(sur: Surrogate, prm, fields, calls: int, check_every: int 
         best, stats = float("inf"), None
         for _ in range(repeats):
             s.init_fields(fields)
-            c = Controller(sur, s, check_every=check_every, tol=tol, persistence=persistence)
+            c = Controller(sur, s, check_every=check_every, tol=tol, persistence=persistence, tol_disp=tol_disp)
             ms, st = timed(lambda: c.run(calls))
             if ms < best:
                 best, stats = ms, st
@@ -425,4 +477,38 @@ def compare_to_solver(sur: Surrogate, prm, fields, calls: int, check_every: int 
     res["interface_mean"], res["interface_max_local"] = interface_error(phi, phi_ref)
     res["interface_max"] = interface_hausdorff(phi, phi_ref)
     res["stats"] = dataclasses.asdict(stats)
+    res["check_tol"] = tol
+    res["check_tol_disp"] = tol_disp
+    res["meets_bars"] = bool(res["phi_l2"] <= BAR_PHI_L2 and res["interface_max"] <= BAR_INTERFACE)
     return res
+
+
+def calibrate_tolerance(sur: Surrogate, cases, calls: int, candidates=(0.3, 0.2, 0.15, 0.1, 0.08, 0.06, 0.04, 0.03,
+                                                                        0.02),
+                        tol: float = DEFAULT_TOL, margin: float = 0.8, repeats: int = 1):
+    """The largest per-call interface-displacement tolerance ``tol_disp``
+    (cells; the phi L2 tolerance stays ``tol``) at which every calibration
+    case (held-out (params, fields) pairs, not used in training nor in the
+    evaluation) ends a run of ``calls`` calls within ``margin`` times both
+    bars: phi L2 <= margin BAR_PHI_L2 and the Hausdorff distance of the
+    interfaces <= margin BAR_INTERFACE cells.  The margin leaves room for
+    problems outside the calibration set.  Returns a dict with the chosen
+    tolerances (tol_disp None if no candidate qualifies) and every candidate's
+    worst errors, mean speedup and share of calls the network took."""
+    rows = []
+    chosen = None
+    for td in sorted(candidates, reverse=True):
+        rs = [compare_to_solver(sur, prm, f, calls=calls, tol=tol, tol_disp=td, repeats=repeats) for prm, f in cases]
+        row = {"tol_disp": td, "phi_l2_max": max(r["phi_l2"] for r in rs),
+               "interface_max_cells": max(r["interface_max"] for r in rs),
+               "speedup_mean": float(np.mean([r["speedup"] for r in rs])),
+               "network_share": float(np.mean([r["stats"]["net_calls"] / max(r["stats"]["calls"], 1) for r in rs])),
+               "check_failures": sum(r["stats"]["failures"] for r in rs)}
+        row["qualifies"] = bool(row["phi_l2_max"] <= margin * BAR_PHI_L2 and
+                                row["interface_max_cells"] <= margin * BAR_INTERFACE)
+        rows.append(row)
+        if row["qualifies"]:
+            chosen = td
+            break
+    return {"tol": tol, "tol_disp": chosen, "margin": margin, "calls": calls, "cases": len(cases),
+            "bars": {"phi_l2": BAR_PHI_L2, "interface_cells": BAR_INTERFACE}, "candidates": rows}

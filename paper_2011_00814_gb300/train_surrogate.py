@@ -8,11 +8,20 @@ batched FP32 solver, one snapshot every K steps -> normalisation statistics
 one-call phase-field error of the network and of the persistence map, and
 the controller's time-to-solution against the plain solver over ``calls``
 calls.  Writes the weights (FP32, with the normalisation) and a JSON summary.
+
+The controller's check tolerance is then calibrated on ``--calibrate``
+further held-out problems (seeds after the evaluated ones) and written next
+to the weights (``surrogate.calibration_path``).  With ``--weights`` an
+existing weights file is calibrated without training:
+
+    python -m paper_2011_00814_gb300.train_surrogate \
+        --weights paper_2011_00814_gb300/data/unet_two_drops_256.npz --calibrate 8
 """
 from __future__ import annotations
 
 import argparse
 import json
+import os
 import time
 
 import numpy as np
@@ -36,14 +45,25 @@ def main(argv=None):
     ap.add_argument("--calls", type=int, default=64, help="controller calls of the time-to-solution runs")
     ap.add_argument("--compare", type=int, default=2, help="held-out cases in the time-to-solution runs")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--out", type=str, required=True)
+    ap.add_argument("--out", type=str, default="")
     ap.add_argument("--json", type=str, default="")
+    ap.add_argument("--weights", type=str, default="", help="calibrate these weights instead of training")
+    ap.add_argument("--calibrate", type=int, default=8, help="held-out problems of the tolerance calibration")
+    ap.add_argument("--skip-eval", type=int, default=4,
+                    help="held-out problems kept for evaluation (the benchmark's), skipped by the calibration")
     a = ap.parse_args(argv)
     import torch
     build.build()
     gpe2p.lib()
     chans = tuple(int(c) for c in a.channels.split(","))
     summary = {"args": vars(a)}
+    if a.weights:
+        sur = S.Surrogate.load(a.weights, max_batch=a.batch)
+        calibrate(sur, a, a.weights)
+        sur.close()
+        return
+    if not a.out:
+        ap.error("--out is required when training")
 
     train_cases = [inputs.two_drops(a.seed * 100000 + s, n=a.n) for s in range(a.train)]
     test_cases = [inputs.two_drops(a.seed * 100000 + 50000 + s, n=a.n) for s in range(a.test)]
@@ -97,10 +117,25 @@ def main(argv=None):
     summary["time_to_solution"] = runs
     sur.save(a.out, meta={"K": a.K, "train": a.train, "snapshots": a.snapshots, "steps": a.steps,
                           "seed": a.seed})
+    summary["calibration"] = calibrate(sur, a, a.out)
     if a.json:
         with open(a.json, "w") as fh:
             json.dump(summary, fh, indent=1)
     sur.close()
+
+
+def calibrate(sur, a, weights_path):
+    """Calibrate the check tolerance on held-out problems and write it beside the weights."""
+    n = sur.n
+    first = a.seed * 100000 + 50000 + a.skip_eval
+    cases = [inputs.two_drops(first + c, n=n) for c in range(a.calibrate)]
+    cal = S.calibrate_tolerance(sur, cases, calls=a.calls)
+    cal["seeds"] = [first, first + a.calibrate - 1]
+    cal["weights"] = os.path.basename(weights_path)
+    with open(S.calibration_path(weights_path), "w") as fh:
+        json.dump(cal, fh, indent=1)
+    print(json.dumps(cal), flush=True)
+    return cal
 
 
 if __name__ == "__main__":
