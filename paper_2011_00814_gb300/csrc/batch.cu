@@ -65,11 +65,16 @@ template <typename real, int TXv, int TYv>
 __device__ __forceinline__ void uh2d_tile(const KParams<real>& P, const real* u0, const real* v0, const real* u1,
                                           const real* v1, real* uh0, real* uh1, int i0, int j0) {
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int i = i0 + tid % TXv, j = j0 + tid / TXv;
-  if (i < P.n[0] && j < P.n[1]) {
-    const long long id = lin(P, i, j, 0);
-    uh0[id] = real(0.25) * ((u0[id] + face_next<0>(u0, P, i, j, 0, id)) + (u1[id] + face_next<0>(u1, P, i, j, 0, id)));
-    uh1[id] = real(0.25) * ((v0[id] + face_next<1>(v0, P, i, j, 0, id)) + (v1[id] + face_next<1>(v1, P, i, j, 0, id)));
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int i = i0 + tid % TXv, j = j0 + 2 * (tid / TXv) + r;
+    if (i < P.n[0] && j < P.n[1]) {
+      const long long id = lin(P, i, j, 0);
+      uh0[id] =
+          real(0.25) * ((u0[id] + face_next<0>(u0, P, i, j, 0, id)) + (u1[id] + face_next<0>(u1, P, i, j, 0, id)));
+      uh1[id] =
+          real(0.25) * ((v0[id] + face_next<1>(v0, P, i, j, 0, id)) + (v1[id] + face_next<1>(v1, P, i, j, 0, id)));
+    }
   }
 }
 
@@ -174,7 +179,7 @@ __device__ __forceinline__ bool grid_barrier(BarrierState* bs, unsigned nblocks,
 constexpr int ERR_BARRIER_TIMEOUT = 2;
 
 template <typename real, int TXv, int TYv>
-__global__ void __launch_bounds__(TXv* TYv) batch_persistent_kernel(const BInst<real>* __restrict__ insts,
+__global__ void __launch_bounds__(TXv* TYv / 2) batch_persistent_kernel(const BInst<real>* __restrict__ insts,
                                                                      const BItem* __restrict__ items, int nitems,
                                                                      int cur, int any_cons, BarrierState* bs,
                                                                      long long limit, int skip_block, int* err) {
@@ -196,7 +201,7 @@ __global__ void __launch_bounds__(TXv* TYv) batch_persistent_kernel(const BInst<
 }
 
 template <typename real, int TXv, int TYv>
-__global__ void __launch_bounds__(TXv* TYv) batch_sweep_kernel(const BInst<real>* __restrict__ insts,
+__global__ void __launch_bounds__(TXv* TYv / 2) batch_sweep_kernel(const BInst<real>* __restrict__ insts,
                                                                 const BItem* __restrict__ items, int cur, int sw) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const BItem it = items[blockIdx.x];
@@ -346,7 +351,7 @@ static cudaError_t enqueue_batch_shape(BatchCtx* b, int si, int persistent, int 
                     (void*)&b->bar, (void*)&lim, (void*)&skip, (void*)&b->err};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(b->grid_persistent[si]);
-    cfg.blockDim = dim3(TXv * TYv);
+    cfg.blockDim = dim3(TXv * TYv / 2);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = b->stream;
     cudaLaunchAttribute attr[1];
@@ -360,7 +365,7 @@ static cudaError_t enqueue_batch_shape(BatchCtx* b, int si, int persistent, int 
   }
   for (int sw = 0; sw < SW_N; ++sw) {
     if (sw == SW_UH && !b->any_cons) continue;
-    batch_sweep_kernel<real, TXv, TYv><<<b->nitems[si], TXv * TYv, smem, b->stream>>>(insts, b->items_dev[si], cur,
+    batch_sweep_kernel<real, TXv, TYv><<<b->nitems[si], TXv * TYv / 2, smem, b->stream>>>(insts, b->items_dev[si], cur,
                                                                                        sw);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -398,7 +403,7 @@ static cudaError_t prepare_shape(BatchCtx* b, int si) {
   b->nitems[si] = (int)items.size();
   // the persistent grid: as many blocks as can be resident at once
   int per_sm = 0, nsm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persistent_kernel<real, TXv, TYv>, TXv * TYv,
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persistent_kernel<real, TXv, TYv>, TXv * TYv / 2,
                                                     smem);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->dev);

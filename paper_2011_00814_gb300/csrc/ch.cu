@@ -13,13 +13,13 @@ namespace gpe2p {
 
 // The single-instance 2D CH stage and mu: one tile per block.
 template <typename real>
-__global__ void __launch_bounds__(NTHR) ch2d_kernel(const KParams<real> P, const CHArgs<real> A) {
+__global__ void __launch_bounds__(NTHR / 2) ch2d_kernel(const KParams<real> P, const CHArgs<real> A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   ch2d_tile<real, TX, TY>(P, A, blockIdx.x * TX, blockIdx.y * TY, reinterpret_cast<real*>(smraw));
 }
 
 template <typename real>
-__global__ void __launch_bounds__(NTHR) mu2d_kernel(const KParams<real> P, const real* __restrict__ phi,
+__global__ void __launch_bounds__(NTHR / 2) mu2d_kernel(const KParams<real> P, const real* __restrict__ phi,
                                                     real* __restrict__ mu) {
   __shared__ real sm[PL];
   mu2d_tile<real, TX, TY>(P, phi, mu, blockIdx.x * TX, blockIdx.y * TY, sm);
@@ -397,6 +397,7 @@ static cudaError_t ch_go(const KParams<real>& P, const CHArgs<real>& A, int kchu
     }
   } else {
     const size_t sm = ch2d_smem<real>();
+    blk.y = TY / 2;  // two cells per thread
     e = cudaFuncSetAttribute(ch2d_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     ch2d_kernel<real><<<grd, blk, sm, s>>>(P, A);
@@ -434,6 +435,7 @@ static cudaError_t mu_go(const KParams<real>& P, const real* phi, real* mu, int 
     if (e != cudaSuccess) return e;
     mu3d_kernel<real, ISO, RING><<<grd, blk, sm, s>>>(*maps, P, phi, mu, kchunk, err);
   } else {
+    blk.y = TY / 2;  // two cells per thread
     mu2d_kernel<real><<<grd, blk, 0, s>>>(P, phi, mu);
   }
   return cudaGetLastError();

@@ -96,9 +96,9 @@ __device__ __forceinline__ void grad_iso(const T& S, const KParams<real>& P, int
 // D2Q9 isotropic gradient over r
 template <typename real, typename T>
 __device__ __forceinline__ real axis_grad_over_r(const T& S, const KParams<real>& P, int f) {
-  const real sx = P.w1 * (S(f, 1, 0, 0) - S(f, -1, 0, 0)) +
-                  P.w2 * ((S(f, 1, 1, 0) - S(f, -1, 1, 0)) + (S(f, 1, -1, 0) - S(f, -1, -1, 0)));
-  return P.grad_c * sx * fdiv(real(2) * P.inv_dx, real(2 * S.gi + 1));
+  const real sx = fma(P.w1, S(f, 1, 0, 0) - S(f, -1, 0, 0),
+                      mul_rn(P.w2, (S(f, 1, 1, 0) - S(f, -1, 1, 0)) + (S(f, 1, -1, 0) - S(f, -1, -1, 0))));
+  return mul_rn(mul_rn(P.grad_c, sx), fdiv(real(2) * P.inv_dx, real(2 * S.gi + 1)));
 }
 
 enum { C_PHI = 0, C_MU = 1, C_UH = 2, C_N = 5 };
@@ -163,7 +163,7 @@ __device__ __forceinline__ real ch_rate(const T& S, const KParams<real>& P, cons
                                        const CHPoint<real>& c) {
   real lapmu = lap_iso<real, DIM, ISO>(S, P, C_MU);
   if constexpr (DIM == 2) {
-    if (P.axisym) lapmu += axis_grad_over_r(S, P, C_MU);
+    if (P.axisym) lapmu = add_rn(lapmu, axis_grad_over_r(S, P, C_MU));
   }
   real adv = real(0);
   if (!A.conservative) {
@@ -248,64 +248,104 @@ __device__ __forceinline__ void ch_cell(const T& S, const KParams<real>& P, cons
 }
 
 // One 2D CH stage on the tile of TXv x TYv cells at (i0, j0), by a block of
-// TXv*TYv threads.  sm holds C_N * (TXv+2)*(TYv+2) reals.
+// TXv*TYv/2 threads (thread t computes the cells (t % TXv, 2 (t / TXv) + r),
+// r = 0, 1).  sm holds C_N * (TXv+2)*(TYv+2) reals, staged straight from the
+// fields on an interior tile and through the boundary maps at the edges.
 template <typename real, int TXv, int TYv>
 __device__ __forceinline__ void ch2d_tile(const KParams<real>& P, const CHArgs<real>& A, int i0, int j0,
                                           real* sm) {
-  constexpr int SXv = TXv + 2, SYv = TYv + 2, PLv = SXv * SYv, NT = TXv * TYv;
+  constexpr int SXv = TXv + 2, SYv = TYv + 2, PLv = SXv * SYv, NT = TXv * TYv / 2;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int tx = tid % TXv, ty = tid / TXv;
   const int nx = P.n[0], ny = P.n[1];
   const bool cons = A.conservative != 0;
+  const bool interior = tile_interior<real, TXv, TYv>(P, i0, j0);
   for (int idx = tid; idx < PLv; idx += NT) {
     const int ly = idx / SXv, lx = idx - ly * SXv;
-    const int gi = clampi(i0 - 1 + lx, -1, nx), gj = clampi(j0 - 1 + ly, -1, ny);
     real* b = sm + idx;
-    b[C_PHI * PLv] = ld_cen(A.phis, P, gi, gj, 0);
-    b[C_MU * PLv] = ld_cen(A.mus, P, gi, gj, 0);
-    if (cons) {
-      b[(C_UH + 0) * PLv] = ld_cvec<0>(A.uh[0], P, gi, gj, 0);
-      b[(C_UH + 1) * PLv] = ld_cvec<1>(A.uh[1], P, gi, gj, 0);
+    if (interior) {
+      const long long q = lin(P, i0 - 1 + lx, j0 - 1 + ly, 0);
+      b[C_PHI * PLv] = A.phis[q];
+      b[C_MU * PLv] = A.mus[q];
+      if (cons) {
+        b[(C_UH + 0) * PLv] = A.uh[0][q];
+        b[(C_UH + 1) * PLv] = A.uh[1][q];
+      }
+    } else {
+      const int gi = clampi(i0 - 1 + lx, -1, nx), gj = clampi(j0 - 1 + ly, -1, ny);
+      b[C_PHI * PLv] = ld_cen(A.phis, P, gi, gj, 0);
+      b[C_MU * PLv] = ld_cen(A.mus, P, gi, gj, 0);
+      if (cons) {
+        b[(C_UH + 0) * PLv] = ld_cvec<0>(A.uh[0], P, gi, gj, 0);
+        b[(C_UH + 1) * PLv] = ld_cvec<1>(A.uh[1], P, gi, gj, 0);
+      }
     }
   }
+  const int i = i0 + tx;
+  // the per-cell values, loaded before the barrier so that their latency
+  // overlaps the staging of the others
+  CHPoint<real> c[2] = {};
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int j = j0 + 2 * ty + r;
+    if (i < nx && j < ny) ch_point_load<real, 2>(P, A, i, j, 0, c[r]);
+  }
   __syncthreads();
-  const int i = i0 + tx, j = j0 + ty;
-  if (i < nx && j < ny) {
+  real L[2], ph0[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
     Tile2<real, SXv, PLv> S;
     S.sm = sm;
-    S.c = (ty + 1) * SXv + (tx + 1);
+    S.c = (2 * ty + r + 1) * SXv + (tx + 1);
     S.gi = i;
-    CHPoint<real> c;
-    ch_point_load<real, 2>(P, A, i, j, 0, c);
-    ch_cell<real, 2, 9>(S, P, A, i, j, 0, c);
+    L[r] = ch_rate<real, 2, 9>(S, P, A, c[r]);
+    ph0[r] = S(C_PHI, 0, 0, 0);
+  }
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int j = j0 + 2 * ty + r;
+    if (i < nx && j < ny) ch_finish<real, 2>(P, A, lin(P, i, j, 0), c[r], L[r], ph0[r]);
   }
   __syncthreads();
 }
 
-// mu of a 2D tile (Eq. chem-pot with the D2Q9 Laplacian); sm holds (TXv+2)*(TYv+2) reals
+// mu of a 2D tile (Eq. chem-pot with the D2Q9 Laplacian) by TXv*TYv/2 threads,
+// two cells each; sm holds (TXv+2)*(TYv+2) reals
 template <typename real, int TXv, int TYv>
 __device__ __forceinline__ void mu2d_tile(const KParams<real>& P, const real* __restrict__ phi,
                                           real* __restrict__ mu, int i0, int j0, real* sm) {
-  constexpr int SXv = TXv + 2, SYv = TYv + 2, PLv = SXv * SYv, NT = TXv * TYv;
+  constexpr int SXv = TXv + 2, SYv = TYv + 2, PLv = SXv * SYv, NT = TXv * TYv / 2;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int tx = tid % TXv, ty = tid / TXv;
   const int nx = P.n[0], ny = P.n[1];
+  const bool interior = tile_interior<real, TXv, TYv>(P, i0, j0);
   for (int idx = tid; idx < PLv; idx += NT) {
     const int ly = idx / SXv, lx = idx - ly * SXv;
-    const int gi = clampi(i0 - 1 + lx, -1, nx), gj = clampi(j0 - 1 + ly, -1, ny);
-    sm[idx] = ld_cen(phi, P, gi, gj, 0);
+    if (interior) {
+      sm[idx] = phi[lin(P, i0 - 1 + lx, j0 - 1 + ly, 0)];
+    } else {
+      const int gi = clampi(i0 - 1 + lx, -1, nx), gj = clampi(j0 - 1 + ly, -1, ny);
+      sm[idx] = ld_cen(phi, P, gi, gj, 0);
+    }
   }
   __syncthreads();
-  const int i = i0 + tx, j = j0 + ty;
-  if (i < nx && j < ny) {
+  const int i = i0 + tx;
+  real out[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
     Tile2<real, SXv, PLv> S;
     S.sm = sm;
-    S.c = (ty + 1) * SXv + (tx + 1);
+    S.c = (2 * ty + r + 1) * SXv + (tx + 1);
     S.gi = i;
     const real f = S(0, 0, 0, 0);
     real lap = lap_iso<real, 2, 9>(S, P, 0);
-    if (P.axisym) lap += axis_grad_over_r(S, P, 0);  // Eq. chem-pot-axisym
-    mu[lin(P, i, j, 0)] = fma(P.a4 * f, fma(f, f, real(-1)), -(P.kappa * lap));
+    if (P.axisym) lap = add_rn(lap, axis_grad_over_r(S, P, 0));  // Eq. chem-pot-axisym
+    out[r] = fma(P.a4 * f, fma(f, f, real(-1)), -(P.kappa * lap));
+  }
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int j = j0 + 2 * ty + r;
+    if (i < nx && j < ny) mu[lin(P, i, j, 0)] = out[r];
   }
   __syncthreads();
 }

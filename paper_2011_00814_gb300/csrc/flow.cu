@@ -16,9 +16,9 @@
 
 namespace gpe2p {
 
-// The single-instance 2D flow stage: one tile per block.
+// The single-instance 2D flow stage: one tile per block, two cells per thread.
 template <typename real, int MODE>
-__global__ void __launch_bounds__(NTHR) flow2d_kernel(const KParams<real> P, const FlowArgs<real> A) {
+__global__ void __launch_bounds__(NTHR / 2) flow2d_kernel(const KParams<real> P, const FlowArgs<real> A) {
   extern __shared__ __align__(16) unsigned char smraw[];
   flow2d_tile<real, MODE, TX, TY>(P, A, blockIdx.x * TX, blockIdx.y * TY, reinterpret_cast<real*>(smraw));
 }
@@ -234,6 +234,7 @@ cudaError_t launch_flow_stage(const KParams<real>& P, const FlowArgs<real>& A, i
 #undef GPE2P_FLOW3_CASE
   } else {
     const size_t sm = flow2d_smem<real>();
+    blk.y = TY / 2;  // two cells per thread
 #define GPE2P_FLOW_CASE(M)                                                                                \
   e = cudaFuncSetAttribute(flow2d_kernel<real, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
   if (e != cudaSuccess) return e;                                                                         \

@@ -27,7 +27,10 @@ enum { F_P = 0, F_U = 1, F_V = 2, F_W = 3, F_PHI = 4, F_RHO = 5, F_ETA = 6, F_NU
 
 // The rates below gather every term with its grid factor applied once:
 // sums of the four edge viscosities, face velocities and transverse
-// pressures are formed unnormalised and scaled together at the end.
+// pressures are formed unnormalised and scaled together at the end.  Every
+// sum of two products is written as the fused multiply-add it is meant to be
+// (the compiler could otherwise fuse either product, and two kernels that
+// inline this code could round differently).
 template <typename real, int DIM, typename T>
 struct FlowOps {
   // dx / (2 r) at the centre of the cell column at x offset ox (axisymmetric form, 2D tiles)
@@ -108,14 +111,14 @@ struct FlowOps {
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       const int ex = a == 0, ey = a == 1, ez = a == 2;
-      diff += (nu0 + S(F_NU, ex, ey, ez)) * (S(F_P, ex, ey, ez) - p0) -
-              (nu0 + S(F_NU, -ex, -ey, -ez)) * (p0 - S(F_P, -ex, -ey, -ez));
+      diff = fma(nu0 + S(F_NU, ex, ey, ez), S(F_P, ex, ey, ez) - p0, diff);
+      diff = fma(nu0 + S(F_NU, -ex, -ey, -ez), S(F_P, -ex, -ey, -ez) - p0, diff);
     }
     if constexpr (DIM == 2) {
       // (nu / r) dp/dr, Eq. gpe-pressure-two-phase-axisym
-      if (P.axisym) diff += real(2) * nu0 * (S(F_P, 1, 0, 0) - S(F_P, -1, 0, 0)) * dx_2r(S, 0);
+      if (P.axisym) diff = fma(real(2) * nu0 * (S(F_P, 1, 0, 0) - S(F_P, -1, 0, 0)), dx_2r(S, 0), diff);
     }
-    return -S(F_RHO, 0, 0, 0) * P.cs2 * (d0 * P.inv_dx) + diff * (real(0.5) * P.inv_dx2);
+    return fma(diff, real(0.5) * P.inv_dx2, -(S(F_RHO, 0, 0, 0) * P.cs2 * mul_rn(d0, P.inv_dx)));
   }
 
   // rate of velocity component C on the cell's low face along C; d0 = dx div u of the cell
@@ -131,8 +134,8 @@ struct FlowOps {
     else
       gradp = (S(F_P, 0, 0, 0) - S(F_P, -cx, -cy, -cz)) * P.inv_dx;
     const real uc0 = S(FC, 0, 0, 0);
-    const real tcc = S(F_ETA, 0, 0, 0) * (S(FC, cx, cy, cz) - uc0) -
-                     S(F_ETA, -cx, -cy, -cz) * (uc0 - S(FC, -cx, -cy, -cz));
+    const real tcc = fma(S(F_ETA, -cx, -cy, -cz), S(FC, -cx, -cy, -cz) - uc0,
+                         mul_rn(S(F_ETA, 0, 0, 0), S(FC, cx, cy, cz) - uc0));
     real edge = real(0), conv4 = real(0);
 #pragma unroll
     for (int t = 0; t < DIM; ++t) {
@@ -144,11 +147,15 @@ struct FlowOps {
       const real ucp = S(FC, tx, ty, tz), ucm = S(FC, -tx, -ty, -tz);
       const real ut0 = S(FT, 0, 0, 0), utc = S(FT, -cx, -cy, -cz);
       const real utp = S(FT, tx, ty, tz), utpc = S(FT, tx - cx, ty - cy, tz - cz);
-      edge += e4p * ((ucp - uc0) + (utp - utpc)) - e4m * ((uc0 - ucm) + (ut0 - utc));
-      conv4 += ((ut0 + utc) + (utp + utpc)) * (ucp - ucm);
+      edge = fma(e4p, (ucp - uc0) + (utp - utpc), edge);
+      edge = fma(e4m, (ucm - uc0) + (utc - ut0), edge);
+      conv4 = fma((ut0 + utc) + (utp + utpc), ucp - ucm, conv4);
     }
-    real visc = real(2) * tcc + real(0.25) * edge;
-    if (P.bulk) visc += S(F_ETA, 0, 0, 0) * d0 - S(F_ETA, -cx, -cy, -cz) * divsum(S, P, -cx, -cy, -cz);
+    real visc = fma(real(2), tcc, mul_rn(real(0.25), edge));
+    if (P.bulk) {
+      visc = fma(S(F_ETA, 0, 0, 0), d0, visc);
+      visc = fma(-S(F_ETA, -cx, -cy, -cz), divsum(S, P, -cx, -cy, -cz), visc);
+    }
     if constexpr (DIM == 2) {
       if (P.axisym) {
         const real eta_f = real(0.5) * (S(F_ETA, -cx, -cy, 0) + S(F_ETA, 0, 0, 0));
@@ -156,19 +163,21 @@ struct FlowOps {
         if (C == 0) {
           // (eta / r)(du_r/dr - u_r / r) on the u face i, r = i dx (i >= 1)
           const real ir = fdiv(real(1), real(S.gi));
-          visc += eta_f * ir * (real(0.5) * dudr2 - uc0 * ir);
+          visc = fma(mul_rn(eta_f, ir), fma(real(0.5), dudr2, -mul_rn(uc0, ir)), visc);
         } else {
           // (eta / r) du_z/dr on the v face of column i, r = (i + 1/2) dx
-          visc += eta_f * dudr2 * dx_2r(S, 0);
+          visc = fma(mul_rn(eta_f, dudr2), dx_2r(S, 0), visc);
         }
       }
     }
     const real st = -P.sigma * (S(F_PHI, 0, 0, 0) + S(F_PHI, -cx, -cy, -cz)) *
-                    (S(F_MU, 0, 0, 0) - S(F_MU, -cx, -cy, -cz)) * P.inv_2dx;
-    const real grav = (real(0.5) * rb2 - P.rho_ref) * P.g[C];
-    const real force = -gradp + visc * P.inv_dx2 + st + grav;
-    const real conv = (uc0 * (S(FC, cx, cy, cz) - S(FC, -cx, -cy, -cz)) + real(0.25) * conv4) * P.inv_2dx;
-    return fdiv(real(2) * force, rb2) - conv;
+                    (S(F_MU, 0, 0, 0) - S(F_MU, -cx, -cy, -cz));
+    const real grav = fma(real(0.5), rb2, -P.rho_ref);
+    real force = fma(visc, P.inv_dx2, -gradp);
+    force = fma(st, P.inv_2dx, force);
+    force = fma(grav, P.g[C], force);
+    const real conv = fma(uc0, S(FC, cx, cy, cz) - S(FC, -cx, -cy, -cz), mul_rn(real(0.25), conv4));
+    return fma(-conv, P.inv_2dx, fdiv(real(2) * force, rb2));
   }
 };
 
@@ -184,59 +193,97 @@ struct Tile2 {
   }
 };
 
+// Whether the one-cell halo of the TXv x TYv tile at (i0, j0) lies inside
+// the domain, so that its staged values need no boundary map: every staged
+// cell (gi, gj) then has 0 <= gi < nx and 0 <= gj < ny, and a face value on
+// it is the stored one (the wall faces 0 of a walled axis lie outside such a
+// halo, since i0, j0 >= 1).
+template <typename real, int TXv, int TYv>
+__device__ __forceinline__ bool tile_interior(const KParams<real>& P, int i0, int j0) {
+  return i0 >= 1 && i0 + TXv + 1 <= P.n[0] && j0 >= 1 && j0 + TYv + 1 <= P.n[1];
+}
+
 // MODE 0: out = L(q);  MODE 1: out = q + dt L(q);  MODE 2: out = a q0 + b (q + dt L(q)).
 // One 2D flow stage on the tile of TXv x TYv cells at (i0, j0), by a block of
-// TXv*TYv threads (thread t owns cell (t % TXv, t / TXv)).  The block stages
-// p, u, v, phi, rho, eta, nu = eta/rho and mu with a one-cell halo (ghosts
-// mapped by the boundary rules) in sm, F_N * (TXv+2)*(TYv+2) reals.
+// TXv*TYv/2 threads: thread t computes the cells (t % TXv, 2 (t / TXv) + r),
+// r = 0, 1, whose stencils share most of their staged values.  The block
+// stages p, u, v, phi, rho, eta, nu = eta/rho and mu with a one-cell halo in
+// sm, F_N * (TXv+2)*(TYv+2) reals: straight from the fields on an interior
+// tile, through the boundary maps (ghosts) on a tile at the domain's edge.
 template <typename real, int MODE, int TXv, int TYv>
 __device__ __forceinline__ void flow2d_tile(const KParams<real>& P, const FlowArgs<real>& A, int i0, int j0,
                                             real* sm) {
-  constexpr int SXv = TXv + 2, SYv = TYv + 2, PLv = SXv * SYv, NT = TXv * TYv;
+  constexpr int SXv = TXv + 2, SYv = TYv + 2, PLv = SXv * SYv, NT = TXv * TYv / 2;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int tx = tid % TXv, ty = tid / TXv;
   const int nx = P.n[0], ny = P.n[1];
+  const bool interior = tile_interior<real, TXv, TYv>(P, i0, j0);
   for (int idx = tid; idx < PLv; idx += NT) {
     const int ly = idx / SXv, lx = idx - ly * SXv;
-    const int gi = clampi(i0 - 1 + lx, -1, nx), gj = clampi(j0 - 1 + ly, -1, ny);
-    const real phi = ld_cen(A.phi, P, gi, gj, 0);
+    real pv, uv, vv, phi, muv;
+    if (interior) {
+      const long long q = lin(P, i0 - 1 + lx, j0 - 1 + ly, 0);
+      pv = A.q[0][q];
+      uv = A.q[1][q];
+      vv = A.q[2][q];
+      phi = A.phi[q];
+      muv = A.mu[q];
+    } else {
+      const int gi = clampi(i0 - 1 + lx, -1, nx), gj = clampi(j0 - 1 + ly, -1, ny);
+      pv = ld_cen(A.q[0], P, gi, gj, 0);
+      uv = ld_face<0>(A.q[1], P, gi, gj, 0);
+      vv = ld_face<1>(A.q[2], P, gi, gj, 0);
+      phi = ld_cen(A.phi, P, gi, gj, 0);
+      muv = ld_cen(A.mu, P, gi, gj, 0);
+    }
     const real rho = rho_of(P, phi), eta = eta_of(P, phi);
     real* b = sm + idx;
-    b[F_P * PLv] = ld_cen(A.q[0], P, gi, gj, 0);
-    b[F_U * PLv] = ld_face<0>(A.q[1], P, gi, gj, 0);
-    b[F_V * PLv] = ld_face<1>(A.q[2], P, gi, gj, 0);
+    b[F_P * PLv] = pv;
+    b[F_U * PLv] = uv;
+    b[F_V * PLv] = vv;
     b[F_PHI * PLv] = phi;
     b[F_RHO * PLv] = rho;
     b[F_ETA * PLv] = eta;
     b[F_NU * PLv] = fdiv(eta, rho);
-    b[F_MU * PLv] = ld_cen(A.mu, P, gi, gj, 0);
+    b[F_MU * PLv] = muv;
   }
   __syncthreads();
-  const int i = i0 + tx, j = j0 + ty;
-  if (i < nx && j < ny) {
+  const int i = i0 + tx;
+  real out[2][3];
+  using Ops = FlowOps<real, 2, Tile2<real, SXv, PLv>>;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int j = j0 + 2 * ty + r;
+    const bool act = i < nx && j < ny;
     Tile2<real, SXv, PLv> S;
     S.sm = sm;
-    S.c = (ty + 1) * SXv + (tx + 1);
+    S.c = (2 * ty + r + 1) * SXv + (tx + 1);
     S.gi = i;
-    using Ops = FlowOps<real, 2, Tile2<real, SXv, PLv>>;
     const real D0 = Ops::divsum(S, P, 0, 0, 0);
     real L[3];
     L[0] = Ops::rate_p(S, P, D0);
     L[1] = (P.bc[0] != BC_PERIODIC && i == 0) ? real(0) : Ops::template rate_vel<0>(S, P, D0);
     L[2] = (P.bc[1] != BC_PERIODIC && j == 0) ? real(0) : Ops::template rate_vel<1>(S, P, D0);
-    const long long id = lin(P, i, j, 0);
     const int F[3] = {F_P, F_U, F_V};
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-      real o;
       if (MODE == 0) {
-        o = L[f];
+        out[r][f] = L[f];
       } else {
         const real q = S(F[f], 0, 0, 0);
-        if (MODE == 1) o = q + P.dt * L[f];
-        else o = A.a * A.q0[f][id] + A.b * (q + P.dt * L[f]);
+        if (MODE == 1) out[r][f] = q + P.dt * L[f];
+        else out[r][f] = A.a * (act ? A.q0[f][lin(P, i, j, 0)] : real(0)) + A.b * (q + P.dt * L[f]);
       }
-      A.out[f][id] = o;
+    }
+  }
+  // stores after both cells, so that nothing separates their shared loads
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int j = j0 + 2 * ty + r;
+    if (i < nx && j < ny) {
+      const long long id = lin(P, i, j, 0);
+#pragma unroll
+      for (int f = 0; f < 3; ++f) A.out[f][id] = out[r][f];
     }
   }
   __syncthreads();

@@ -132,6 +132,16 @@ __device__ __forceinline__ real eta_of(const KParams<real>& P, real phi) {
   return fma(P.eta_d, phi, P.eta_m);
 }
 
+// an add and a multiply that the compiler never fuses with a neighbouring
+// operation: where a sum of two products could be contracted into a fused
+// multiply-add either way, the operator code spells out the fusion it wants
+// with fma() and these, so that every kernel that inlines the same operator
+// code rounds alike
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // division: the FP32 path uses the fast approximate quotient (2 ulp), the
 // FP64 path the IEEE one
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
