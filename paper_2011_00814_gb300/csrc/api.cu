@@ -332,8 +332,8 @@ static cudaError_t enqueue_step(gpe2p_ctx* h, int cur, ProfHook* hook = nullptr)
   for (int f = 0; f < 4; ++f) { A.q[f] = q(s2, f); A.out[f] = q(s1, f); }
   A.a = real(1.0 / 3.0);
   A.b = real(2.0 / 3.0);
-  // 3D advective steps: the last stage also leaves u^n + u^{n+1} per face
-  const bool usum = DIM == 3 && !h->prm.ch_advection;
+  // advective steps: the last stage also leaves u^n + u^{n+1} per face
+  const bool usum = !h->prm.ch_advection;
   if (usum)
     for (int a = 0; a < 3; ++a) A.usum[a] = (real*)h->usum[a];
   if ((e = launch_flow_stage<real, DIM>(P, A, 2, h->kchunk, s, &h->flow_maps[s2], h->d_err)) != cudaSuccess)

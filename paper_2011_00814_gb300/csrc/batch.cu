@@ -44,6 +44,7 @@ struct BInst {
   real* phis;      // CH stage state
   real* mus;       // mu of the stage state
   real* uh[2];     // time-centred cell velocity
+  real* us[2];     // u^n + u^{n+1} per face (advective form), left by the last flow stage
   int conservative;
 };
 
@@ -94,6 +95,10 @@ __device__ __forceinline__ void do_sweep(int sw, const BInst<real>& b, const BIt
     A.out[3] = nullptr;
     A.phi = b.phi;
     A.mu = b.mu;
+    const bool sums = sw == SW_FLOW3 && !b.conservative;
+    A.usum[0] = sums ? b.us[0] : nullptr;
+    A.usum[1] = sums ? b.us[1] : nullptr;
+    A.usum[2] = nullptr;
     if (sw == SW_FLOW1) {
       A.a = real(0);
       A.b = real(1);
@@ -129,6 +134,10 @@ __device__ __forceinline__ void do_sweep(int sw, const BInst<real>& b, const BIt
   C.conservative = b.conservative;
   C.acc = nullptr;
   C.phin = b.phi;
+  C.usum[0] = b.conservative ? nullptr : b.us[0];
+  C.usum[1] = b.conservative ? nullptr : b.us[1];
+  C.usum[2] = nullptr;
+  C.phi_lo = nullptr;
   if (sw == SW_CH1) {
     C.stage = 1;
     C.phis = b.phi;
@@ -310,7 +319,7 @@ struct BatchCtx {
 };
 
 // field roles inside an instance block
-enum { BF_Q = 0, BF_PHI = 9, BF_MU = 10, BF_PHIS = 11, BF_MUS = 12, BF_UH = 13, BF_N = 15 };
+enum { BF_Q = 0, BF_PHI = 9, BF_MU = 10, BF_PHIS = 11, BF_MUS = 12, BF_UH = 13, BF_US = 15, BF_N = 17 };
 
 template <typename real>
 static void fill_insts(BatchCtx* b) {
@@ -330,6 +339,8 @@ static void fill_insts(BatchCtx* b) {
     I[k].mus = fld(BF_MUS);
     I[k].uh[0] = fld(BF_UH);
     I[k].uh[1] = fld(BF_UH + 1);
+    I[k].us[0] = fld(BF_US);
+    I[k].us[1] = fld(BF_US + 1);
     I[k].conservative = p.ch_advection;
   }
 }

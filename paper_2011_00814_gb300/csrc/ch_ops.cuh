@@ -251,20 +251,32 @@ __device__ __forceinline__ void ch_cell(const T& S, const KParams<real>& P, cons
 // TXv*TYv/2 threads (thread t computes the cells (t % TXv, 2 (t / TXv) + r),
 // r = 0, 1).  sm holds C_N * (TXv+2)*(TYv+2) reals, staged straight from the
 // fields on an interior tile and through the boundary maps at the edges.
+// Stage 1 of the advective form with A.usum set forms the time-centred
+// velocity from the face sums u^n + u^{n+1} the last flow stage left.
 template <typename real, int TXv, int TYv>
 __device__ __forceinline__ void ch2d_tile(const KParams<real>& P, const CHArgs<real>& A, int i0, int j0,
                                           real* sm) {
-  constexpr int SXv = TXv + 2, SYv = TYv + 2, PLv = SXv * SYv, NT = TXv * TYv / 2;
+  constexpr int SXv = TXv + 2, SYv = TYv + 2, PLv = SXv * SYv;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int tx = tid % TXv, ty = tid / TXv;
   const int nx = P.n[0], ny = P.n[1];
   const bool cons = A.conservative != 0;
-  const bool interior = tile_interior<real, TXv, TYv>(P, i0, j0);
-  for (int idx = tid; idx < PLv; idx += NT) {
-    const int ly = idx / SXv, lx = idx - ly * SXv;
-    real* b = sm + idx;
-    if (interior) {
-      const long long q = lin(P, i0 - 1 + lx, j0 - 1 + ly, 0);
+  const bool usum = !cons && A.usum[0] && A.stage == 1;
+  const int i = i0 + tx;
+  // the per-cell values, loaded first so that their latency overlaps the staging
+  CHPoint<real> c[2] = {};
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int j = j0 + 2 * ty + r;
+    if (i < nx && j < ny) {
+      if (usum) ch_point_load<real, 2, true>(P, A, i, j, 0, c[r]);
+      else ch_point_load<real, 2>(P, A, i, j, 0, c[r]);
+    }
+  }
+  stage2d<real, TXv, TYv>(P, i0, j0, tile_interior<real, TXv, TYv>(P, i0, j0),
+                          [&](int e, int lx, int ly, long long q) {
+    real* b = sm + e;
+    if (q >= 0) {
       b[C_PHI * PLv] = A.phis[q];
       b[C_MU * PLv] = A.mus[q];
       if (cons) {
@@ -280,16 +292,7 @@ __device__ __forceinline__ void ch2d_tile(const KParams<real>& P, const CHArgs<r
         b[(C_UH + 1) * PLv] = ld_cvec<1>(A.uh[1], P, gi, gj, 0);
       }
     }
-  }
-  const int i = i0 + tx;
-  // the per-cell values, loaded before the barrier so that their latency
-  // overlaps the staging of the others
-  CHPoint<real> c[2] = {};
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const int j = j0 + 2 * ty + r;
-    if (i < nx && j < ny) ch_point_load<real, 2>(P, A, i, j, 0, c[r]);
-  }
+  });
   __syncthreads();
   real L[2], ph0[2];
 #pragma unroll
@@ -300,6 +303,7 @@ __device__ __forceinline__ void ch2d_tile(const KParams<real>& P, const CHArgs<r
     S.gi = i;
     L[r] = ch_rate<real, 2, 9>(S, P, A, c[r]);
     ph0[r] = S(C_PHI, 0, 0, 0);
+    if (usum) c[r].pn = ph0[r];  // stage 1: phi^{n+1/2} = phi_s
   }
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
@@ -314,20 +318,19 @@ __device__ __forceinline__ void ch2d_tile(const KParams<real>& P, const CHArgs<r
 template <typename real, int TXv, int TYv>
 __device__ __forceinline__ void mu2d_tile(const KParams<real>& P, const real* __restrict__ phi,
                                           real* __restrict__ mu, int i0, int j0, real* sm) {
-  constexpr int SXv = TXv + 2, SYv = TYv + 2, PLv = SXv * SYv, NT = TXv * TYv / 2;
+  constexpr int SXv = TXv + 2, PLv = SXv * (TYv + 2);
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int tx = tid % TXv, ty = tid / TXv;
   const int nx = P.n[0], ny = P.n[1];
-  const bool interior = tile_interior<real, TXv, TYv>(P, i0, j0);
-  for (int idx = tid; idx < PLv; idx += NT) {
-    const int ly = idx / SXv, lx = idx - ly * SXv;
-    if (interior) {
-      sm[idx] = phi[lin(P, i0 - 1 + lx, j0 - 1 + ly, 0)];
+  stage2d<real, TXv, TYv>(P, i0, j0, tile_interior<real, TXv, TYv>(P, i0, j0),
+                          [&](int e, int lx, int ly, long long q) {
+    if (q >= 0) {
+      sm[e] = phi[q];
     } else {
       const int gi = clampi(i0 - 1 + lx, -1, nx), gj = clampi(j0 - 1 + ly, -1, ny);
-      sm[idx] = ld_cen(phi, P, gi, gj, 0);
+      sm[e] = ld_cen(phi, P, gi, gj, 0);
     }
-  }
+  });
   __syncthreads();
   const int i = i0 + tx;
   real out[2];

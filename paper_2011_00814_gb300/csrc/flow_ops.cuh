@@ -203,6 +203,23 @@ __device__ __forceinline__ bool tile_interior(const KParams<real>& P, int i0, in
   return i0 >= 1 && i0 + TXv + 1 <= P.n[0] && j0 >= 1 && j0 + TYv + 1 <= P.n[1];
 }
 
+// The staged region of a 2D tile, (TXv + 2) x (TYv + 2) cells, spread over
+// the block's threads.  fn(e, lx, ly, off) is called for every staged cell
+// e = ly (TXv + 2) + lx, i.e. the cell (i0 - 1 + lx, j0 - 1 + ly); off is its
+// element offset when the tile is interior (every staged cell inside the
+// domain; formed from one per-tile base in 32-bit arithmetic), else -1.
+template <typename real, int TXv, int TYv, typename Fn>
+__device__ __forceinline__ void stage2d(const KParams<real>& P, int i0, int j0, bool interior, Fn fn) {
+  constexpr int SXv = TXv + 2, PLv = SXv * (TYv + 2), NT = TXv * TYv / 2;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const long long base = interior ? lin(P, i0 - 1, j0 - 1, 0) : -1LL;
+  const int sy = (int)P.sy;
+  for (int e = tid; e < PLv; e += NT) {
+    const int ly = e / SXv, lx = e - ly * SXv;
+    fn(e, lx, ly, interior ? base + (ly * sy + lx) : -1LL);
+  }
+}
+
 // MODE 0: out = L(q);  MODE 1: out = q + dt L(q);  MODE 2: out = a q0 + b (q + dt L(q)).
 // One 2D flow stage on the tile of TXv x TYv cells at (i0, j0), by a block of
 // TXv*TYv/2 threads: thread t computes the cells (t % TXv, 2 (t / TXv) + r),
@@ -210,19 +227,31 @@ __device__ __forceinline__ bool tile_interior(const KParams<real>& P, int i0, in
 // stages p, u, v, phi, rho, eta, nu = eta/rho and mu with a one-cell halo in
 // sm, F_N * (TXv+2)*(TYv+2) reals: straight from the fields on an interior
 // tile, through the boundary maps (ghosts) on a tile at the domain's edge.
+// With A.usum set (MODE 2, the last stage), it also stores u^n + u^{n+1} on
+// the cells' faces, from which the CH step forms the time-centred velocity.
 template <typename real, int MODE, int TXv, int TYv>
 __device__ __forceinline__ void flow2d_tile(const KParams<real>& P, const FlowArgs<real>& A, int i0, int j0,
                                             real* sm) {
-  constexpr int SXv = TXv + 2, SYv = TYv + 2, PLv = SXv * SYv, NT = TXv * TYv / 2;
+  constexpr int SXv = TXv + 2, SYv = TYv + 2, PLv = SXv * SYv;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int tx = tid % TXv, ty = tid / TXv;
   const int nx = P.n[0], ny = P.n[1];
-  const bool interior = tile_interior<real, TXv, TYv>(P, i0, j0);
-  for (int idx = tid; idx < PLv; idx += NT) {
-    const int ly = idx / SXv, lx = idx - ly * SXv;
+  const int i = i0 + tx;
+  // q^n at the thread's cells, loaded first so that its latency overlaps the staging
+  real q0v[2][3];
+  if (MODE == 2) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int j = j0 + 2 * ty + r;
+      const bool act = i < nx && j < ny;
+#pragma unroll
+      for (int f = 0; f < 3; ++f) q0v[r][f] = act ? A.q0[f][lin(P, i, j, 0)] : real(0);
+    }
+  }
+  stage2d<real, TXv, TYv>(P, i0, j0, tile_interior<real, TXv, TYv>(P, i0, j0),
+                          [&](int e, int lx, int ly, long long q) {
     real pv, uv, vv, phi, muv;
-    if (interior) {
-      const long long q = lin(P, i0 - 1 + lx, j0 - 1 + ly, 0);
+    if (q >= 0) {
       pv = A.q[0][q];
       uv = A.q[1][q];
       vv = A.q[2][q];
@@ -237,7 +266,7 @@ __device__ __forceinline__ void flow2d_tile(const KParams<real>& P, const FlowAr
       muv = ld_cen(A.mu, P, gi, gj, 0);
     }
     const real rho = rho_of(P, phi), eta = eta_of(P, phi);
-    real* b = sm + idx;
+    real* b = sm + e;
     b[F_P * PLv] = pv;
     b[F_U * PLv] = uv;
     b[F_V * PLv] = vv;
@@ -246,15 +275,13 @@ __device__ __forceinline__ void flow2d_tile(const KParams<real>& P, const FlowAr
     b[F_ETA * PLv] = eta;
     b[F_NU * PLv] = fdiv(eta, rho);
     b[F_MU * PLv] = muv;
-  }
+  });
   __syncthreads();
-  const int i = i0 + tx;
   real out[2][3];
   using Ops = FlowOps<real, 2, Tile2<real, SXv, PLv>>;
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int j = j0 + 2 * ty + r;
-    const bool act = i < nx && j < ny;
     Tile2<real, SXv, PLv> S;
     S.sm = sm;
     S.c = (2 * ty + r + 1) * SXv + (tx + 1);
@@ -271,8 +298,9 @@ __device__ __forceinline__ void flow2d_tile(const KParams<real>& P, const FlowAr
         out[r][f] = L[f];
       } else {
         const real q = S(F[f], 0, 0, 0);
-        if (MODE == 1) out[r][f] = q + P.dt * L[f];
-        else out[r][f] = A.a * (act ? A.q0[f][lin(P, i, j, 0)] : real(0)) + A.b * (q + P.dt * L[f]);
+        const real s1 = fma(P.dt, L[f], q);
+        if (MODE == 1) out[r][f] = s1;
+        else out[r][f] = fma(A.a, q0v[r][f], mul_rn(A.b, s1));
       }
     }
   }
@@ -284,6 +312,10 @@ __device__ __forceinline__ void flow2d_tile(const KParams<real>& P, const FlowAr
       const long long id = lin(P, i, j, 0);
 #pragma unroll
       for (int f = 0; f < 3; ++f) A.out[f][id] = out[r][f];
+      if (MODE == 2 && A.usum[0]) {
+        A.usum[0][id] = q0v[r][1] + out[r][1];
+        A.usum[1][id] = q0v[r][2] + out[r][2];
+      }
     }
   }
   __syncthreads();
