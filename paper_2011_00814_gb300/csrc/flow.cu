@@ -57,6 +57,116 @@ struct RingTile {
   }
 };
 
+// The -z side terms of a cell's 3D rates are what the same thread formed on
+// the +z side of the cell below, one plane earlier: the stresses on the x-z
+// and y-z edges between the two planes (the u and v faces' -z edge terms, and
+// the w face's -x and -y edge terms, are their negatives), the averaged
+// pressure and the divergence of the cell below (the w face's gradient and
+// bulk terms), and the flux nu (p_k - p_{k-1}) of the pressure diffusion.
+// The block marches along z, so these are carried in registers.
+template <typename real>
+struct ZCarry {
+  real tau_xz, tau_yz;  // 4 eta_edge x (du/dz + dw/dx) and (dv/dz + dw/dy), times dx, on the +z edges
+  real psum2;           // 36 x the pressure averaged over the x-y plane (Eq. gradp-u-p-ave-3d)
+  real div;             // dx div u
+  real pflux;           // (nu + nu(+z)) (p(+z) - p)
+};
+
+// FlowOps with the -z side terms taken from the carry of the plane below and
+// the +z side terms returned for the plane above (3D ring tiles only)
+template <typename real, typename T>
+struct FlowOpsZ : FlowOps<real, 3, T> {
+  using B = FlowOps<real, 3, T>;
+
+  // the +z side terms of the cell (planes 0 and +1 only); d0 = dx div u of the cell
+  __device__ __forceinline__ static void plus_z(const T& S, const KParams<real>& P, real d0, ZCarry<real>& o) {
+    real e4p, e4m;
+    B::template edge_eta4<0>(S, 2, e4p, e4m);
+    o.tau_xz = e4p * ((S(F_U, 0, 0, 1) - S(F_U, 0, 0, 0)) + (S(F_W, 0, 0, 1) - S(F_W, -1, 0, 1)));
+    B::template edge_eta4<1>(S, 2, e4p, e4m);
+    o.tau_yz = e4p * ((S(F_V, 0, 0, 1) - S(F_V, 0, 0, 0)) + (S(F_W, 0, 0, 1) - S(F_W, 0, -1, 1)));
+    o.psum2 = B::averaged(P) ? B::template psum<2>(S, 0, 0, 0) : real(0);
+    o.div = d0;
+    o.pflux = (S(F_NU, 0, 0, 0) + S(F_NU, 0, 0, 1)) * (S(F_P, 0, 0, 1) - S(F_P, 0, 0, 0));
+  }
+
+  // the pressure rate with the -z flux from the carry
+  __device__ __forceinline__ static real rate_p(const T& S, const KParams<real>& P, real d0, const ZCarry<real>& in,
+                                                const ZCarry<real>& out) {
+    real diff = out.pflux - in.pflux;
+    const real nu0 = S(F_NU, 0, 0, 0), p0 = S(F_P, 0, 0, 0);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const int ex = a == 0, ey = a == 1;
+      diff = fma(nu0 + S(F_NU, ex, ey, 0), S(F_P, ex, ey, 0) - p0, diff);
+      diff = fma(nu0 + S(F_NU, -ex, -ey, 0), S(F_P, -ex, -ey, 0) - p0, diff);
+    }
+    return fma(diff, real(0.5) * P.inv_dx2, -(S(F_RHO, 0, 0, 0) * P.cs2 * mul_rn(d0, P.inv_dx)));
+  }
+
+  // the velocity rate of component C with its z-side (C = 0, 1) or x- and
+  // y-side (C = 2) edge terms below the cell, and the w face's averaged
+  // pressure and divergence below, from the carry
+  template <int C>
+  __device__ __forceinline__ static real rate_vel(const T& S, const KParams<real>& P, real d0,
+                                                  const ZCarry<real>& in, const ZCarry<real>& out) {
+    constexpr int cx = C == 0, cy = C == 1, cz = C == 2;
+    const int FC = F_U + C;
+    const real rb2 = S(F_RHO, -cx, -cy, -cz) + S(F_RHO, 0, 0, 0);
+    real gradp;
+    if (B::averaged(P)) {
+      const real pm = C == 2 ? in.psum2 : B::template psum<C>(S, -cx, -cy, -cz);
+      const real p0 = C == 2 ? out.psum2 : B::template psum<C>(S, 0, 0, 0);
+      gradp = (p0 - pm) * (P.inv_dx * real(1.0 / 36.0));
+    } else {
+      gradp = (S(F_P, 0, 0, 0) - S(F_P, -cx, -cy, -cz)) * P.inv_dx;
+    }
+    const real uc0 = S(FC, 0, 0, 0);
+    const real tcc = fma(S(F_ETA, -cx, -cy, -cz), S(FC, -cx, -cy, -cz) - uc0,
+                         mul_rn(S(F_ETA, 0, 0, 0), S(FC, cx, cy, cz) - uc0));
+    real edge = real(0), conv4 = real(0);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      if (t == C) continue;
+      const int tx = t == 0, ty = t == 1, tz = t == 2;
+      const int FT = F_U + t;
+      const real ucp = S(FC, tx, ty, tz), ucm = S(FC, -tx, -ty, -tz);
+      const real ut0 = S(FT, 0, 0, 0), utc = S(FT, -cx, -cy, -cz);
+      const real utp = S(FT, tx, ty, tz), utpc = S(FT, tx - cx, ty - cy, tz - cz);
+      if (t == 2) {
+        // the x-z or y-z edges above and below the u or v face
+        edge += (C == 0 ? out.tau_xz : out.tau_yz) - (C == 0 ? in.tau_xz : in.tau_yz);
+      } else if (C == 2) {
+        // the w face: the edge on its -t side lies between the planes, below the cell
+        real e4p, e4m;
+        B::template edge_eta4<C>(S, t, e4p, e4m);
+        edge = fma(e4p, (ucp - uc0) + (utp - utpc), edge);
+        edge -= t == 0 ? in.tau_xz : in.tau_yz;
+      } else {
+        real e4p, e4m;
+        B::template edge_eta4<C>(S, t, e4p, e4m);
+        edge = fma(e4p, (ucp - uc0) + (utp - utpc), edge);
+        edge = fma(e4m, (ucm - uc0) + (utc - ut0), edge);
+      }
+      conv4 = fma((ut0 + utc) + (utp + utpc), ucp - ucm, conv4);
+    }
+    real visc = fma(real(2), tcc, mul_rn(real(0.25), edge));
+    if (P.bulk) {
+      const real dm = C == 2 ? in.div : B::divsum(S, P, -cx, -cy, -cz);
+      visc = fma(S(F_ETA, 0, 0, 0), d0, visc);
+      visc = fma(-S(F_ETA, -cx, -cy, -cz), dm, visc);
+    }
+    const real st = -P.sigma * (S(F_PHI, 0, 0, 0) + S(F_PHI, -cx, -cy, -cz)) *
+                    (S(F_MU, 0, 0, 0) - S(F_MU, -cx, -cy, -cz));
+    const real grav = fma(real(0.5), rb2, -P.rho_ref);
+    real force = fma(visc, P.inv_dx2, -gradp);
+    force = fma(st, P.inv_2dx, force);
+    force = fma(grav, P.g[C], force);
+    const real conv = fma(uc0, S(FC, cx, cy, cz) - S(FC, -cx, -cy, -cz), mul_rn(real(0.25), conv4));
+    return fma(-conv, P.inv_2dx, fdiv(real(2) * force, rb2));
+  }
+};
+
 // One block: a TX x FLOW_K3_TY column of cells over the planes [kbeg, kend);
 // thread (tx, ty) computes the cells (i0 + tx, j0 + 2 ty + r), r = 0, 1.  The
 // two cells share most of their stencil, so the loads and sub-expressions
@@ -127,6 +237,20 @@ __global__ void __launch_bounds__(FLOW_NTHR, FLOW_MINB) flow3d_kernel(const __gr
   const real* smr = reinterpret_cast<const real*>(smraw);
   const int raw0 = (int)(R.raw - smr);
   const int cell0 = G::at(tx + 1, 2 * ty + 1);
+  using Ops = FlowOpsZ<real, RingTile<real, PAVG>>;
+  // the +z side terms of the cells of plane kbeg - 1 (planes kbeg - 1 and kbeg
+  // only), after every thread's writes of the two planes' out-of-domain cells
+  if (edge_tile || kbeg == 0 || kbeg + 1 >= nz) __syncthreads();
+  ZCarry<real> zc[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    RingTile<real, PAVG> S;
+    S.sm = smr;
+    S.P = &P;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) S.r[dz + 1] = raw0 + R.slot(kbeg - 1 + dz) * NRAW_FLOW * G::PE + cell0 + r * G::BX;
+    Ops::plus_z(S, P, Ops::divsum(S, P, 0, 0, 0), zc[r]);
+  }
   long long id = lin(P, i, ja, kbeg);
   for (int k = kbeg; k < kend; ++k, id += P.sz) {
     real q0v[2][4];
@@ -143,7 +267,6 @@ __global__ void __launch_bounds__(FLOW_NTHR, FLOW_MINB) flow3d_kernel(const __gr
     // stencil reads them; a plane that needed none is visible to every thread
     // after its own wait on the plane's barrier
     if (edge_tile || k + 1 >= nz) __syncthreads();
-    using Ops = FlowOps<real, 3, RingTile<real, PAVG>>;
     real out[2][4];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -153,11 +276,14 @@ __global__ void __launch_bounds__(FLOW_NTHR, FLOW_MINB) flow3d_kernel(const __gr
 #pragma unroll
       for (int dz = -1; dz <= 1; ++dz) S.r[dz + 1] = raw0 + R.slot(k + dz) * NRAW_FLOW * G::PE + cell0 + r * G::BX;
       const real D0 = Ops::divsum(S, P, 0, 0, 0);
+      ZCarry<real> zo;
+      Ops::plus_z(S, P, D0, zo);
       real L[4];
-      L[0] = Ops::rate_p(S, P, D0);
-      L[1] = Ops::template rate_vel<0>(S, P, D0);
-      L[2] = Ops::template rate_vel<1>(S, P, D0);
-      L[3] = Ops::template rate_vel<2>(S, P, D0);
+      L[0] = Ops::rate_p(S, P, D0, zc[r], zo);
+      L[1] = Ops::template rate_vel<0>(S, P, D0, zc[r], zo);
+      L[2] = Ops::template rate_vel<1>(S, P, D0, zc[r], zo);
+      L[3] = Ops::template rate_vel<2>(S, P, D0, zc[r], zo);
+      zc[r] = zo;
       // faces on a wall are never updated
       if (P.bc[0] != BC_PERIODIC && i == 0) L[1] = real(0);
       if (P.bc[1] != BC_PERIODIC && ja + r == 0) L[2] = real(0);
