@@ -12,16 +12,17 @@
 //      unless the CTA holds all its weights resident in shared memory.
 // The A operand of tap (dy, dx) is the same window read from a start address
 // shifted by (dy, dx) pixels: with 8-pixel tile rows, consecutive 8-row core
-// matrices of M sit one window row (160 bytes) apart for every tap.  One
-// thread issues the 9 tcgen05.mma (kind::f16, BF16 in, FP32 accumulator in
-// tensor memory) of a chunk and commits them to the chunk's mbarrier; a
-// stage is refilled only after that barrier completes.
+// matrices of M sit one window row (160 bytes) apart for every tap.  The 9
+// tcgen05.mma of a chunk (kind::f16, BF16 in, FP32 accumulator in tensor
+// memory) are issued by one thread and committed to the stage's mbarrier.
 //
-// The CTAs are persistent: CTA (x, y) takes the output-channel block y and
-// the tiles x, x + gridDim.x, ...; the chunks of its tiles form one
-// pipelined stream.  The accumulator is double-buffered in tensor memory, so
-// the epilogue of a tile (tcgen05.ld, bias, SiLU, BF16 NHWC stores) runs
-// while the tensor cores work on the next one.
+// The CTAs are persistent and warp-specialised: CTA (x, y) takes the
+// output-channel block y and the tiles x, x + gridDim.x, ...; the chunks of
+// its tiles stream through a ring of stages filled by two producer warps,
+// consumed by the MMA thread, and the double-buffered accumulator is drained
+// by four epilogue warps (tcgen05.ld, bias, SiLU, BF16 NHWC stores) while
+// the tensor cores work on the next tile.  The producers form their source
+// pointers once per tile, so that a chunk costs a thread a handful of copies.
 //
 // The forward input may be read as the nearest 2x upsampling of a tensor of
 // half the resolution (a.up), which fuses the decoder's upsampling into the
@@ -44,9 +45,6 @@ namespace {
 constexpr int TH = 16, TW = 8;              // output tile (M = 128 pixels)
 constexpr int WH = TH + 2, WW = TW + 2;     // input window with the halo
 constexpr int KC = 16;                      // channels per K chunk
-constexpr int NTHR = 128;
-constexpr int S = 4;                        // pipeline stages
-constexpr int PD = 2;                       // chunks loaded ahead
 constexpr int A_BYTES = 2 * WH * WW * 16;   // 5760
 constexpr int HEAD = 1024;                  // barriers and the tensor-memory slot
 constexpr int SMEM_MAX = 200 * 1024;
@@ -56,12 +54,6 @@ struct Cfg {
   static constexpr int BCHUNK = 9 * 2 * BN * 16;   // weights of one chunk
   static constexpr int TCOLS = 2 * BN < 32 ? 32 : 2 * BN;   // two accumulators
 };
-
-// shared memory of a launch: streaming B per stage, or resident weights of all chunks
-__host__ __device__ __forceinline__ int smem_bytes(int bn, int nchunks, bool resident) {
-  const int bchunk = 9 * 2 * bn * 16;
-  return 1024 + HEAD + S * (A_BYTES + (resident ? 0 : bchunk)) + (resident ? nchunks * bchunk : 0);
-}
 
 __device__ __forceinline__ int wrapm(int v, int n) {
   int r = v % n;
@@ -135,38 +127,152 @@ __device__ __forceinline__ TileGeom tile_of(int t, int tiles_x, int tiles_y) {
   return g;
 }
 
-// MODE 0: forward  y = act(conv(x) + bias) (and z = conv(x) + bias if a.z);
-// MODE 1: data gradient  dx (+)= conv^T(dz)
+// ---------------------------------------------------------------------------
+// the warp-specialised form: each warp has one role
+// ---------------------------------------------------------------------------
+//   warps 0-3: epilogue; warp w reads tensor-memory lanes 32w .. 32w + 31
+//              (the pixels of its quarter of the tile), applies bias and SiLU
+//              and stores BF16;
+//   warps 4-5: producers; they stage the input window and (unless resident)
+//              the weights of each K chunk with cp.async into a ring of ns
+//              stages; ns - 2 chunks after issuing one they wait for its
+//              copies, fence them to the async proxy and arrive on the
+//              stage's full barrier;
+//   warp 6:    one thread issues the chunk's tcgen05.mma and commits them to
+//              the stage's empty barrier, and at a tile's last chunk to the
+//              accumulator's full barrier.
+// The accumulator is double-buffered in tensor memory; the epilogue frees a
+// buffer (its empty barrier) as soon as it has read it.  Every wait is
+// bounded: a wait that runs out sets an abort flag that every role polls, and
+// the CTA records the error, lets its MMAs finish and frees its tensor memory.
+constexpr int EPI_WARPS = 4, PROD_WARPS = 2;
+constexpr int NTHR = 32 * (EPI_WARPS + PROD_WARPS + 1);
+constexpr int MMA_WARP = EPI_WARPS + PROD_WARPS;
+constexpr int SMIN = 4, SMAX = 8;  // stages of the ring (chosen per launch)
+
+__host__ __device__ __forceinline__ int smem_bytes(int bn, int nchunks, bool resident, int ns) {
+  const int bchunk = 9 * 2 * bn * 16;
+  return 1024 + HEAD + ns * (A_BYTES + (resident ? 0 : bchunk)) + (resident ? nchunks * bchunk : 0);
+}
+
+// wait until at most n of this thread's cp.async groups are pending (n in 0 .. SMAX - 2)
+__device__ __forceinline__ void cp_async_wait_n(int n) {
+  switch (n) {
+    case 0: cp_async_wait<0>(); break;
+    case 1: cp_async_wait<1>(); break;
+    case 2: cp_async_wait<2>(); break;
+    case 3: cp_async_wait<3>(); break;
+    case 4: cp_async_wait<4>(); break;
+    case 5: cp_async_wait<5>(); break;
+    default: cp_async_wait<6>(); break;
+  }
+}
+
+// BF16 results of one tile from its accumulator at acc (columns acc .. acc + BN):
+// forward y = act(z + bias) (and z), data gradient dx (+)= value; one pixel
+// per epilogue thread (lane m of the tile)
+template <int MODE, int BN>
+__device__ __forceinline__ void epilogue_tile(const ConvArgs& a, uint32_t acc, const TileGeom& tg, int n0, int m,
+                                            int warp) {
+  const int y = tg.y0 + m / TW, x = tg.x0 + m % TW;
+  const bool valid = y < a.H && x < a.W;
+  const size_t p = ((size_t)tg.b * a.H + (valid ? y : 0)) * a.W + (valid ? x : 0);
+#pragma unroll 1
+  for (int j = 0; j < BN; j += 16) {
+    uint32_t v[16];
+    const uint32_t ta = acc + ((uint32_t)(warp * 32) << 16) + (uint32_t)j;
+    tmem_ld8(ta, v);
+    tmem_ld8(ta + 8, v + 8);
+    tmem_wait_ld();
+    if (!valid) continue;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      const int n = n0 + j + 8 * hh;
+      float f[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) f[e] = __uint_as_float(v[8 * hh + e]);
+      if (MODE == 0) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) f[e] += a.bias[n + e];  // the bias sits at any offset of the parameters
+        if (a.z) {
+          uint4 zz;
+          __nv_bfloat162* zp = reinterpret_cast<__nv_bfloat162*>(&zz);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) zp[e] = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
+          *reinterpret_cast<uint4*>(a.z + p * a.cout + n) = zz;
+        }
+        uint4 yv;
+        __nv_bfloat162* yp = reinterpret_cast<__nv_bfloat162*>(&yv);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float u0 = a.act ? silu_f(f[2 * e]) : f[2 * e];
+          const float u1 = a.act ? silu_f(f[2 * e + 1]) : f[2 * e + 1];
+          yp[e] = __floats2bfloat162_rn(u0, u1);
+        }
+        *reinterpret_cast<uint4*>(a.y + p * a.ldy + a.yoff + n) = yv;
+      } else {
+        __nv_bfloat16* dst = a.dx + p * a.lddx + a.dxoff + n;
+        if (a.accumulate) {
+          const uint4 old = *reinterpret_cast<const uint4*>(dst);
+          const __nv_bfloat162* op = reinterpret_cast<const __nv_bfloat162*>(&old);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 o = __bfloat1622float2(op[e]);
+            f[2 * e] += o.x;
+            f[2 * e + 1] += o.y;
+          }
+        }
+        uint4 dd;
+        __nv_bfloat162* dp = reinterpret_cast<__nv_bfloat162*>(&dd);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) dp[e] = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
+        *reinterpret_cast<uint4*>(dst) = dd;
+      }
+    }
+  }
+}
+
 template <int MODE, int BN>
 __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, int tiles_x, int tiles_y, int ntiles,
-                                                         int resident) {
+                                                            int resident, int ns) {
   using C = Cfg<BN>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm);   // ns: a stage's copies landed (the producers arrive)
+  uint64_t* empty = full + SMAX;                   // ns: a stage's MMAs finished (tcgen05.commit)
+  uint64_t* accf = empty + SMAX;                     // 2: an accumulator's tile is complete (tcgen05.commit)
+  uint64_t* acce = accf + 2;                          // 2: an accumulator has been read (the epilogue arrives)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 512);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + 520);
   unsigned char* stages = sm + HEAD;
   const int stage_bytes = A_BYTES + (resident ? 0 : C::BCHUNK);
-  unsigned char* wres = stages + S * stage_bytes;   // resident weights [chunk][tap][half][n][8]
+  unsigned char* wres = stages + ns * stage_bytes;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   const int n0 = blockIdx.y * BN;
   const int H = a.H, W = a.W;
-  const int Hs = a.up ? H >> 1 : H, Ws = a.up ? W >> 1 : W;   // stored size of the source
-  const int Cin = MODE == 0 ? a.cin : a.cout;                  // channels of the K dimension
+  const int Hs = a.up ? H >> 1 : H, Ws = a.up ? W >> 1 : W;
+  const int Cin = MODE == 0 ? a.cin : a.cout;
   const __nv_bfloat16* src = MODE == 0 ? a.x : a.dz;
   const int lds = MODE == 0 ? a.ldx : a.ldz;
   const int soff = MODE == 0 ? a.xoff : 0;
   const __nv_bfloat16* wsrc = MODE == 0 ? a.wt : a.wd;
-  const int Kw = 9 * Cin;                                      // row length of the weight matrix
+  const int Kw = 9 * Cin;
   const int nchunks = Cin / KC;
   const int nitems = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const int G = nitems * nchunks;                              // chunks of this CTA
+  const int G = nitems * nchunks;
 
   if (tid == 0) {
-    for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < ns; ++s) {
+      mbar_init(&full[s], 32 * PROD_WARPS);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 32 * EPI_WARPS);
+    }
+    *abort_flag = 0;
     fence_mbar_init();
-    fence_proxy_async_smem();
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -179,153 +285,137 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, int ti
   tc_fence_after();
   const uint32_t tmem = *tslot;
 
-  auto load_weights = [&](unsigned char* B, int c0) {
-    for (int q = tid; q < 9 * 2 * BN; q += NTHR) {
-      const int h = q & 1, r = q >> 1;
-      const int tap = r / BN, n = r - tap * BN;
-      cp_async16(B + ((tap * 2 + h) * BN + n) * 16, wsrc + (size_t)(n0 + n) * Kw + tap * Cin + c0 + 8 * h);
-    }
-  };
-  auto load_chunk = [&](int g) {
-    const int item = g / nchunks, k = g - item * nchunks;
-    const TileGeom tg = tile_of(blockIdx.x + item * gridDim.x, tiles_x, tiles_y);
-    unsigned char* A = stages + (g % S) * stage_bytes;
-    const int c0 = k * KC;
-    for (int q = tid; q < 2 * WH * WW; q += NTHR) {
-      const int h = q & 1, r = q >> 1;
-      const int wy = r / WW, wx = r - wy * WW;
-      int yy = wrapm(tg.y0 + wy - 1, H), xx = wrapm(tg.x0 + wx - 1, W);
-      if (a.up) { yy >>= 1; xx >>= 1; }
-      const __nv_bfloat16* gp = src + ((size_t)(tg.b * Hs + yy) * Ws + xx) * lds + soff + c0 + 8 * h;
-      cp_async16(A + ((h * WH + wy) * WW + wx) * 16, gp);
-    }
-    if (!resident) load_weights(A + A_BYTES, c0);
-  };
-
-  auto epilogue = [&](int item) {
-    const TileGeom tg = tile_of(blockIdx.x + item * gridDim.x, tiles_x, tiles_y);
-    const uint32_t acc = tmem + (uint32_t)((item & 1) * BN);
-    const int m = warp * 32 + lane;
-    const int y = tg.y0 + m / TW, x = tg.x0 + m % TW;
-    const bool valid = y < H && x < W;
-    const size_t p = ((size_t)tg.b * H + (valid ? y : 0)) * W + (valid ? x : 0);
-#pragma unroll 1
-    for (int j = 0; j < BN; j += 16) {
-      uint32_t v[16];
-      const uint32_t ta = acc + ((uint32_t)(warp * 32) << 16) + (uint32_t)j;
-      tmem_ld8(ta, v);
-      tmem_ld8(ta + 8, v + 8);
-      tmem_wait_ld();
-      if (!valid) continue;
+  if (warp >= EPI_WARPS && warp < MMA_WARP) {
+    // ---- producers ----
+    // thread pt copies the 8-channel half hq of the window entries r0 + 32 j
+    // and, for the weights, of output channels r0 + 32 jj: its source
+    // pointers are formed once per tile (window) or once per launch
+    // (weights), so a chunk costs it only the copies and pointer increments
+    const int pt = tid - 32 * EPI_WARPS;
+    constexpr int NP = 32 * PROD_WARPS;
+    static_assert(NP == 64, "two producer warps: 32 window entries per pass");
+    constexpr int NWIN = (WH * WW + 31) / 32;
+    const int hq = pt & 1, r0 = pt >> 1;
+    auto load_weights = [&](unsigned char* B, int c0) {
+      if constexpr (BN >= 32) {
+        const __nv_bfloat16* wb = wsrc + (size_t)(n0 + r0) * Kw + c0 + 8 * hq;
+        unsigned char* db = B + (hq * BN + r0) * 16;
 #pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
-        const int n = n0 + j + 8 * hh;
-        float f[8];
+        for (int tap = 0; tap < 9; ++tap)
 #pragma unroll
-        for (int e = 0; e < 8; ++e) f[e] = __uint_as_float(v[8 * hh + e]);
-        if (MODE == 0) {
-#pragma unroll
-          for (int e = 0; e < 8; ++e) f[e] += a.bias[n + e];
-          if (a.z) {
-            uint4 zz;
-            __nv_bfloat162* zp = reinterpret_cast<__nv_bfloat162*>(&zz);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) zp[e] = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
-            *reinterpret_cast<uint4*>(a.z + p * a.cout + n) = zz;
-          }
-          uint4 yv;
-          __nv_bfloat162* yp = reinterpret_cast<__nv_bfloat162*>(&yv);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float u0 = a.act ? silu_f(f[2 * e]) : f[2 * e];
-            const float u1 = a.act ? silu_f(f[2 * e + 1]) : f[2 * e + 1];
-            yp[e] = __floats2bfloat162_rn(u0, u1);
-          }
-          *reinterpret_cast<uint4*>(a.y + p * a.ldy + a.yoff + n) = yv;
-        } else {
-          __nv_bfloat16* dst = a.dx + p * a.lddx + a.dxoff + n;
-          if (a.accumulate) {
-            const uint4 old = *reinterpret_cast<const uint4*>(dst);
-            const __nv_bfloat162* op = reinterpret_cast<const __nv_bfloat162*>(&old);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float2 o = __bfloat1622float2(op[e]);
-              f[2 * e] += o.x;
-              f[2 * e + 1] += o.y;
-            }
-          }
-          uint4 dd;
-          __nv_bfloat162* dp = reinterpret_cast<__nv_bfloat162*>(&dd);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) dp[e] = __floats2bfloat162_rn(f[2 * e], f[2 * e + 1]);
-          *reinterpret_cast<uint4*>(dst) = dd;
+          for (int jj = 0; jj < BN / 32; ++jj)
+            cp_async16(db + (tap * 2 * BN + 32 * jj) * 16, wb + (size_t)jj * 32 * Kw + tap * Cin);
+      } else {
+        for (int q = pt; q < 9 * 2 * BN; q += NP) {
+          const int h = q & 1, r = q >> 1;
+          const int tap = r / BN, n = r - tap * BN;
+          cp_async16(B + ((tap * 2 + h) * BN + n) * 16, wsrc + (size_t)(n0 + n) * Kw + tap * Cin + c0 + 8 * h);
         }
       }
-    }
-  };
-
-  // prologue: the resident weights join the first group
-  if (resident && G > 0)
-    for (int k = 0; k < nchunks; ++k) load_weights(wres + k * C::BCHUNK, k * KC);
-  for (int g = 0; g < PD; ++g) {
-    if (g < G) load_chunk(g);
-    cp_async_commit();
-  }
-
-  bool bad = false;
-  for (int g = 0; g < G; ++g) {
-    const int gn = g + PD;
-    if (gn < G) {
-      bool to = false;
-      if (gn >= S) to = !mbar_wait_bounded(&bar[gn % S], (uint32_t)(((gn - S) / S) & 1), WAIT_CYCLES);
-      if (__syncthreads_or(to)) { bad = true; break; }
-      load_chunk(gn);
-    }
-    cp_async_commit();
-    cp_async_wait<PD>();
-    fence_proxy_async_smem();
-    __syncthreads();
-    const int item = g / nchunks, k = g - item * nchunks;
-    if (tid == 0) {
-      tc_fence_after();
-      const int s = g % S;
-      const uint32_t Aa = smem_u32(stages + s * stage_bytes);
-      const uint32_t Ba = resident ? smem_u32(wres + k * C::BCHUNK) : Aa + A_BYTES;
-      const uint32_t acc = tmem + (uint32_t)((item & 1) * BN);
-#pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        int dy = tap / 3 - 1, dx = tap % 3 - 1;
-        if (MODE == 1) { dy = -dy; dx = -dx; }
-        const uint64_t ad = sdesc(Aa + (uint32_t)(((dy + 1) * WW + (dx + 1)) * 16), WH * WW * 16, WW * 16);
-        const uint64_t bd = sdesc(Ba + (uint32_t)(tap * 2 * BN * 16), BN * 16, 128);
-        mma_tc(acc, ad, bd, idesc_bf16<BN>(), (k > 0 || tap > 0) ? 1u : 0u);
+    };
+    const __nv_bfloat16* wp[NWIN];  // this tile's window sources of this thread (channel 0 of its half)
+    // the resident weights join the first chunk's group: the first full barrier covers them
+    if (resident && G > 0)
+      for (int k = 0; k < nchunks; ++k) load_weights(wres + k * C::BCHUNK, k * KC);
+    const int lag = ns - 2; // chunks issued after a chunk before its copies are awaited
+    int issued = 0, handed = 0;
+    for (int g = 0; g < G; ++g) {
+      if (*abort_flag) break;
+      const int s = g % ns;
+      if (g >= ns && !mbar_wait_bounded(&empty[s], (uint32_t)(((g - ns) / ns) & 1), WAIT_CYCLES)) {
+        *abort_flag = 1;
+        break;
       }
-      mma_commit(&bar[s]);
+      const int item = g / nchunks, k = g - item * nchunks;
+      if (k == 0) {
+        const TileGeom tg = tile_of(blockIdx.x + item * gridDim.x, tiles_x, tiles_y);
+#pragma unroll
+        for (int j = 0; j < NWIN; ++j) {
+          const int r = r0 + 32 * j;
+          const int wy = r / WW, wx = r - wy * WW;
+          int yy = wrapm(tg.y0 + wy - 1, H), xx = wrapm(tg.x0 + wx - 1, W);
+          if (a.up) { yy >>= 1; xx >>= 1; }
+          wp[j] = src + ((size_t)(tg.b * Hs + yy) * Ws + xx) * lds + soff + 8 * hq;
+        }
+      }
+      unsigned char* A = stages + s * stage_bytes;
+      const int c0 = k * KC;
+      unsigned char* da = A + (hq * WH * WW + r0) * 16;
+#pragma unroll
+      for (int j = 0; j < NWIN; ++j)
+        if (r0 + 32 * j < WH * WW) cp_async16(da + 512 * j, wp[j] + c0);
+      if (!resident) load_weights(A + A_BYTES, c0);
+      cp_async_commit();
+      issued = g + 1;
+      if (g >= lag) {
+        // chunk g - lag: this thread's copies have landed; hand them to the tensor cores
+        cp_async_wait_n(lag);
+        fence_proxy_async_smem();
+        mbar_arrive(&full[(g - lag) % ns]);
+        handed = g - lag + 1;
+      }
     }
-    if (k == 0 && item > 0) {
-      // the previous tile is fully issued: its epilogue overlaps this tile's MMAs
-      const bool ok = mbar_wait_bounded(&bar[(g - 1) % S], (uint32_t)(((g - 1) / S) & 1), WAIT_CYCLES);
-      if (__syncthreads_or(!ok)) { bad = true; break; }
+    cp_async_wait<0>();
+    fence_proxy_async_smem();
+    for (int g = handed; g < issued; ++g) mbar_arrive(&full[g % ns]);
+  } else if (warp == MMA_WARP) {
+    // ---- the MMA issuer ----
+    if (lane == 0 && G > 0) {
+      bool ok = true;
+      for (int g = 0; g < G; ++g) {
+        if (*abort_flag) { ok = false; break; }
+        const int item = g / nchunks, k = g - item * nchunks, s = g % ns;
+        const int buf = item & 1;
+        // the buffer's tile of two items ago has been read by the epilogue
+        if (k == 0 && item >= 2 && !mbar_wait_bounded(&acce[buf], (uint32_t)(((item - 2) >> 1) & 1), WAIT_CYCLES)) {
+          ok = false;
+          break;
+        }
+        if (!mbar_wait_bounded(&full[s], (uint32_t)((g / ns) & 1), WAIT_CYCLES)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t Aa = smem_u32(stages + s * stage_bytes);
+        const uint32_t Ba = resident ? smem_u32(wres + k * C::BCHUNK) : Aa + A_BYTES;
+        const uint32_t acc = tmem + (uint32_t)(buf * BN);
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+          int dy = tap / 3 - 1, dx = tap % 3 - 1;
+          if (MODE == 1) { dy = -dy; dx = -dx; }
+          const uint64_t ad = sdesc(Aa + (uint32_t)(((dy + 1) * WW + (dx + 1)) * 16), WH * WW * 16, WW * 16);
+          const uint64_t bd = sdesc(Ba + (uint32_t)(tap * 2 * BN * 16), BN * 16, 128);
+          mma_tc(acc, ad, bd, idesc_bf16<BN>(), (k > 0 || tap > 0) ? 1u : 0u);
+        }
+        mma_commit(&empty[s]);
+        if (k == nchunks - 1) mma_commit(&accf[buf]);
+      }
+      if (!ok) *abort_flag = 1;
+    }
+  } else {
+    // ---- epilogue: warp w holds tensor-memory lanes 32w .. 32w + 31 ----
+    for (int item = 0; item < nitems; ++item) {
+      const int buf = item & 1;
+      const bool ok = mbar_wait_bounded(&accf[buf], (uint32_t)((item >> 1) & 1), WAIT_CYCLES);
+      // every lane of the warp takes the same branch before the aligned tensor-memory loads
+      if (!__all_sync(0xffffffffu, ok ? 1 : 0) || __any_sync(0xffffffffu, *abort_flag != 0)) {
+        *abort_flag = 1;
+        break;
+      }
       tc_fence_after();
-      epilogue(item - 1);
+      const TileGeom tg = tile_of(blockIdx.x + item * gridDim.x, tiles_x, tiles_y);
+      epilogue_tile<MODE, BN>(a, tmem + (uint32_t)(buf * BN), tg, n0, warp * 32 + lane, warp);
       tc_fence_before();
+      mbar_arrive(&acce[buf]);
     }
   }
-  cp_async_wait<0>();
 
-  bool done = G == 0;
-  if (!bad && G > 0) done = mbar_wait_bounded(&bar[(G - 1) % S], (uint32_t)(((G - 1) / S) & 1), WAIT_CYCLES);
-  if (__syncthreads_or(!done)) {
-    if (tid == 0 && a.err) atomicExch(a.err, 1);
-    // give the MMAs issued so far a bounded time to finish before the memory is freed
-    const long long t0 = clock64();
-    while (clock64() - t0 < 1000000) {}
-  } else if (G > 0) {
-    tc_fence_after();
-    epilogue(nitems - 1);
-  }
   tc_fence_before();
   __syncthreads();
+  if (*abort_flag) {
+    if (tid == 0 && a.err) atomicExch(a.err, 1);
+    // give the MMAs issued so far a bounded time to finish before the tensor memory is freed
+    const long long t0 = clock64();
+    while (clock64() - t0 < 1000000) {}
+  }
+  tc_fence_after();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TCOLS) : "memory");
   }
@@ -341,27 +431,39 @@ cudaError_t launch_tc(const ConvArgs& a, int tiles_x, int tiles_y, int ntiles, i
     attr_set = 1;
   }
   const int nch = (MODE == 0 ? a.cin : a.cout) / KC;
-  // resident CTAs per SM, from the SM's shared memory (with the per-block
-  // reservation), its 512 tensor-memory columns and its 2048 threads; the
-  // weights stay resident in shared memory only if that leaves two CTAs per SM
   int dev = 0, nsm = 152, sm_smem = 233472, reserved = 1024;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-  const int smem_res = smem_bytes(BN, nch, true);
-  const bool resident = smem_res <= SMEM_MAX && sm_smem / (smem_res + reserved) >= 2;
-  const int smem = smem_bytes(BN, nch, resident);
-  int occ = sm_smem / (smem + reserved);
-  if (occ > 512 / Cfg<BN>::TCOLS) occ = 512 / Cfg<BN>::TCOLS;
-  if (occ > 2048 / NTHR) occ = 2048 / NTHR;
-  if (occ < 1) occ = 1;
+  // two CTAs per SM where the tensor memory allows it (one's epilogue and
+  // start-up overlap the other's MMAs); the weights stay resident if that
+  // still leaves the minimum ring, else they stream through the ring, which
+  // takes as many stages as fit (up to SMAX)
+  const int tm_occ = 512 / Cfg<BN>::TCOLS;
+  bool resident = false;
+  int ns = 0, occ = 1;
+  for (int want = tm_occ >= 2 ? 2 : 1; want >= 1 && ns == 0; --want) {
+    int budget = sm_smem / want - reserved;
+    if (budget > SMEM_MAX) budget = SMEM_MAX;
+    if (smem_bytes(BN, nch, true, SMIN) <= budget) {
+      resident = true;
+      ns = SMIN;
+      while (ns < SMAX && smem_bytes(BN, nch, true, ns + 1) <= budget) ++ns;
+    } else if (smem_bytes(BN, nch, false, SMIN) <= budget) {
+      ns = SMIN;
+      while (ns < SMAX && smem_bytes(BN, nch, false, ns + 1) <= budget) ++ns;
+    }
+    occ = want;
+  }
+  if (ns == 0) return cudaErrorInvalidValue;
+  const int smem = smem_bytes(BN, nch, resident, ns);
   const int nblk_n = nout / BN;
   long long gx = ((long long)occ * nsm + nblk_n - 1) / nblk_n;
   if (gx > ntiles) gx = ntiles;
   if (gx < 1) gx = 1;
   dim3 grid((unsigned)gx, (unsigned)nblk_n);
-  k<<<grid, NTHR, smem, s>>>(a, tiles_x, tiles_y, ntiles, resident ? 1 : 0);
+  k<<<grid, NTHR, smem, s>>>(a, tiles_x, tiles_y, ntiles, resident ? 1 : 0, ns);
   return cudaGetLastError();
 }
 
@@ -391,7 +493,7 @@ bool conv_tc_supported(const ConvArgs& a, int mode) {
   if (mode == 1 && a.up) return false;
   const int ld = mode == 0 ? a.ldx : a.ldz, off = mode == 0 ? a.xoff : 0;
   const int ldo = mode == 0 ? a.ldy : a.lddx, offo = mode == 0 ? a.yoff : a.dxoff;
-  if (smem_bytes(16, kin / KC, false) > SMEM_MAX) return false;
+  if (smem_bytes(16, kin / KC, false, SMIN) > SMEM_MAX) return false;
   return ld % 8 == 0 && off % 8 == 0 && ldo % 8 == 0 && offo % 8 == 0;
 }
 
