@@ -20,6 +20,7 @@ import pytest
 from paper_2011_00814_gb300 import surrogate
 
 K = 64
+DISP_PER_DRIFT = 100.0
 
 
 class FakeSolver:
@@ -43,9 +44,18 @@ class FakeSolver:
             return (1e300, 1.0)
         return ((float(buf.flat[1]) - self.drift) ** 2, 1.0)
 
+    def interface_distance(self, buf):
+        # interface displacement in cells: DISP_PER_DRIFT cells per unit of drift
+        if int(buf.flat[0]) != self.t:
+            return (math.inf, math.inf)
+        d = abs(float(buf.flat[1]) - self.drift) * DISP_PER_DRIFT
+        return (d, d)
+
 
 class FakeNet:
     """Advances the packed state by K steps and adds errs[i] on its i-th call."""
+
+    check_tol, check_tol_disp = 2e-2, 1.0
 
     def __init__(self, errs):
         self.K, self.n = K, 2
@@ -99,6 +109,27 @@ def test_failed_check_rolls_back_and_cools_down(numpy_buffers):
     # kept: three network results of window 1 and three of window 4
     assert sol.drift == pytest.approx(3 * 1e-3 + 3 * 2e-3)
     assert st.max_check_l2 == pytest.approx(5e-2)
+
+
+def test_interface_displacement_alone_fails_a_check(numpy_buffers):
+    # every check's phi error (1e-2) is within tol = 2e-2, but its interface
+    # displacement (1 cell) exceeds tol_disp = 0.5: each check fails, its
+    # window is recomputed by the solver and none of the network's results is kept
+    errs = [0.0, 0.0, 0.0, 1e-2] * 2
+    st, sol, net = _run(errs, 12, check_every=4, tol=2e-2, tol_disp=0.5, cooldown=1)
+    assert st.checks == 2 and st.failures == 2
+    assert st.check_l2 == pytest.approx([1e-2, 1e-2])
+    assert st.check_disp == pytest.approx([1.0, 1.0])
+    assert sol.drift == 0.0
+    # the same run with the displacement tolerance at 2 cells keeps every window
+    st, sol, net = _run(errs + [0.0] * 4, 12, check_every=4, tol=2e-2, tol_disp=2.0, cooldown=1)
+    assert st.failures == 0 and st.checks == 3
+
+
+def test_defaults_come_from_the_surrogate(numpy_buffers):
+    net, sol = FakeNet([0.0] * 4), FakeSolver()
+    c = surrogate.Controller(net, sol)
+    assert (c.tol, c.tol_disp) == (FakeNet.check_tol, FakeNet.check_tol_disp)
 
 
 def test_nan_check_counts_as_a_failure(numpy_buffers):
