@@ -33,6 +33,7 @@
 // frees its tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
 
 #include "nn.h"
@@ -63,11 +64,8 @@ __device__ __forceinline__ int wrapm(int v, int n) {
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
+// wait until every cp.async this thread has issued has completed
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -135,11 +133,13 @@ __device__ __forceinline__ TileGeom tile_of(int t, int tiles_x, int tiles_y) {
 //              and stores BF16;
 //   warps 4-5: producers; they stage the input window and (unless resident)
 //              the weights of each K chunk with cp.async into a ring of ns
-//              stages; ns - 2 chunks after issuing one they wait for its
-//              copies, fence them to the async proxy and arrive on the
-//              stage's full barrier;
-//   warp 6:    one thread issues the chunk's tcgen05.mma and commits them to
-//              the stage's empty barrier, and at a tile's last chunk to the
+//              stages; each thread's copies arrive on the stage's full
+//              barrier by themselves when they land (cp.async.mbarrier.arrive
+//              .noinc), so a producer waits only for a free stage and keeps up
+//              to ns chunks in flight;
+//   warp 6:    one thread waits for a full stage, fences it to the async
+//              proxy, issues the chunk's tcgen05.mma and commits them to the
+//              stage's empty barrier, and at a tile's last chunk to the
 //              accumulator's full barrier.
 // The accumulator is double-buffered in tensor memory; the epilogue frees a
 // buffer (its empty barrier) as soon as it has read it.  Every wait is
@@ -148,24 +148,18 @@ __device__ __forceinline__ TileGeom tile_of(int t, int tiles_x, int tiles_y) {
 constexpr int EPI_WARPS = 4, PROD_WARPS = 2;
 constexpr int NTHR = 32 * (EPI_WARPS + PROD_WARPS + 1);
 constexpr int MMA_WARP = EPI_WARPS + PROD_WARPS;
-constexpr int SMIN = 4, SMAX = 8;  // stages of the ring (chosen per launch)
+constexpr int SMIN = 3, SMAX = 8;  // stages of the ring (chosen per launch)
+constexpr int MAX_OCC = 2;         // CTAs per SM at most
 
 __host__ __device__ __forceinline__ int smem_bytes(int bn, int nchunks, bool resident, int ns) {
   const int bchunk = 9 * 2 * bn * 16;
   return 1024 + HEAD + ns * (A_BYTES + (resident ? 0 : bchunk)) + (resident ? nchunks * bchunk : 0);
 }
 
-// wait until at most n of this thread's cp.async groups are pending (n in 0 .. SMAX - 2)
-__device__ __forceinline__ void cp_async_wait_n(int n) {
-  switch (n) {
-    case 0: cp_async_wait<0>(); break;
-    case 1: cp_async_wait<1>(); break;
-    case 2: cp_async_wait<2>(); break;
-    case 3: cp_async_wait<3>(); break;
-    case 4: cp_async_wait<4>(); break;
-    case 5: cp_async_wait<5>(); break;
-    default: cp_async_wait<6>(); break;
-  }
+// the mbarrier receives one arrival (counted in its expected count, "noinc")
+// once every cp.async this thread has issued so far has completed
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // BF16 results of one tile from its accumulator at acc (columns acc .. acc + BN):
@@ -233,8 +227,8 @@ __device__ __forceinline__ void epilogue_tile(const ConvArgs& a, uint32_t acc, c
 }
 
 template <int MODE, int BN>
-__global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, int tiles_x, int tiles_y, int ntiles,
-                                                            int resident, int ns) {
+__global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, const __grid_constant__ CUtensorMap wmap,
+                                                       int tiles_x, int tiles_y, int ntiles, int resident, int ns) {
   using C = Cfg<BN>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -242,6 +236,7 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, int ti
   uint64_t* empty = full + SMAX;                   // ns: a stage's MMAs finished (tcgen05.commit)
   uint64_t* accf = empty + SMAX;                     // 2: an accumulator's tile is complete (tcgen05.commit)
   uint64_t* acce = accf + 2;                          // 2: an accumulator has been read (the epilogue arrives)
+  uint64_t* wbar = acce + 2;                          // the resident weights have landed
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + 512);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + 520);
   unsigned char* stages = sm + HEAD;
@@ -256,8 +251,6 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, int ti
   const __nv_bfloat16* src = MODE == 0 ? a.x : a.dz;
   const int lds = MODE == 0 ? a.ldx : a.ldz;
   const int soff = MODE == 0 ? a.xoff : 0;
-  const __nv_bfloat16* wsrc = MODE == 0 ? a.wt : a.wd;
-  const int Kw = 9 * Cin;
   const int nchunks = Cin / KC;
   const int nitems = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int G = nitems * nchunks;
@@ -271,6 +264,7 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, int ti
       mbar_init(&accf[b], 1);
       mbar_init(&acce[b], 32 * EPI_WARPS);
     }
+    mbar_init(wbar, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -287,46 +281,41 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, int ti
 
   if (warp >= EPI_WARPS && warp < MMA_WARP) {
     // ---- producers ----
-    // thread pt copies the 8-channel half hq of the window entries r0 + 32 j
-    // and, for the weights, of output channels r0 + 32 jj: its source
-    // pointers are formed once per tile (window) or once per launch
-    // (weights), so a chunk costs it only the copies and pointer increments
+    // thread pt copies the 8-channel half hq of the window entries r0 + 32 j,
+    // from source pointers formed once per tile, so that a chunk costs it a
+    // handful of copies.  The weights of a chunk are 18 TMA boxes (9 taps x
+    // 2 halves) of 8 channels x BN output channels, each landing as one
+    // [n][8] block of core matrices, issued by lanes 0-17 of the first
+    // producer warp.
     const int pt = tid - 32 * EPI_WARPS;
     constexpr int NP = 32 * PROD_WARPS;
     static_assert(NP == 64, "two producer warps: 32 window entries per pass");
     constexpr int NWIN = (WH * WW + 31) / 32;
     const int hq = pt & 1, r0 = pt >> 1;
-    auto load_weights = [&](unsigned char* B, int c0) {
-      if constexpr (BN >= 32) {
-        const __nv_bfloat16* wb = wsrc + (size_t)(n0 + r0) * Kw + c0 + 8 * hq;
-        unsigned char* db = B + (hq * BN + r0) * 16;
-#pragma unroll
-        for (int tap = 0; tap < 9; ++tap)
-#pragma unroll
-          for (int jj = 0; jj < BN / 32; ++jj)
-            cp_async16(db + (tap * 2 * BN + 32 * jj) * 16, wb + (size_t)jj * 32 * Kw + tap * Cin);
-      } else {
-        for (int q = pt; q < 9 * 2 * BN; q += NP) {
-          const int h = q & 1, r = q >> 1;
-          const int tap = r / BN, n = r - tap * BN;
-          cp_async16(B + ((tap * 2 + h) * BN + n) * 16, wsrc + (size_t)(n0 + n) * Kw + tap * Cin + c0 + 8 * h);
-        }
+    // the weights of chunk c0 into B ([tap][half][n][8]), counted on bar: box
+    // q = 2 tap + h is issued by lane q mod 32 of the first producer warp
+    auto load_weights = [&](unsigned char* B, int c0, uint64_t* bar) {
+      if (pt < 18) {
+        const int tap = pt >> 1, h = pt & 1;
+        tma_load_2d(B + pt * BN * 16, &wmap, tap * Cin + c0 + 8 * h, n0, bar);
       }
     };
     const __nv_bfloat16* wp[NWIN];  // this tile's window sources of this thread (channel 0 of its half)
-    // the resident weights join the first chunk's group: the first full barrier covers them
-    if (resident && G > 0)
-      for (int k = 0; k < nchunks; ++k) load_weights(wres + k * C::BCHUNK, k * KC);
-    const int lag = ns - 2; // chunks issued after a chunk before its copies are awaited
-    int issued = 0, handed = 0;
+    if (resident && G > 0 && pt < 32) {
+      if (pt == 0) mbar_arrive_expect_tx(wbar, (uint32_t)(nchunks * C::BCHUNK));
+      __syncwarp();  // the bytes are announced before any of them can land
+      for (int kk = 0; kk < nchunks; ++kk) load_weights(wres + kk * C::BCHUNK, kk * KC, wbar);
+    }
+    int s = 0, k = 0, item = 0;
+    uint32_t epar = 1;  // parity of the empty phase a stage's next use waits for (none in the first round)
     for (int g = 0; g < G; ++g) {
-      if (*abort_flag) break;
-      const int s = g % ns;
-      if (g >= ns && !mbar_wait_bounded(&empty[s], (uint32_t)(((g - ns) / ns) & 1), WAIT_CYCLES)) {
+      // the warp leaves together (its lanes meet at __syncwarp below)
+      bool stop = *abort_flag != 0;
+      if (!stop && g >= ns) stop = !mbar_wait_bounded_sleep(&empty[s], epar, WAIT_CYCLES);
+      if (__any_sync(0xffffffffu, stop)) {
         *abort_flag = 1;
         break;
       }
-      const int item = g / nchunks, k = g - item * nchunks;
       if (k == 0) {
         const TileGeom tg = tile_of(blockIdx.x + item * gridDim.x, tiles_x, tiles_y);
 #pragma unroll
@@ -340,52 +329,63 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, int ti
       }
       unsigned char* A = stages + s * stage_bytes;
       const int c0 = k * KC;
+      if (!resident && pt < 32) {
+        // the bytes are announced before any of them can land, and before this
+        // thread's own arrival below can complete the phase
+        if (pt == 0) mbar_expect_tx(&full[s], (uint32_t)C::BCHUNK);
+        __syncwarp();
+        load_weights(A + A_BYTES, c0, &full[s]);
+      }
       unsigned char* da = A + (hq * WH * WW + r0) * 16;
 #pragma unroll
       for (int j = 0; j < NWIN; ++j)
         if (r0 + 32 * j < WH * WW) cp_async16(da + 512 * j, wp[j] + c0);
-      if (!resident) load_weights(A + A_BYTES, c0);
-      cp_async_commit();
-      issued = g + 1;
-      if (g >= lag) {
-        // chunk g - lag: this thread's copies have landed; hand them to the tensor cores
-        cp_async_wait_n(lag);
-        fence_proxy_async_smem();
-        mbar_arrive(&full[(g - lag) % ns]);
-        handed = g - lag + 1;
-      }
+      // the stage's full barrier receives this thread's arrival once every
+      // window copy it has issued so far has landed
+      cp_async_arrive_noinc(&full[s]);
+      if (++s == ns) { s = 0; epar ^= 1u; }
+      if (++k == nchunks) { k = 0; ++item; }
     }
-    cp_async_wait<0>();
-    fence_proxy_async_smem();
-    for (int g = handed; g < issued; ++g) mbar_arrive(&full[g % ns]);
+    cp_async_wait_all();  // no copy may be in flight when the CTA exits
   } else if (warp == MMA_WARP) {
     // ---- the MMA issuer ----
     if (lane == 0 && G > 0) {
-      bool ok = true;
-      for (int g = 0; g < G; ++g) {
+      // stage s, its use parity fpar, chunk k of item: kept as counters (no divisions in the loop);
+      // the descriptors are formed once per chunk, each tap adding a constant to the address field
+      const uint32_t idesc = idesc_bf16<BN>();
+      const uint64_t ad_lay = sdesc(0, WH * WW * 16, WW * 16), bd_lay = sdesc(0, BN * 16, 128);
+      const uint32_t a_base = smem_u32(stages), w_base = smem_u32(wres);
+      bool ok = !resident || mbar_wait_bounded(wbar, 0, WAIT_CYCLES);  // the resident weights
+      int s = 0, k = 0, item = 0;
+      uint32_t fpar = 0;
+      for (int g = 0; g < G && ok; ++g) {
         if (*abort_flag) { ok = false; break; }
-        const int item = g / nchunks, k = g - item * nchunks, s = g % ns;
         const int buf = item & 1;
         // the buffer's tile of two items ago has been read by the epilogue
         if (k == 0 && item >= 2 && !mbar_wait_bounded(&acce[buf], (uint32_t)(((item - 2) >> 1) & 1), WAIT_CYCLES)) {
           ok = false;
           break;
         }
-        if (!mbar_wait_bounded(&full[s], (uint32_t)((g / ns) & 1), WAIT_CYCLES)) { ok = false; break; }
+        if (!mbar_wait_bounded(&full[s], fpar, WAIT_CYCLES)) { ok = false; break; }
+        // the window was written through the generic proxy (cp.async); the MMAs read it through the async proxy
+        fence_proxy_async_smem();
         tc_fence_after();
-        const uint32_t Aa = smem_u32(stages + s * stage_bytes);
-        const uint32_t Ba = resident ? smem_u32(wres + k * C::BCHUNK) : Aa + A_BYTES;
+        const uint32_t Aa = a_base + (uint32_t)(s * stage_bytes);
+        const uint32_t Ba = resident ? w_base + (uint32_t)(k * C::BCHUNK) : Aa + A_BYTES;
+        const uint64_t ad0 = ad_lay | ((Aa & 0x3FFFFu) >> 4), bd0 = bd_lay | ((Ba & 0x3FFFFu) >> 4);
         const uint32_t acc = tmem + (uint32_t)(buf * BN);
 #pragma unroll
         for (int tap = 0; tap < 9; ++tap) {
           int dy = tap / 3 - 1, dx = tap % 3 - 1;
           if (MODE == 1) { dy = -dy; dx = -dx; }
-          const uint64_t ad = sdesc(Aa + (uint32_t)(((dy + 1) * WW + (dx + 1)) * 16), WH * WW * 16, WW * 16);
-          const uint64_t bd = sdesc(Ba + (uint32_t)(tap * 2 * BN * 16), BN * 16, 128);
-          mma_tc(acc, ad, bd, idesc_bf16<BN>(), (k > 0 || tap > 0) ? 1u : 0u);
+          const uint32_t aoff = (uint32_t)(((dy + 1) * WW + (dx + 1)) * 16) >> 4;
+          const uint32_t boff = (uint32_t)(tap * 2 * BN * 16) >> 4;
+          mma_tc(acc, ad0 + aoff, bd0 + boff, idesc, (k > 0 || tap > 0) ? 1u : 0u);
         }
         mma_commit(&empty[s]);
         if (k == nchunks - 1) mma_commit(&accf[buf]);
+        if (++s == ns) { s = 0; fpar ^= 1u; }
+        if (++k == nchunks) { k = 0; ++item; }
       }
       if (!ok) *abort_flag = 1;
     }
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, int ti
     // ---- epilogue: warp w holds tensor-memory lanes 32w .. 32w + 31 ----
     for (int item = 0; item < nitems; ++item) {
       const int buf = item & 1;
-      const bool ok = mbar_wait_bounded(&accf[buf], (uint32_t)((item >> 1) & 1), WAIT_CYCLES);
+      const bool ok = mbar_wait_bounded_sleep(&accf[buf], (uint32_t)((item >> 1) & 1), WAIT_CYCLES);
       // every lane of the warp takes the same branch before the aligned tensor-memory loads
       if (!__all_sync(0xffffffffu, ok ? 1 : 0) || __any_sync(0xffffffffu, *abort_flag != 0)) {
         *abort_flag = 1;
@@ -421,6 +421,27 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, int ti
   }
 }
 
+// the weight matrix [nout rows][9 * K channels] (BF16) as a 2D tensor map
+// whose box is 8 channels x bn rows: one [n][8] block of core matrices
+static bool encode_weight_map(CUtensorMap* m, const __nv_bfloat16* w, int nout, int kw, int bn) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return false;
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)kw, (cuuint64_t)nout};
+  cuuint64_t strides[1] = {(cuuint64_t)kw * 2};
+  cuuint32_t box[2] = {8, (cuuint32_t)bn};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(w), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int MODE, int BN>
 cudaError_t launch_tc(const ConvArgs& a, int tiles_x, int tiles_y, int ntiles, int nout, cudaStream_t s) {
   static int attr_set = 0;
@@ -436,14 +457,16 @@ cudaError_t launch_tc(const ConvArgs& a, int tiles_x, int tiles_y, int ntiles, i
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-  // two CTAs per SM where the tensor memory allows it (one's epilogue and
-  // start-up overlap the other's MMAs); the weights stay resident if that
-  // still leaves the minimum ring, else they stream through the ring, which
-  // takes as many stages as fit (up to SMAX)
+  // Up to MAX_OCC CTAs per SM as the tensor memory and shared memory allow,
+  // each with a ring of at least SMIN stages: a CTA issues its MMAs from one
+  // thread, at about one per 86 cycles, so the tensor pipe of an SM is kept
+  // busy at N <= 128 only by several issuing CTAs.  The weights stay resident
+  // if that still leaves the ring, else they stream through it; the ring
+  // takes as many stages as fit (up to SMAX).
   const int tm_occ = 512 / Cfg<BN>::TCOLS;
   bool resident = false;
   int ns = 0, occ = 1;
-  for (int want = tm_occ >= 2 ? 2 : 1; want >= 1 && ns == 0; --want) {
+  for (int want = tm_occ < MAX_OCC ? tm_occ : MAX_OCC; want >= 1 && ns == 0; --want) {
     int budget = sm_smem / want - reserved;
     if (budget > SMEM_MAX) budget = SMEM_MAX;
     if (smem_bytes(BN, nch, true, SMIN) <= budget) {
@@ -463,7 +486,10 @@ cudaError_t launch_tc(const ConvArgs& a, int tiles_x, int tiles_y, int ntiles, i
   if (gx > ntiles) gx = ntiles;
   if (gx < 1) gx = 1;
   dim3 grid((unsigned)gx, (unsigned)nblk_n);
-  k<<<grid, NTHR, smem, s>>>(a, tiles_x, tiles_y, ntiles, resident ? 1 : 0, ns);
+  const int kin = MODE == 0 ? a.cin : a.cout;
+  CUtensorMap wmap;
+  if (!encode_weight_map(&wmap, MODE == 0 ? a.wt : a.wd, nout, 9 * kin, BN)) return cudaErrorNotSupported;
+  k<<<grid, NTHR, smem, s>>>(a, wmap, tiles_x, tiles_y, ntiles, resident ? 1 : 0, ns);
   return cudaGetLastError();
 }
 
