@@ -308,6 +308,14 @@ def measure_fp_rates():
     for prec in (64, 32):
         r = gpe2p.fma_rate(prec)
         out[f"fp{prec}_tflops"] = r["flops_per_s"] / 1e12
+    # the surrogate convolutions' bound: tcgen05.mma cycles per MMA of one SM
+    # (M = 128, K = 16) at their N, with the two issuing CTAs per SM they run
+    # with, and at N = 256 (the tensor pipe's own rate)
+    mma = {}
+    for n, k in ((32, 2), (64, 2), (128, 2), (256, 1)):
+        c = gpe2p.mma_rate(n, k)
+        mma[f"n{n}_issuers{k}"] = {"cycles_per_mma": c, "mac_per_cycle_per_sm": 128 * n * 16 / c}
+    out["tcgen05_mma"] = mma
     return out
 
 

@@ -182,6 +182,21 @@ int gpe2p_profile_steps(gpe2p_handle h, int nsteps, double *ms, int max_launches
  * pointer or another precision, GPE2P_ECUDA if a launch fails. */
 int gpe2p_fma_rate(int precision, double *flops_per_s, double *ms, void *stream);
 
+/* Measurement aid (the paper has no counterpart): the issue rate of the
+ * tensor cores as the surrogate's convolutions use them.  On one SM, lane 0
+ * of `issuers` warps (1, 2 or 4) each issues back-to-back tcgen05.mma
+ * (kind::f16, BF16 operands from shared memory, FP32 accumulator in tensor
+ * memory, M = 128, N = n in {32, 64, 128, 256}, K = 16) into its own
+ * accumulator, n * issuers <= 512 columns.  *cycles_per_mma receives the SM
+ * clock cycles per MMA of the whole SM (the slowest issuer's elapsed cycles
+ * over all issuers' MMAs), the best of three launches after a warm-up, on
+ * stream (a cudaStream_t, NULL for the legacy default stream).  128 n 16
+ * multiply-adds over this figure is the SM's multiply-add rate at that N.
+ * Allocates nothing; synchronises the stream.  GPE2P_EINVAL for a NULL
+ * pointer or another n or issuer count, GPE2P_ETIMEOUT if the bounded wait
+ * for the MMAs gave up, GPE2P_ECUDA if a launch or copy fails. */
+int gpe2p_mma_rate(int n, int issuers, double *cycles_per_mma, void *stream);
+
 /* Device pointer of a field of the current state, in the handle's precision
  * (float or double): which = 0 p, 1 u, 2 v, 3 w, 4 phi, 5 mu, 6 the low part
  * of phi under the compensated accumulation (phi = field 4 + field 6; see

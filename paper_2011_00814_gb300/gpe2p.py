@@ -129,6 +129,8 @@ def lib():
         L.gpe2p_fma_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                      vp]
         L.gpe2p_fma_rate.restype = ctypes.c_int
+        L.gpe2p_mma_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+        L.gpe2p_mma_rate.restype = ctypes.c_int
         L.gpe2p_last_error.argtypes = [vp]
         L.gpe2p_last_error.restype = ctypes.c_char_p
         L.gpe2p_destroy.argtypes = [vp]
@@ -150,6 +152,16 @@ def fma_rate(precision: int, stream: int | None = None) -> dict:
     if rc != OK:
         raise GPE2PError(rc, "gpe2p_fma_rate failed")
     return {"flops_per_s": f.value, "ms": ms.value}
+
+
+def mma_rate(n: int, issuers: int = 1, stream: int | None = None) -> float:
+    """SM clock cycles per tcgen05.mma (M = 128, N = n, K = 16, BF16) of one
+    SM with `issuers` issuing threads (gpe2p_mma_rate)."""
+    c = ctypes.c_double()
+    rc = lib().gpe2p_mma_rate(int(n), int(issuers), ctypes.byref(c), stream)
+    if rc != OK:
+        raise GPE2PError(rc, "gpe2p_mma_rate failed")
+    return c.value
 
 
 def params(prm: dict) -> Params:
