@@ -40,6 +40,8 @@ sys.path.insert(0, ROOT)
 from paper_2011_00814_gb300 import inputs  # noqa: E402
 
 METRIC = "cell-updates/s (RK3 step)"
+# the fraction of the HBM roofline the bubble's dominant kernel is aimed at
+TARGET_FRAC = 0.70
 UNIT = "cell-updates/s"
 WORKLOAD = "3D buoyant bubble 256x256x512 FP32 (no-slip walls, D3Q15, RK4 CH)"
 
@@ -588,6 +590,7 @@ def main():
                      "peak_kind": peak_kind, "traffic": stored_traffic(),
                      "algorithmic_bytes_per_launch": dom_bytes,
                      "step_algorithmic_gbs": step_gbs, "step_frac": step_gbs / peak,
+                     "target_frac": TARGET_FRAC, "gap_to_target": TARGET_FRAC - achieved / peak,
                      "shares": {k: round(v, 4) for k, v in share.items()}},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 5 * 8 * ncell,
                 "d2h_bytes_per_step": 5 * 8 * ncell, "steps": args.e2e_steps},

@@ -337,9 +337,19 @@ int gpe2p_net_train_step(gpe2p_net_handle n, const float *x, const float *t, int
  * mma.sync kernels.  Both compute the same products (FP32 accumulation in a
  * different order). */
 int gpe2p_net_set_backend(gpe2p_net_handle n, int tcgen05);
+/* Host-side test switch of the tcgen05 convolutions (the forward graph is
+ * rebuilt).  GPE2P_FAULT_LOSE_COPY with value 1: in every CTA of those
+ * kernels the first wait for a filled pipeline stage, whose copies have in
+ * fact all landed, is reported as timed out; the CTA's other roles give up
+ * their waits, it lets any copy or MMA in flight finish, frees its tensor
+ * memory, records the error word and returns, and gpe2p_net_sync then
+ * reports GPE2P_ETIMEOUT (the outputs of those calls are undefined); value 0
+ * turns it off.  GPE2P_FAULT_CLEAR turns it off and clears the error word.
+ * No fault reaches the GPU.  GPE2P_EINVAL for other kinds or values. */
+int gpe2p_net_fault(gpe2p_net_handle n, int what, int value);
 /* Waits for the network's stream and reports GPE2P_ETIMEOUT if a tensor-core
- * kernel gave up a bounded wait since the handle was created (the outputs of
- * that call are then undefined).  gpe2p_net_gradients and
+ * kernel gave up a bounded wait since the handle was created or the error
+ * word was last cleared (the outputs of that call are then undefined).  gpe2p_net_gradients and
  * gpe2p_net_train_step (with a loss pointer) report it too. */
 int gpe2p_net_sync(gpe2p_net_handle n);
 /* Multiply-add FLOPs (x2) of one forward pass of a batch. */

@@ -67,6 +67,18 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 // wait until every cp.async this thread has issued has completed
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// a bounded wait that also gives up as soon as another role of the CTA has
+// aborted (sleeping between polls when asked, for roles with nothing else to do)
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag, bool sleep) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag != 0 || clock64() - t0 > WAIT_CYCLES) return false;
+    if (sleep) __nanosleep(128);
+  }
+  return true;
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -311,7 +323,7 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, const 
     for (int g = 0; g < G; ++g) {
       // the warp leaves together (its lanes meet at __syncwarp below)
       bool stop = *abort_flag != 0;
-      if (!stop && g >= ns) stop = !mbar_wait_bounded_sleep(&empty[s], epar, WAIT_CYCLES);
+      if (!stop && g >= ns) stop = !wait_or_abort(&empty[s], epar, abort_flag, true);
       if (__any_sync(0xffffffffu, stop)) {
         *abort_flag = 1;
         break;
@@ -355,18 +367,20 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, const 
       const uint32_t idesc = idesc_bf16<BN>();
       const uint64_t ad_lay = sdesc(0, WH * WW * 16, WW * 16), bd_lay = sdesc(0, BN * 16, 128);
       const uint32_t a_base = smem_u32(stages), w_base = smem_u32(wres);
-      bool ok = !resident || mbar_wait_bounded(wbar, 0, WAIT_CYCLES);  // the resident weights
+      bool ok = !resident || wait_or_abort(wbar, 0, abort_flag, false);  // the resident weights
       int s = 0, k = 0, item = 0;
       uint32_t fpar = 0;
       for (int g = 0; g < G && ok; ++g) {
         if (*abort_flag) { ok = false; break; }
         const int buf = item & 1;
         // the buffer's tile of two items ago has been read by the epilogue
-        if (k == 0 && item >= 2 && !mbar_wait_bounded(&acce[buf], (uint32_t)(((item - 2) >> 1) & 1), WAIT_CYCLES)) {
+        if (k == 0 && item >= 2 && !wait_or_abort(&acce[buf], (uint32_t)(((item - 2) >> 1) & 1), abort_flag, false)) {
           ok = false;
           break;
         }
-        if (!mbar_wait_bounded(&full[s], fpar, WAIT_CYCLES)) { ok = false; break; }
+        if (!wait_or_abort(&full[s], fpar, abort_flag, false)) { ok = false; break; }
+        // test switch: the first filled stage is reported as lost (its copies have all landed)
+        if (g == 0 && a.wait_fault) { ok = false; break; }
         // the window was written through the generic proxy (cp.async); the MMAs read it through the async proxy
         fence_proxy_async_smem();
         tc_fence_after();
@@ -393,7 +407,7 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, const 
     // ---- epilogue: warp w holds tensor-memory lanes 32w .. 32w + 31 ----
     for (int item = 0; item < nitems; ++item) {
       const int buf = item & 1;
-      const bool ok = mbar_wait_bounded_sleep(&accf[buf], (uint32_t)((item >> 1) & 1), WAIT_CYCLES);
+      const bool ok = wait_or_abort(&accf[buf], (uint32_t)((item >> 1) & 1), abort_flag, true);
       // every lane of the warp takes the same branch before the aligned tensor-memory loads
       if (!__all_sync(0xffffffffu, ok ? 1 : 0) || __any_sync(0xffffffffu, *abort_flag != 0)) {
         *abort_flag = 1;
@@ -411,7 +425,8 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, const 
   __syncthreads();
   if (*abort_flag) {
     if (tid == 0 && a.err) atomicExch(a.err, 1);
-    // give the MMAs issued so far a bounded time to finish before the tensor memory is freed
+    // give the MMAs and the weight copies issued so far a bounded time to
+    // finish before the tensor memory and the shared memory are released
     const long long t0 = clock64();
     while (clock64() - t0 < 1000000) {}
   }

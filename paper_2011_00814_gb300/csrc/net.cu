@@ -51,6 +51,7 @@ struct gpe2p_net {
   float *P = nullptr, *G = nullptr, *Am = nullptr, *Av = nullptr;
   long long adam_t = 0;
   int use_tc = 1;                // 3x3 forward / data gradient on tcgen05
+  int wait_fault = 0;            // test switch of the tcgen05 kernels (gpe2p_net_fault)
   // the inference forward captured in a CUDA graph for one (x, y, batch)
   cudaGraphExec_t fwd_exec = nullptr;
   const float* fwd_x = nullptr;
@@ -136,6 +137,7 @@ static ConvArgs conv_args(const gpe2p_net* n, const ConvL& c, int B) {
   a.ksplit = 2048;
   a.tc = n->use_tc;
   a.err = n->d_err;
+  a.wait_fault = n->wait_fault;
   return a;
 }
 
@@ -425,6 +427,23 @@ static int net_err_word(gpe2p_net* n) {
 extern "C" int gpe2p_net_sync(gpe2p_net_handle n) {
   if (!n) return net_fail(n, GPE2P_EINVAL, "NULL handle");
   return net_err_word(n);
+}
+
+extern "C" int gpe2p_net_fault(gpe2p_net_handle n, int what, int value) {
+  if (!n) return net_fail(n, GPE2P_EINVAL, "NULL handle");
+  if (what == GPE2P_FAULT_LOSE_COPY) {
+    if (value != 0 && value != 1) return net_fail(n, GPE2P_EINVAL, "bad fault value");
+    n->wait_fault = value;
+  } else if (what == GPE2P_FAULT_CLEAR) {
+    n->wait_fault = 0;
+    NK(n, cudaStreamSynchronize(n->stream), "fault clear");
+    NK(n, cudaMemsetAsync(n->d_err, 0, sizeof(int), n->stream), "fault clear");
+    NK(n, cudaStreamSynchronize(n->stream), "fault clear");
+  } else {
+    return net_fail(n, GPE2P_EINVAL, "fault kind not taken by a network");
+  }
+  drop_forward_graph(n);
+  return GPE2P_OK;
 }
 
 extern "C" int gpe2p_net_set_backend(gpe2p_net_handle n, int tcgen05) {

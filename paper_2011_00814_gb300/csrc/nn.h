@@ -40,6 +40,7 @@ struct ConvArgs {
   int ksplit;
   int tc;     // 1: 3x3 forward and data gradient on the tcgen05 kernels (conv_tc.cu)
   int* err;   // device error word: set to 1 by a tcgen05 kernel whose wait timed out
+  int wait_fault;  // test switch: the first wait of each tcgen05 CTA for a filled stage reports a timeout
 };
 
 cudaError_t conv_forward(const ConvArgs& a, cudaStream_t s);

@@ -102,6 +102,8 @@ def lib():
         L.gpe2p_net_forward.argtypes = [vp, vp, vp, ctypes.c_int]
         L.gpe2p_net_set_normalization.argtypes = [vp, fp, fp, fp, ctypes.c_int]
         L.gpe2p_net_set_backend.argtypes = [vp, ctypes.c_int]
+        L.gpe2p_net_fault.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        L.gpe2p_net_fault.restype = ctypes.c_int
         L.gpe2p_net_sync.argtypes = [vp]
         L.gpe2p_net_gradients.argtypes = [vp, vp, vp, ctypes.c_int, fp, fp]
         L.gpe2p_net_train_step.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_float, fp]
@@ -501,6 +503,11 @@ class Net:
     def set_backend(self, tcgen05: bool):
         """3x3 convolutions on tcgen05 (True, default) or on mma.sync (False)."""
         self._check(lib().gpe2p_net_set_backend(self.h, int(bool(tcgen05))))
+
+    def fault(self, what: int, value: int = 0):
+        """Host-side test switch of the tcgen05 convolutions (gpe2p_net_fault):
+        FAULT_LOSE_COPY (value 1 on, 0 off) or FAULT_CLEAR."""
+        self._check(lib().gpe2p_net_fault(self.h, int(what), int(value)))
 
     def sync(self):
         self._check(lib().gpe2p_net_sync(self.h))

@@ -1,11 +1,17 @@
-"""The bounded waits of the 3D kernels, made to report a timeout from the host
-(GPE2P_FAULT_LOSE_COPY): in every block of the chosen kernel the first wait
-of the chosen kind completes and is then treated as timed out, as if its copy
-had been lost.  The block records the error, waits for its other copies in
-flight and returns; the next diagnostics report GPE2P_ETIMEOUT.  After
-GPE2P_FAULT_CLEAR and gpe2p_init_fields the same handle steps cleanly again,
-bit for bit as a handle that never saw the switch.  Nothing faults on the
-GPU: only the kernels' own timeout bookkeeping runs."""
+"""The bounded waits of the 3D kernels and of the tcgen05 convolutions, made
+to report a timeout from the host (GPE2P_FAULT_LOSE_COPY).
+
+3D kernels: in every block of the chosen kernel the first wait of the chosen
+kind completes and is then treated as timed out, as if its copy had been
+lost.  The block records the error, waits for its other copies in flight and
+returns; the next diagnostics report GPE2P_ETIMEOUT.  After GPE2P_FAULT_CLEAR
+and gpe2p_init_fields the same handle steps cleanly again, bit for bit as a
+handle that never saw the switch.
+
+Convolutions: the same for the first wait of every CTA for a filled pipeline
+stage (gpe2p_net_fault).
+
+Nothing faults on the GPU: only the kernels' own timeout bookkeeping runs."""
 from __future__ import annotations
 
 import numpy as np
@@ -72,3 +78,41 @@ def test_lose_copy_is_refused_where_it_does_not_apply():
             s.fault(gpe2p.FAULT_LOSE_COPY, 16)
         with pytest.raises(gpe2p.GPE2PError):
             s.fault(gpe2p.FAULT_SKIP_BARRIER, 0)
+
+
+@pytest.mark.parametrize("shape", [(3, [16, 32, 64], 32, 32, 2), (4, [32, 64, 128, 256], 64, 64, 2)])
+def test_lost_stage_of_the_tcgen05_convolutions_reports_timeout_and_the_net_recovers(shape):
+    """The tcgen05 convolutions' pipeline waits (gpe2p_net_fault): with the
+    switch on, the first wait of every CTA for a filled stage reports a
+    timeout; the other roles give up their waits and the CTA returns, and the
+    forward's gpe2p_net_sync and gpe2p_net_gradients report GPE2P_ETIMEOUT.
+    After GPE2P_FAULT_CLEAR the same handle computes the forward bit for bit
+    as before the switch.  On the small net the layers keep their weights in
+    shared memory; on the 4-level net some stream them through the ring."""
+    import torch
+    L, ch, h, w, b = shape
+    rng = np.random.default_rng(4)
+    with gpe2p.Net(L, ch, 4, 4, h, w, b, seed=3) as net:
+        net.set_backend(True)
+        x = torch.from_numpy(rng.normal(size=(b, h, w, 4)).astype(np.float32)).cuda()
+        t = torch.from_numpy(rng.normal(size=(b, h, w, 4)).astype(np.float32)).cuda()
+        y0 = torch.empty((b, h, w, 4), dtype=torch.float32, device="cuda")
+        net.forward(x, y0, b)
+        net.sync()
+        net.fault(gpe2p.FAULT_LOSE_COPY, 1)
+        y1 = torch.empty_like(y0)
+        net.forward(x, y1, b)
+        with pytest.raises(gpe2p.GPE2PError) as e:
+            net.sync()
+        assert e.value.code == gpe2p.ETIMEOUT
+        with pytest.raises(gpe2p.GPE2PError) as e:
+            net.gradients(x, t, b)
+        assert e.value.code == gpe2p.ETIMEOUT
+        net.fault(gpe2p.FAULT_CLEAR)
+        y2 = torch.empty_like(y0)
+        net.forward(x, y2, b)
+        net.sync()
+        assert torch.equal(y2, y0)
+        with pytest.raises(gpe2p.GPE2PError) as e:
+            net.fault(gpe2p.FAULT_SKIP_BARRIER, 0)
+        assert e.value.code == gpe2p.EINVAL
