@@ -267,6 +267,9 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, const 
   const int nitems = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int G = nitems * nchunks;
 
+  // the next kernel on the stream may start its own set-up now; it reads
+  // this kernel's outputs only after its grid-dependency wait
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (tid == 0) {
     for (int s = 0; s < ns; ++s) {
       mbar_init(&full[s], 32 * PROD_WARPS);
@@ -318,6 +321,8 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, const 
       __syncwarp();  // the bytes are announced before any of them can land
       for (int kk = 0; kk < nchunks; ++kk) load_weights(wres + kk * C::BCHUNK, kk * KC, wbar);
     }
+    // the window is the previous kernel's output: wait until that kernel has completed
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     int s = 0, k = 0, item = 0;
     uint32_t epar = 1;  // parity of the empty phase a stage's next use waits for (none in the first round)
     for (int g = 0; g < G; ++g) {
@@ -361,6 +366,9 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, const 
     cp_async_wait_all();  // no copy may be in flight when the CTA exits
   } else if (warp == MMA_WARP) {
     // ---- the MMA issuer ----
+    // no stage can fill before the previous kernel completes: wait for it
+    // here rather than by polling the first stage's barrier meanwhile
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (lane == 0 && G > 0) {
       // stage s, its use parity fpar, chunk k of item: kept as counters (no divisions in the loop);
       // the descriptors are formed once per chunk, each tap adding a constant to the address field
@@ -405,6 +413,8 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, const 
     }
   } else {
     // ---- epilogue: warp w holds tensor-memory lanes 32w .. 32w + 31 ----
+    // its stores (and the data gradient's reads of dx) follow the previous kernel
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int item = 0; item < nitems; ++item) {
       const int buf = item & 1;
       const bool ok = wait_or_abort(&accf[buf], (uint32_t)((item >> 1) & 1), abort_flag, true);
@@ -504,8 +514,24 @@ cudaError_t launch_tc(const ConvArgs& a, int tiles_x, int tiles_y, int ntiles, i
   const int kin = MODE == 0 ? a.cin : a.cout;
   CUtensorMap wmap;
   if (!encode_weight_map(&wmap, MODE == 0 ? a.wt : a.wd, nout, 9 * kin, BN)) return cudaErrorNotSupported;
-  k<<<grid, NTHR, smem, s>>>(a, wmap, tiles_x, tiles_y, ntiles, resident ? 1 : 0, ns);
-  return cudaGetLastError();
+  // Programmatic dependent launch where a CTA has at most two work items
+  // (small batches, the deep levels): its set-up (barriers, tensor memory,
+  // resident weights) then overlaps the tail of the kernel before it.  With
+  // many items per CTA there is little tail to overlap, and the early
+  // launch measured slower.  The kernel's grid-dependency instructions are
+  // no-ops when it is launched without the attribute.
+  const bool pdl = (ntiles + gx - 1) / gx <= 2;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(NTHR);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = s;
+  cfg.attrs = pdl ? attr : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, a, wmap, tiles_x, tiles_y, ntiles, resident ? 1 : 0, ns);
 }
 
 template <int MODE>
