@@ -33,7 +33,6 @@
 // frees its tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
-#include <cudaTypedefs.h>
 #include <stdint.h>
 
 #include "nn.h"
@@ -66,6 +65,15 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 }
 // wait until every cp.async this thread has issued has completed
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// contiguous bulk copy global -> shared of `bytes` (a multiple of 16, both
+// addresses 16-byte aligned), completion counted on bar
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
 
 // a bounded wait that also gives up as soon as another role of the CTA has
 // aborted (sleeping between polls when asked, for roles with nothing else to do)
@@ -239,8 +247,8 @@ __device__ __forceinline__ void epilogue_tile(const ConvArgs& a, uint32_t acc, c
 }
 
 template <int MODE, int BN>
-__global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, const __grid_constant__ CUtensorMap wmap,
-                                                       int tiles_x, int tiles_y, int ntiles, int resident, int ns) {
+__global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, int tiles_x, int tiles_y, int ntiles,
+                                                       int resident, int ns) {
   using C = Cfg<BN>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -264,6 +272,7 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, const 
   const int lds = MODE == 0 ? a.ldx : a.ldz;
   const int soff = MODE == 0 ? a.xoff : 0;
   const int nchunks = Cin / KC;
+  const int nout_all = MODE == 0 ? a.cout : a.cin;  // rows of the packed weights
   const int nitems = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int G = nitems * nchunks;
 
@@ -298,28 +307,27 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, const 
     // ---- producers ----
     // thread pt copies the 8-channel half hq of the window entries r0 + 32 j,
     // from source pointers formed once per tile, so that a chunk costs it a
-    // handful of copies.  The weights of a chunk are 18 TMA boxes (9 taps x
-    // 2 halves) of 8 channels x BN output channels, each landing as one
-    // [n][8] block of core matrices, issued by lanes 0-17 of the first
-    // producer warp.
+    // handful of copies.  The weights of a chunk come as 18 contiguous bulk
+    // copies from the weights packed per chunk.
     const int pt = tid - 32 * EPI_WARPS;
     constexpr int NP = 32 * PROD_WARPS;
     static_assert(NP == 64, "two producer warps: 32 window entries per pass");
     constexpr int NWIN = (WH * WW + 31) / 32;
     const int hq = pt & 1, r0 = pt >> 1;
-    // the weights of chunk c0 into B ([tap][half][n][8]), counted on bar: box
-    // q = 2 tap + h is issued by lane q mod 32 of the first producer warp
-    auto load_weights = [&](unsigned char* B, int c0, uint64_t* bar) {
-      if (pt < 18) {
-        const int tap = pt >> 1, h = pt & 1;
-        tma_load_2d(B + pt * BN * 16, &wmap, tap * Cin + c0 + 8 * h, n0, bar);
-      }
+    // the weights of chunk kk into B ([tap][half][n][8]), counted on bar: the
+    // packed weights hold each (tap, half) run of the block's BN output
+    // channels as BN x 16 contiguous bytes, one bulk copy by lane q < 18 of
+    // the first producer warp
+    const __nv_bfloat16* wpk = MODE == 0 ? a.wtp : a.wdp;
+    auto load_weights = [&](unsigned char* B, int kk, uint64_t* bar) {
+      if (pt < 18)
+        bulk_load(B + pt * BN * 16, wpk + (((size_t)kk * 18 + pt) * nout_all + n0) * 8, (uint32_t)(BN * 16), bar);
     };
     const __nv_bfloat16* wp[NWIN];  // this tile's window sources of this thread (channel 0 of its half)
     if (resident && G > 0 && pt < 32) {
       if (pt == 0) mbar_arrive_expect_tx(wbar, (uint32_t)(nchunks * C::BCHUNK));
       __syncwarp();  // the bytes are announced before any of them can land
-      for (int kk = 0; kk < nchunks; ++kk) load_weights(wres + kk * C::BCHUNK, kk * KC, wbar);
+      for (int kk = 0; kk < nchunks; ++kk) load_weights(wres + kk * C::BCHUNK, kk, wbar);
     }
     // the window is the previous kernel's output: wait until that kernel has completed
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -351,7 +359,7 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, const 
         // thread's own arrival below can complete the phase
         if (pt == 0) mbar_expect_tx(&full[s], (uint32_t)C::BCHUNK);
         __syncwarp();
-        load_weights(A + A_BYTES, c0, &full[s]);
+        load_weights(A + A_BYTES, k, &full[s]);
       }
       unsigned char* da = A + (hq * WH * WW + r0) * 16;
 #pragma unroll
@@ -446,27 +454,6 @@ __global__ void __launch_bounds__(NTHR) conv3_tc_kernel(const ConvArgs a, const 
   }
 }
 
-// the weight matrix [nout rows][9 * K channels] (BF16) as a 2D tensor map
-// whose box is 8 channels x bn rows: one [n][8] block of core matrices
-static bool encode_weight_map(CUtensorMap* m, const __nv_bfloat16* w, int nout, int kw, int bn) {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      return false;
-    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
-  cuuint64_t dims[2] = {(cuuint64_t)kw, (cuuint64_t)nout};
-  cuuint64_t strides[1] = {(cuuint64_t)kw * 2};
-  cuuint32_t box[2] = {8, (cuuint32_t)bn};
-  cuuint32_t estr[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(w), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 template <int MODE, int BN>
 cudaError_t launch_tc(const ConvArgs& a, int tiles_x, int tiles_y, int ntiles, int nout, cudaStream_t s) {
   static int attr_set = 0;
@@ -511,9 +498,6 @@ cudaError_t launch_tc(const ConvArgs& a, int tiles_x, int tiles_y, int ntiles, i
   if (gx > ntiles) gx = ntiles;
   if (gx < 1) gx = 1;
   dim3 grid((unsigned)gx, (unsigned)nblk_n);
-  const int kin = MODE == 0 ? a.cin : a.cout;
-  CUtensorMap wmap;
-  if (!encode_weight_map(&wmap, MODE == 0 ? a.wt : a.wd, nout, 9 * kin, BN)) return cudaErrorNotSupported;
   // Programmatic dependent launch where a CTA has at most two work items
   // (small batches, the deep levels): its set-up (barriers, tensor memory,
   // resident weights) then overlaps the tail of the kernel before it.  With
@@ -531,7 +515,7 @@ cudaError_t launch_tc(const ConvArgs& a, int tiles_x, int tiles_y, int ntiles, i
   cfg.stream = s;
   cfg.attrs = pdl ? attr : nullptr;
   cfg.numAttrs = pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, k, a, wmap, tiles_x, tiles_y, ntiles, resident ? 1 : 0, ns);
+  return cudaLaunchKernelEx(&cfg, k, a, tiles_x, tiles_y, ntiles, resident ? 1 : 0, ns);
 }
 
 template <int MODE>
@@ -561,6 +545,7 @@ bool conv_tc_supported(const ConvArgs& a, int mode) {
   const int ld = mode == 0 ? a.ldx : a.ldz, off = mode == 0 ? a.xoff : 0;
   const int ldo = mode == 0 ? a.ldy : a.lddx, offo = mode == 0 ? a.yoff : a.dxoff;
   if (smem_bytes(16, kin / KC, false, SMIN) > SMEM_MAX) return false;
+  if (!(mode == 0 ? a.wtp : a.wdp)) return false;  // the weights packed per K chunk
   return ld % 8 == 0 && off % 8 == 0 && ldo % 8 == 0 && offo % 8 == 0;
 }
 

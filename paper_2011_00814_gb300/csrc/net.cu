@@ -29,6 +29,8 @@ struct ConvL {
   long long w, b;                 // offsets of weights and bias in the flat parameters
   __nv_bfloat16* wt = nullptr;    // [cout][taps*cin]
   __nv_bfloat16* wd = nullptr;    // [cin][taps*cout]
+  __nv_bfloat16* wtp = nullptr;   // wt and wd packed per K chunk for the tcgen05 kernels (3x3 only)
+  __nv_bfloat16* wdp = nullptr;
   __nv_bfloat16* z = nullptr;     // pre-activation [npix][cout]
 };
 
@@ -112,7 +114,7 @@ static int add_conv(gpe2p_net* n, int cin, int cout, int taps, int level) {
 
 static cudaError_t refresh_bf16(gpe2p_net* n) {
   for (auto& c : n->conv) {
-    cudaError_t e = weights_bf16(n->P + c.w, c.wt, c.wd, c.cout, c.cin, c.taps, n->stream);
+    cudaError_t e = weights_bf16(n->P + c.w, c.wt, c.wd, c.wtp, c.wdp, c.cout, c.cin, c.taps, n->stream);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -129,6 +131,8 @@ static ConvArgs conv_args(const gpe2p_net* n, const ConvL& c, int B) {
   a.taps = c.taps;
   a.wt = c.wt;
   a.wd = c.wd;
+  a.wtp = c.wtp;
+  a.wdp = c.wdp;
   a.bias = n->P + c.b;
   a.z = c.z;
   a.act = 1;
@@ -333,6 +337,9 @@ extern "C" int gpe2p_net_create(int levels, const int* channels, int in_ch, int 
   long long zmax = 0;
   for (auto& c : n->conv) {
     const long long np = npix_at(n, c.level, B);
+    if (c.taps == 9 && ((e = nalloc(n, &c.wtp, (size_t)c.cout * c.taps * c.cin)) ||
+                        (e = nalloc(n, &c.wdp, (size_t)c.cout * c.taps * c.cin))))
+      return fail_alloc(e);
     if ((e = nalloc(n, &c.wt, (size_t)c.cout * c.taps * c.cin)) || (e = nalloc(n, &c.wd, (size_t)c.cout * c.taps * c.cin)) ||
         (e = nalloc(n, &c.z, (size_t)np * c.cout)))
       return fail_alloc(e);

@@ -504,7 +504,15 @@ __global__ void adam_kernel(float* w, const float* gr, float* m, float* v, long 
 }
 
 // WT (FP32 master, [co][tap*cin + ci]) -> BF16 WT and its transpose WD [ci][tap*cout + co]
-__global__ void weights_bf16_kernel(const float* w, __nv_bfloat16* wt, __nv_bfloat16* wd, int cout, int cin, int taps) {
+// The BF16 copies of a convolution's weights w[co][tap][ci]: wt in the same
+// order, wd transposed for the data gradient ([ci][tap][co]), and for the
+// tcgen05 kernels wtp / wdp (either may be NULL) packed per K chunk of 16
+// channels as [chunk][tap][half][n][8], n the output channel of the product
+// (co for the forward, ci for the data gradient) and the 8 channels of the
+// half contiguous: the weights of a chunk for a block of n are 18 runs of
+// 16-byte rows, one box of one bulk tensor copy.
+__global__ void weights_bf16_kernel(const float* w, __nv_bfloat16* wt, __nv_bfloat16* wd, __nv_bfloat16* wtp,
+                                    __nv_bfloat16* wdp, int cout, int cin, int taps) {
   const long long n = (long long)cout * taps * cin;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int co = (int)(i / ((long long)taps * cin));
@@ -513,6 +521,8 @@ __global__ void weights_bf16_kernel(const float* w, __nv_bfloat16* wt, __nv_bflo
     const __nv_bfloat16 b = __float2bfloat16_rn(w[i]);
     wt[i] = b;
     if (wd) wd[((size_t)ci * taps + tap) * cout + co] = b;
+    if (wtp) wtp[(((size_t)(ci >> 4) * 18 + tap * 2 + ((ci >> 3) & 1)) * cout + co) * 8 + (ci & 7)] = b;
+    if (wdp) wdp[(((size_t)(co >> 4) * 18 + tap * 2 + ((co >> 3) & 1)) * cin + ci) * 8 + (co & 7)] = b;
   }
 }
 
@@ -626,9 +636,11 @@ cudaError_t adam(float* w, const float* g, float* m, float* v, long long n, floa
   return cudaGetLastError();
 }
 
-cudaError_t weights_bf16(const float* w, __nv_bfloat16* wt, __nv_bfloat16* wd, int cout, int cin, int taps,
-                         cudaStream_t s) {
-  weights_bf16_kernel<<<blocks_for((long long)cout * cin * taps), 256, 0, s>>>(w, wt, wd, cout, cin, taps);
+cudaError_t weights_bf16(const float* w, __nv_bfloat16* wt, __nv_bfloat16* wd, __nv_bfloat16* wtp,
+                         __nv_bfloat16* wdp, int cout, int cin, int taps, cudaStream_t s) {
+  const bool packable = taps == 9 && cin % 16 == 0 && cout % 16 == 0;
+  weights_bf16_kernel<<<blocks_for((long long)cout * cin * taps), 256, 0, s>>>(
+      w, wt, wd, packable ? wtp : nullptr, packable ? wdp : nullptr, cout, cin, taps);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@ struct ConvArgs {
   int ldx, xoff;       // x: row stride (channels per pixel) and channel offset
   int up;              // 1: x is stored at (H/2, W/2) and read as its nearest 2x upsampling
   const __nv_bfloat16* wt;  // [cout][taps*cin]
+  const __nv_bfloat16* wtp; // the same packed per K chunk, [cin/16][9][2][cout][8] (tcgen05 forward)
   const float* bias;
   __nv_bfloat16* z;    // pre-activation [npix][cout] (or nullptr)
   __nv_bfloat16* y;
@@ -33,6 +34,7 @@ struct ConvArgs {
   const __nv_bfloat16* dz;  // [npix][cout]
   int ldz;
   const __nv_bfloat16* wd;  // [cin][taps*cout]
+  const __nv_bfloat16* wdp; // the same packed per K chunk, [cout/16][9][2][cin][8] (tcgen05 data gradient)
   __nv_bfloat16* dx;
   int lddx, dxoff, accumulate;
   // wgrad: dw[co][tap*cin + ci] += sum over pixels (FP32, split over ksplit pixels per block)
@@ -70,8 +72,8 @@ cudaError_t mse(const float* y, const float* t, float* dy, long long n, int cout
                 cudaStream_t s);
 cudaError_t adam(float* w, const float* g, float* m, float* v, long long n, float lr, float b1, float b2, float eps,
                  float c1, float c2, cudaStream_t s);
-cudaError_t weights_bf16(const float* w, __nv_bfloat16* wt, __nv_bfloat16* wd, int cout, int cin, int taps,
-                         cudaStream_t s);
+cudaError_t weights_bf16(const float* w, __nv_bfloat16* wt, __nv_bfloat16* wd, __nv_bfloat16* wtp,
+                         __nv_bfloat16* wdp, int cout, int cin, int taps, cudaStream_t s);
 
 }  // namespace nn
 }  // namespace gpe2p
