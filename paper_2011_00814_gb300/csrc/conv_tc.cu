@@ -169,7 +169,7 @@ constexpr int EPI_WARPS = 4, PROD_WARPS = 2;
 constexpr int NTHR = 32 * (EPI_WARPS + PROD_WARPS + 1);
 constexpr int MMA_WARP = EPI_WARPS + PROD_WARPS;
 constexpr int SMIN = 3, SMAX = 8;  // stages of the ring (chosen per launch)
-constexpr int MAX_OCC = 2;         // CTAs per SM at most
+constexpr int MAX_OCC = 4;         // CTAs per SM at most
 
 __host__ __device__ __forceinline__ int smem_bytes(int bn, int nchunks, bool resident, int ns) {
   const int bchunk = 9 * 2 * bn * 16;
@@ -524,9 +524,15 @@ cudaError_t conv3_tc(const ConvArgs& a, cudaStream_t s) {
   const int tiles_x = (a.W + TW - 1) / TW, tiles_y = (a.H + TH - 1) / TH;
   const long long tiles = (long long)a.B * tiles_x * tiles_y;
   if (tiles > (1LL << 30)) return cudaErrorInvalidValue;
+  // the widest block of output channels (up to 128) that still gives every
+  // SM a work item: a wider N makes fewer, more efficient MMAs (one per 53
+  // issue cycles at any N up to 128) and reads each window for more outputs
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int bn = 128;
   while (bn > 16 && nout % bn) bn >>= 1;
-  while (bn > 32 && tiles * (nout / bn) < 2 * 152) bn >>= 1;
+  while (bn > 32 && tiles * (nout / bn) < nsm) bn >>= 1;
   switch (bn) {
     case 128: return launch_tc<MODE, 128>(a, tiles_x, tiles_y, (int)tiles, nout, s);
     case 64: return launch_tc<MODE, 64>(a, tiles_x, tiles_y, (int)tiles, nout, s);
