@@ -389,6 +389,26 @@ __global__ void to_bf16_kernel(const float* x, int cin, __nv_bfloat16* y, int ld
   }
 }
 
+// the same for the network's input row of 16 channels (cin <= 16): a thread
+// takes a pixel, reads its cin values once and writes its 16 BF16 channels
+// as two 16-byte stores
+__global__ void to_bf16_16_kernel(const float* x, int cin, __nv_bfloat16* y, long long npix, const Norm nm) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix; p += (long long)gridDim.x * blockDim.x) {
+    uint4 o[2];
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(o);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int c0 = 2 * e, c1 = 2 * e + 1;
+      const float v0 = c0 < cin ? (x[p * cin + c0] - nm.mean[c0]) * nm.inv[c0] : 0.f;
+      const float v1 = c1 < cin ? (x[p * cin + c1] - nm.mean[c1]) * nm.inv[c1] : 0.f;
+      h[e] = __halves2bfloat162(__float2bfloat16_rn(v0), __float2bfloat16_rn(v1));
+    }
+    uint4* dst = reinterpret_cast<uint4*>(y + p * 16);
+    dst[0] = o[0];
+    dst[1] = o[1];
+  }
+}
+
 // output layer: 1x1 convolution cin -> cout (cout <= 16), FP32 out, no activation, then the
 // output map (scale, optional residual from the raw FP32 input xin of in_ch channels);
 // a thread takes one pixel, weights in shared memory
@@ -596,7 +616,10 @@ cudaError_t copy_ch(const __nv_bfloat16* src, int lds, int soff, __nv_bfloat16* 
 
 cudaError_t to_bf16(const float* x, int cin, __nv_bfloat16* y, int ldo, long long npix, const Norm& nm,
                     cudaStream_t s) {
-  to_bf16_kernel<<<blocks_for(npix * ldo), 256, 0, s>>>(x, cin, y, ldo, npix, nm);
+  if (ldo == 16 && cin <= 16 && (reinterpret_cast<uintptr_t>(y) & 15) == 0)
+    to_bf16_16_kernel<<<blocks_for(npix), 256, 0, s>>>(x, cin, y, npix, nm);
+  else
+    to_bf16_kernel<<<blocks_for(npix * ldo), 256, 0, s>>>(x, cin, y, ldo, npix, nm);
   return cudaGetLastError();
 }
 
