@@ -610,19 +610,6 @@ static size_t field_bytes(const gpe2p_ctx* h) {
 
 static int diag_impl(gpe2p_ctx* h, gpe2p_diag* d);
 
-// the reference of the conservation drift: the integral of the stored initial
-// phi (the integral of |phi_0| is taken by init_fields)
-static int drift_reference(gpe2p_ctx* h) {
-  if (h->esize != 4) return GPE2P_OK;  // FP64 problems ignore the policy
-  gpe2p_diag d{};
-  const int rc = diag_impl(h, &d);
-  if (rc != GPE2P_OK) return rc;
-  h->int_phi0 = d.int_phi;
-  h->last_drift = 0.0;
-  h->switched_at = -1;
-  return GPE2P_OK;
-}
-
 // start the compensated accumulation of phi: a zero low part; the step graphs
 // are rebuilt at the next step
 static int phi_acc_on(gpe2p_ctx* h) {
@@ -687,8 +674,6 @@ static cudaError_t init_impl(gpe2p_ctx* h, const double* phi, const double* u, c
   for (int f = 0; f < 1 + h->prm.dim; ++f)
     if ((e = put_field<real>(h, src[f], h->Q[0][f], f - 1)) != cudaSuccess) return e;
   if ((e = put_field<real>(h, phi, h->phi, -1, true)) != cudaSuccess) return e;
-  if ((e = cudaMemcpyAsync(h->h_out, h->d_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
-    return e;
   const KParams<real> P = kparams<real>(h->prm);
   if (h->prm.dim == 2)
     e = launch_mu<real, 2>(P, (real*)h->phi, (real*)h->mu, h->prm.iso, h->kchunk, h->stream, nullptr, h->d_err);
@@ -696,6 +681,10 @@ static cudaError_t init_impl(gpe2p_ctx* h, const double* phi, const double* u, c
     e = launch_mu<real, 3>(P, (real*)h->phi, (real*)h->mu, h->prm.iso, h->kchunk_mu, h->stream, &h->mu_maps[0],
                            h->d_err);
   if (e != cudaSuccess) return e;
+  // the integrals of |phi_0| and phi_0 (d_out[0], d_out[1]) and the error word after it
+  if ((e = cudaMemcpyAsync(h->h_out, h->d_out, 4 * sizeof(double) + sizeof(int), cudaMemcpyDeviceToHost,
+                           h->stream)) != cudaSuccess)
+    return e;
   return cudaStreamSynchronize(h->stream);
 }
 
@@ -714,7 +703,15 @@ extern "C" int gpe2p_init_fields(gpe2p_handle h, const double* phi, const double
   h->step = 0;
   h->initialized = true;
   h->abs_phi0 = h->h_out[0];
-  return drift_reference(h);
+  int errw = 0;
+  std::memcpy(&errw, h->h_out + 4, sizeof(int));
+  if (errw != 0) return fail(h, GPE2P_ETIMEOUT, "a device-side copy did not complete within its bounded wait");
+  // the reference of the conservation drift: the integral of phi_0 as stored,
+  // summed by the conversion pass
+  h->int_phi0 = h->h_out[1];
+  h->last_drift = 0.0;
+  h->switched_at = -1;
+  return GPE2P_OK;
 }
 
 static int diag_impl(gpe2p_ctx* h, gpe2p_diag* d) {

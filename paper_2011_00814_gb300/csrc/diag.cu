@@ -135,39 +135,65 @@ cudaError_t launch_diag(const KParams<real>& P, const real* p, const real* const
 
 // dense FP64 (host layout) -> padded rows in the working precision.  Blocks
 // stride over the rows (j, k) and threads along x, so that both sides are
-// read and written in order; src may be a pinned host array read in place.
-// With ABS, the block also sums |src| (in FP64, fixed order) into partial[4 b]
-// in the layout diag_final_kernel reduces, so that the integral of |phi_0|
-// needs no second read of the input.
+// read and written in order; src may be a pinned host array read in place,
+// in 16-byte pairs where the rows allow.  With ABS, the block also sums
+// |src| and the stored value (in FP64, fixed order) into partial[4 b] and
+// partial[4 b + 1], in the layout diag_final_kernel reduces: the integral of
+// |phi_0| and that of phi_0 as stored (the reference of the conservation
+// drift) need no second read.
 template <typename real, bool ABS>
 __global__ void __launch_bounds__(DIAG_THREADS) from_double_kernel(const KParams<real> P, const double* src,
                                                                    real* dst, int c, double* partial) {
   const int nx = P.n[0], ny = P.n[1];
   const long long rows = (long long)ny * P.n[2];
-  double a = 0.0;
+  const bool pairs = (nx & 1) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+  double a = 0.0, b = 0.0;
   for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
     const int j = (int)(r % ny), k = (int)(r / ny);
     const bool wall_row = c >= 0 && P.bc[c] != BC_PERIODIC && ((c == 1 && j == 0) || (c == 2 && k == 0));
+    const bool wall_x = c == 0 && P.bc[0] != BC_PERIODIC;
     const double* s = src + r * nx;
     real* d = dst + lin(P, 0, j, k);
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const double x = s[i];
-      if (ABS) a += fabs(x);
-      real v = (real)x;
-      if (wall_row || (c == 0 && P.bc[0] != BC_PERIODIC && i == 0)) v = real(0);
-      d[i] = v;
+    if (pairs) {
+      const double2* s2 = reinterpret_cast<const double2*>(s);
+      for (int i2 = threadIdx.x; i2 < (nx >> 1); i2 += blockDim.x) {
+        const double2 x = s2[i2];
+        if (ABS) a += fabs(x.x) + fabs(x.y);
+        real v0 = (real)x.x, v1 = (real)x.y;
+        if (wall_row || (wall_x && i2 == 0)) v0 = real(0);
+        if (wall_row) v1 = real(0);
+        if (ABS) b += (double)v0 + (double)v1;
+        d[2 * i2] = v0;
+        d[2 * i2 + 1] = v1;
+      }
+    } else {
+      for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const double x = s[i];
+        if (ABS) a += fabs(x);
+        real v = (real)x;
+        if (wall_row || (wall_x && i == 0)) v = real(0);
+        if (ABS) b += (double)v;
+        d[i] = v;
+      }
     }
   }
   if (ABS) {
-    __shared__ double red[DIAG_THREADS / 32];
+    __shared__ double red[2][DIAG_THREADS / 32];
     a = warp_sum(a);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    b = warp_sum(b);
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = a;
+      red[1][threadIdx.x >> 5] = b;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < DIAG_THREADS / 32; ++w) t += red[w];
+      double t = 0.0, u = 0.0;
+      for (int w = 0; w < DIAG_THREADS / 32; ++w) {
+        t += red[0][w];
+        u += red[1][w];
+      }
       partial[4 * blockIdx.x + 0] = t;
-      partial[4 * blockIdx.x + 1] = 0.0;
+      partial[4 * blockIdx.x + 1] = u;
       partial[4 * blockIdx.x + 2] = 0.0;
       partial[4 * blockIdx.x + 3] = 0.0;
     }
