@@ -209,12 +209,15 @@ __global__ void __launch_bounds__(TXv* TYv / 2) batch_persistent_kernel(const BI
   }
 }
 
-template <typename real, int TXv, int TYv>
+// one sweep SW over the work table, a tile per block: the sweep is a template
+// parameter, so that each sweep's kernel has the registers of its own tile
+// code (the flow stages need the most) and the others keep their occupancy
+template <typename real, int TXv, int TYv, int SW>
 __global__ void __launch_bounds__(TXv* TYv / 2) batch_sweep_kernel(const BInst<real>* __restrict__ insts,
-                                                                const BItem* __restrict__ items, int cur, int sw) {
+                                                                const BItem* __restrict__ items, int cur) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const BItem it = items[blockIdx.x];
-  do_sweep<real, TXv, TYv>(sw, insts[it.inst], it, cur, reinterpret_cast<real*>(smraw));
+  do_sweep<real, TXv, TYv>(SW, insts[it.inst], it, cur, reinterpret_cast<real*>(smraw));
 }
 
 template <typename real, int TXv, int TYv>
@@ -374,14 +377,19 @@ static cudaError_t enqueue_batch_shape(BatchCtx* b, int si, int persistent, int 
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
-  for (int sw = 0; sw < SW_N; ++sw) {
-    if (sw == SW_UH && !b->any_cons) continue;
-    batch_sweep_kernel<real, TXv, TYv><<<b->nitems[si], TXv * TYv / 2, smem, b->stream>>>(insts, b->items_dev[si], cur,
-                                                                                       sw);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  const unsigned grid = (unsigned)b->nitems[si], nt = TXv * TYv / 2;
+  const BItem* items = b->items_dev[si];
+  cudaStream_t st = b->stream;
+  batch_sweep_kernel<real, TXv, TYv, SW_FLOW1><<<grid, nt, smem, st>>>(insts, items, cur);
+  batch_sweep_kernel<real, TXv, TYv, SW_FLOW2><<<grid, nt, smem, st>>>(insts, items, cur);
+  batch_sweep_kernel<real, TXv, TYv, SW_FLOW3><<<grid, nt, smem, st>>>(insts, items, cur);
+  if (b->any_cons) batch_sweep_kernel<real, TXv, TYv, SW_UH><<<grid, nt, smem, st>>>(insts, items, cur);
+  batch_sweep_kernel<real, TXv, TYv, SW_CH1><<<grid, nt, smem, st>>>(insts, items, cur);
+  batch_sweep_kernel<real, TXv, TYv, SW_MU1><<<grid, nt, smem, st>>>(insts, items, cur);
+  batch_sweep_kernel<real, TXv, TYv, SW_CH2><<<grid, nt, smem, st>>>(insts, items, cur);
+  batch_sweep_kernel<real, TXv, TYv, SW_MU2><<<grid, nt, smem, st>>>(insts, items, cur);
+  static_assert(SW_N == 8, "the per-sweep form launches every sweep above, in order");
+  return cudaGetLastError();
 }
 
 template <typename real>
@@ -403,9 +411,17 @@ static cudaError_t prepare_shape(BatchCtx* b, int si) {
   cudaError_t e = cudaFuncSetAttribute(batch_persistent_kernel<real, TXv, TYv>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(batch_sweep_kernel<real, TXv, TYv>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
-  if (e != cudaSuccess) return e;
+  const void* sweeps[SW_N] = {(const void*)batch_sweep_kernel<real, TXv, TYv, SW_FLOW1>,
+                              (const void*)batch_sweep_kernel<real, TXv, TYv, SW_FLOW2>,
+                              (const void*)batch_sweep_kernel<real, TXv, TYv, SW_FLOW3>,
+                              (const void*)batch_sweep_kernel<real, TXv, TYv, SW_UH>,
+                              (const void*)batch_sweep_kernel<real, TXv, TYv, SW_CH1>,
+                              (const void*)batch_sweep_kernel<real, TXv, TYv, SW_MU1>,
+                              (const void*)batch_sweep_kernel<real, TXv, TYv, SW_CH2>,
+                              (const void*)batch_sweep_kernel<real, TXv, TYv, SW_MU2>};
+  for (int w = 0; w < SW_N; ++w)
+    if ((e = cudaFuncSetAttribute(sweeps[w], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
   // the work table of this tile shape: the tiles of every instance in order
   std::vector<BItem> items;
   for (int k = 0; k < b->n; ++k)
