@@ -4,12 +4,13 @@
 // A work item is a tile of 128 output pixels (16 rows x 8 columns of one
 // image: GEMM rows M = 128) for a block of BN output channels (GEMM columns
 // N).  Its K dimension (tap, input channel) is walked in chunks of 16
-// channels.  For a chunk the CTA stages, with cp.async:
+// channels.  For a chunk the CTA stages:
 //   A: the 18 x 10 input window of the tile (the 1-pixel halo wrapped
 //      periodically), 16 channels, as no-swizzle K-major core matrices
-//      [8-channel half][window row][window column][8 channels];
-//   B: the weights of the 9 taps for those channels, [tap][half][n][8],
-//      unless the CTA holds all its weights resident in shared memory.
+//      [8-channel half][window row][window column][8 channels], by cp.async;
+//   B: the weights of the 9 taps for those channels, [tap][half][n][8], by
+//      bulk copies from weights packed per chunk in that order, unless the
+//      CTA holds all its weights resident in shared memory.
 // The A operand of tap (dy, dx) is the same window read from a start address
 // shifted by (dy, dx) pixels: with 8-pixel tile rows, consecutive 8-row core
 // matrices of M sit one window row (160 bytes) apart for every tap.  The 9
@@ -151,12 +152,13 @@ __device__ __forceinline__ TileGeom tile_of(int t, int tiles_x, int tiles_y) {
 //   warps 0-3: epilogue; warp w reads tensor-memory lanes 32w .. 32w + 31
 //              (the pixels of its quarter of the tile), applies bias and SiLU
 //              and stores BF16;
-//   warps 4-5: producers; they stage the input window and (unless resident)
-//              the weights of each K chunk with cp.async into a ring of ns
-//              stages; each thread's copies arrive on the stage's full
-//              barrier by themselves when they land (cp.async.mbarrier.arrive
-//              .noinc), so a producer waits only for a free stage and keeps up
-//              to ns chunks in flight;
+//   warps 4-5: producers; they stage the input window of each K chunk with
+//              cp.async and (unless resident) its weights with bulk copies
+//              into a ring of ns stages; each thread's copies arrive on the
+//              stage's full barrier by themselves when they land
+//              (cp.async.mbarrier.arrive.noinc), the bulk copies count their
+//              bytes on it, so a producer waits only for a free stage and
+//              keeps up to ns chunks in flight;
 //   warp 6:    one thread waits for a full stage, fences it to the async
 //              proxy, issues the chunk's tcgen05.mma and commits them to the
 //              stage's empty barrier, and at a tile's last chunk to the
