@@ -170,7 +170,7 @@ __device__ __forceinline__ TileGeom tile_of(int t, int tiles_x, int tiles_y) {
 constexpr int EPI_WARPS = 4, PROD_WARPS = 2;
 constexpr int NTHR = 32 * (EPI_WARPS + PROD_WARPS + 1);
 constexpr int MMA_WARP = EPI_WARPS + PROD_WARPS;
-constexpr int SMIN = 3, SMAX = 8;  // stages of the ring (chosen per launch)
+constexpr int SMIN = 2, SMAX = 8;  // stages of the ring (chosen per launch)
 constexpr int MAX_OCC = 4;         // CTAs per SM at most
 
 __host__ __device__ __forceinline__ int smem_bytes(int bn, int nchunks, bool resident, int ns) {
