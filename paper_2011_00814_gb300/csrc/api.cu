@@ -1087,8 +1087,8 @@ extern "C" int gpe2p_batch_config(gpe2p_handle h, int* tile_x, int* tile_y, int*
   return batch_config(h->batch, tile_x, tile_y, persistent, ms_per_step);
 }
 
-static_assert(GPE2P_LOSE_FLOW_RING == WF_FLOW_RING && GPE2P_LOSE_CH_RING == WF_CH_RING &&
-                  GPE2P_LOSE_MU_RING == WF_MU_RING && GPE2P_LOSE_CH_POINTS == WF_CH_POINTS,
+static_assert((int)GPE2P_LOSE_FLOW_RING == (int)WF_FLOW_RING && (int)GPE2P_LOSE_CH_RING == (int)WF_CH_RING &&
+                  (int)GPE2P_LOSE_MU_RING == (int)WF_MU_RING && (int)GPE2P_LOSE_CH_POINTS == (int)WF_CH_POINTS,
               "the header's bits are the kernels' bits");
 
 extern "C" int gpe2p_set_fault_injection(gpe2p_handle h, int what, long long value) {

@@ -14,8 +14,8 @@ namespace gpe2p {
 // The single-instance 2D CH stage and mu: one tile per block.
 template <typename real>
 __global__ void __launch_bounds__(NTHR / 2) ch2d_kernel(const KParams<real> P, const CHArgs<real> A) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  ch2d_tile<real, TX, TY>(P, A, blockIdx.x * TX, blockIdx.y * TY, reinterpret_cast<real*>(smraw));
+  extern __shared__ __align__(16) unsigned char smraw2d[];
+  ch2d_tile<real, TX, TY>(P, A, blockIdx.x * TX, blockIdx.y * TY, reinterpret_cast<real*>(smraw2d));
 }
 
 template <typename real>
