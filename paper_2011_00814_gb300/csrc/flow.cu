@@ -19,8 +19,8 @@ namespace gpe2p {
 // The single-instance 2D flow stage: one tile per block, two cells per thread.
 template <typename real, int MODE>
 __global__ void __launch_bounds__(NTHR / 2) flow2d_kernel(const KParams<real> P, const FlowArgs<real> A) {
-  extern __shared__ __align__(16) unsigned char smraw2d[];
-  flow2d_tile<real, MODE, TX, TY>(P, A, blockIdx.x * TX, blockIdx.y * TY, reinterpret_cast<real*>(smraw2d));
+  extern __shared__ __align__(16) unsigned char smraw[];
+  flow2d_tile<real, MODE, TX, TY>(P, A, blockIdx.x * TX, blockIdx.y * TY, reinterpret_cast<real*>(smraw));
 }
 
 // ---------------------------------------------------------------------------
