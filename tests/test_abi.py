@@ -211,3 +211,44 @@ def test_noalloc_diagnostics_validate_on_the_host(lib):
     # well formed: it gets as far as the device lookup
     assert call(good2, w=None) == gpe2p.ECUDA
     assert call(good3) == gpe2p.ECUDA
+
+
+def test_measurement_fault_and_network_calls_validate_on_the_host(lib):
+    """The rate probes, the fault switches and the network calls refuse bad
+    arguments before they touch a device, so the refusals hold without one."""
+    out = ctypes.c_double()
+    # gpe2p_mma_rate: N in {32, 64, 128, 256}, 1, 2 or 4 issuers, N x issuers <= 512 TMEM columns
+    assert lib.gpe2p_mma_rate(48, 1, ctypes.byref(out), None) == gpe2p.EINVAL
+    assert lib.gpe2p_mma_rate(64, 3, ctypes.byref(out), None) == gpe2p.EINVAL
+    assert lib.gpe2p_mma_rate(256, 4, ctypes.byref(out), None) == gpe2p.EINVAL
+    assert lib.gpe2p_mma_rate(128, 2, None, None) == gpe2p.EINVAL
+    # gpe2p_fma_rate: precision 32 or 64, an output
+    assert lib.gpe2p_fma_rate(16, ctypes.byref(out), None, None) == gpe2p.EINVAL
+    assert lib.gpe2p_fma_rate(64, None, None, None) == gpe2p.EINVAL
+    # fault switches without a handle
+    assert lib.gpe2p_set_fault_injection(None, gpe2p.FAULT_LOSE_COPY, 1) == gpe2p.EINVAL
+    assert lib.gpe2p_net_fault(None, gpe2p.FAULT_LOSE_COPY, 1) == gpe2p.EINVAL
+    # network calls without a handle
+    assert lib.gpe2p_net_sync(None) == gpe2p.EINVAL
+    assert lib.gpe2p_net_set_backend(None, 1) == gpe2p.EINVAL
+    assert lib.gpe2p_net_forward(None, None, None, 1) == gpe2p.EINVAL
+    assert lib.gpe2p_net_gradients(None, None, None, 1, None, None) == gpe2p.EINVAL
+    assert lib.gpe2p_net_train_step(None, None, None, 1, 1e-3, None) == gpe2p.EINVAL
+    # gpe2p_net_create: each shape rule refused with its reason, and no handle left behind
+    h = ctypes.c_void_p(1)
+
+    def create(levels=4, ch=(32, 64, 128, 256), in_ch=4, out_ch=4, H=64, W=64, B=2, out=True):
+        arr = (ctypes.c_int * max(len(ch), 1))(*ch)
+        return lib.gpe2p_net_create(levels, arr, in_ch, out_ch, H, W, B, 0, None,
+                                    ctypes.byref(h) if out else None)
+
+    assert create(out=False) == gpe2p.EINVAL
+    for kw, why in ((dict(levels=0), b"levels"), (dict(levels=7, ch=(32,) * 7), b"levels"),
+                    (dict(ch=(32, 64, 120, 256)), b"channels"), (dict(ch=(8, 64, 128, 256)), b"channels"),
+                    (dict(in_ch=0), b"channels"), (dict(out_ch=17), b"channels"),
+                    (dict(H=60), b"multiples"), (dict(W=4), b"multiples"),
+                    (dict(B=0), b"max_batch"), (dict(B=1 << 20, H=256, W=256), b"max_batch")):
+        assert create(**kw) == gpe2p.EINVAL, kw
+        assert h.value is None, kw
+        assert why in lib.gpe2p_net_last_error(None), kw
+        h = ctypes.c_void_p(1)
