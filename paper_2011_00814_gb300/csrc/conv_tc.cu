@@ -473,8 +473,10 @@ cudaError_t launch_tc(const ConvArgs& a, int tiles_x, int tiles_y, int ntiles, i
   cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
   // Up to MAX_OCC CTAs per SM as the tensor memory and shared memory allow,
   // each with a ring of at least SMIN stages: a CTA issues its MMAs from one
-  // thread, at about one per 86 cycles, so the tensor pipe of an SM is kept
-  // busy at N <= 128 only by several issuing CTAs.  The weights stay resident
+  // thread, at most one per 53 cycles (gpe2p_mma_rate), while the SM takes
+  // one every 40 (N = 32), 48 (N = 64) or 64 (N = 128) cycles from several
+  // issuers, so the tensor pipe is kept busy only by several issuing CTAs.
+  // The weights stay resident
   // if that still leaves the ring, else they stream through it; the ring
   // takes as many stages as fit (up to SMAX).
   const int tm_occ = 512 / Cfg<BN>::TCOLS;
@@ -527,8 +529,9 @@ cudaError_t conv3_tc(const ConvArgs& a, cudaStream_t s) {
   const long long tiles = (long long)a.B * tiles_x * tiles_y;
   if (tiles > (1LL << 30)) return cudaErrorInvalidValue;
   // the widest block of output channels (up to 128) that still gives every
-  // SM a work item: a wider N makes fewer, more efficient MMAs (one per 53
-  // issue cycles at any N up to 128) and reads each window for more outputs
+  // SM a work item: a wider N does the same work in fewer MMAs (one thread
+  // issues at most one per 53 cycles whatever N) and reads each window for
+  // more outputs
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
