@@ -3,7 +3,9 @@
 bench.py's own byte counts: every key the contract asks for is there, and the
 derived numbers agree with the measured ones they come from (the value with
 the step time and the grid, the roofline fraction with its rate and peak, the
-algorithmic bytes with the per-cell word counts of the 3D step)."""
+algorithmic bytes with the per-cell word counts of the 3D step, and in the
+batch, axisymmetric, static-drop and surrogate sections each rate, speedup,
+Laplace ratio, bar verdict and forward roofline with its own inputs)."""
 import json
 import math
 import os
@@ -95,3 +97,61 @@ def test_the_clock_record_is_clean(line):
     for bad in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
         assert bad not in c["reasons"]
     assert c["sm_mhz"] >= 0.9 * c["sm_max_mhz"]
+
+
+def test_the_batch_axisymmetric_and_static_drop_sections(line):
+    from paper_2011_00814_gb300 import inputs
+    b = line["batch2d"]
+    prms, _ = inputs.batch_instances(n=96, seed=0, precision=32)
+    assert b["cells"] == sum(p["nx"] * p["ny"] for p in prms)
+    for arm in ("batched", "loop"):
+        assert close(b[arm]["cell_updates_per_s"] * b[arm]["ms_per_step"] / 1e3, b["cells"])
+    assert close(b["speedup"], b["batched"]["cell_updates_per_s"] / b["loop"]["cell_updates_per_s"])
+    # 49 words (196 B) per 2D cell-update with TVD-RK2 CH
+    assert close(b["step_algorithmic_gbs"], 49 * 4 * b["batched"]["cell_updates_per_s"] / 1e9)
+    assert close(b["step_frac"], b["step_algorithmic_gbs"] / line["roofline"]["peak"])
+    a = line["axisym"]
+    assert a["cells"] == 400 * 1200
+    for prec in ("fp32", "fp64"):
+        assert close(a[prec]["cell_updates_per_s"] * a[prec]["ms_per_step"] / 1e3, a["cells"])
+        assert a[prec]["nan"] == 0
+    sd = line["static_drop"]
+    for r in (sd["advective"], sd["advective"]["settled"]):
+        assert close(r["sigma_over_R_eff"] * r["R_eff"], sd["advective"]["sigma_over_R_eff"] * sd["advective"]["R_eff"])
+        assert close(r["dP_over_laplace"], r["dP"] / r["sigma_over_R_eff"])
+        assert close(r["dp_over_laplace"], r["dp"] / r["sigma_over_R_eff"])
+        assert r["within_2pct"] == (abs(r["dP_over_laplace"] - 1.0) <= 0.02)
+    for form in ("advective", "conservative"):
+        r = sd[form]
+        assert close(r["max_spurious_u_over_Uc"], r["max_spurious_u"] / sd["U_c"])
+    assert sd["conservative"]["int_phi_drift"] == 0.0
+
+
+def test_the_surrogate_section(line):
+    s = line["surrogate"]
+    bars = s["bars"]
+    for key in ("network", "persistence"):
+        rs = [c[key] for c in s["cases"]]
+        for r in rs:
+            assert close(r["speedup"], r["solver_ms"] / r["controller_ms"])
+            assert r["meets_bars"] == (r["phi_l2"] <= bars["phi_l2"] and r["interface_max"] <= bars["interface_cells"])
+            st = r["stats"]
+            assert st["calls"] == 64 and st["net_calls"] <= st["calls"] and st["failures"] <= st["checks"]
+        summ = s[key]
+        assert close(summ["speedup"], sum(r["speedup"] for r in rs) / len(rs))
+        assert summ["phi_l2_max"] == max(r["phi_l2"] for r in rs)
+        assert summ["interface_max_cells"] == max(r["interface_max"] for r in rs)
+        assert summ["check_failures"] == sum(r["stats"]["failures"] for r in rs)
+        assert summ["meets_bars_every_case"] == all(r["meets_bars"] for r in rs)
+    # the speedup is claimed only for a configuration that meets both bars on every case
+    if s["network"]["meets_bars_every_case"]:
+        assert s["speedup_at_tolerance"] == s["network"]["speedup"]
+    else:
+        assert s["speedup_at_tolerance"] is None
+    f8, f1 = s["forward"], s["forward_batch1"]
+    assert f8["batch"] == 8 and f1["batch"] == 1 and close(f8["gflop"], 8 * f1["gflop"])
+    for f in (f8, f1):
+        r = f["roofline"]
+        assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+        assert close(r["achieved"], f["gflop"] / (f["ms"] / 1e3) / 1e3)
+        assert close(r["frac"], r["achieved"] / r["peak"]) and 0 < r["frac"] < 1.05
