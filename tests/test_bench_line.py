@@ -155,3 +155,20 @@ def test_the_surrogate_section(line):
         assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
         assert close(r["achieved"], f["gflop"] / (f["ms"] / 1e3) / 1e3)
         assert close(r["frac"], r["achieved"] / r["peak"]) and 0 < r["frac"] < 1.05
+
+
+def test_the_stored_dram_traffic_is_the_capture_scaled_to_the_grid(line):
+    with open(os.path.join(HERE, "..", "profiles", "flow_stage_bubble3d_traffic.json")) as f:
+        t = json.load(f)
+    per = [t[s]["dram_bytes_read"] + t[s]["dram_bytes_write"] for s in ("stage2", "stage3")]
+    assert close(t["bytes_per_launch_captured"], sum(per) / 2)
+    # captured on 128 x 128 x 256, scaled by cells to 256 x 256 x 512
+    assert t["scale_to_full_grid"] == (256 * 256 * 512) / (128 * 128 * 256)
+    assert close(t["bytes_per_launch_full_grid"], t["bytes_per_launch_captured"] * t["scale_to_full_grid"])
+    w = (t["stage2"]["algorithmic_bytes_per_cell"] + t["stage3"]["algorithmic_bytes_per_cell"]) / 2
+    assert w == (bench.WORDS["flow_stage2"] + bench.WORDS["flow_stage3"]) / 2 * 4
+    assert close(t["algorithmic_bytes_per_launch_full_grid"], w * 256 * 256 * 512)
+    assert t["command"].startswith("ncu ") and "--clock-control none" in t["command"]
+    # the bench line carries this figure when its kernel sources were those of the capture
+    if line["roofline"]["traffic"] is not None:
+        assert close(line["roofline"]["traffic"], t["bytes_per_launch_full_grid"])
