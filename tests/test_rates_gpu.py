@@ -45,7 +45,7 @@ def test_mma_issue_rates():
             print(f"N {n:3d} issuers {k}: {c:6.1f} cycles per MMA per SM, {128 * n * 16 / c:6.0f} MAC/cycle")
             assert math.isfinite(c) and c >= 128 * n * 16 / 4096 * 0.98
     for n in (32, 64, 128):
-        assert rows[n, 2] <= rows[n, 1] * 1.02
+        assert rows[n, 2] <= rows[n, 1] * 1.05
     with pytest.raises(gpe2p.GPE2PError):
         gpe2p.mma_rate(48, 1)
     with pytest.raises(gpe2p.GPE2PError):
