@@ -2,6 +2,13 @@
 // the face density, max |u|, NaN/Inf flag) and the FP64 <-> working-precision
 // copies used at the host boundary.
 //
+// The sum of phi is the integral the Cahn-Hilliard equation (Eq. che)
+// conserves. The advective form conserves it only up to the flow's
+// compressibility, so its drift measures the method. The kinetic energy takes
+// each face velocity with the density of its face, the mean of the two cells'
+// densities (Eq. density-viscosity-op-two-phase, linear in phi). max |u| gives
+// the spurious currents of a drop at rest.
+//
 // The reduction is deterministic: a fixed grid of blocks walks the cells with
 // a grid-stride loop, each block reduces its partial sums with warp shuffles
 // into a slot of a scratch array, and a single block then sums the slots in
