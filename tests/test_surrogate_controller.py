@@ -8,6 +8,10 @@ alone) is host logic.  Here the state is two numbers, the time t in steps and
 a "drift" that only the network adds; the solver advances t exactly and adds
 nothing.  So after every call t must equal calls * K, and the drift tells
 which network results were kept.
+
+The calibration of the check's displacement tolerance is host logic too: with
+a stand-in for the solver comparison it must keep the largest candidate at
+which every case ends within the margin of both bars.
 """
 from __future__ import annotations
 
@@ -148,3 +152,56 @@ def test_persistence_baseline_never_calls_the_network(numpy_buffers):
     for _ in range(3):
         c.call()
     assert c.stats.failures == 1 and sol.t == 4 * K and net.calls == 0
+
+
+def _fake_compare(errors):
+    """A stand-in for compare_to_solver: errors[(case, tol_disp)] = (phi_l2,
+    interface); records every (case, tol_disp) it is asked for."""
+    asked = []
+
+    def compare(sur, prm, f, calls, tol=None, tol_disp=None, repeats=1):
+        asked.append((prm, tol_disp))
+        l2, itf = errors[(prm, tol_disp)]
+        return {"phi_l2": l2, "interface_max": itf, "speedup": 1.0 + tol_disp,
+                "stats": {"calls": calls, "net_calls": calls // 2, "failures": 0}}
+    return compare, asked
+
+
+def test_calibration_takes_the_largest_tolerance_within_the_margin(monkeypatch):
+    """Candidates are tried from the largest down and the first at which
+    every case ends within margin x both bars is kept; a case inside the bars
+    but outside the margin disqualifies a candidate, on either measure."""
+    bar_l2, bar_if = surrogate.BAR_PHI_L2, surrogate.BAR_INTERFACE
+    cands = (0.3, 0.1, 0.03)
+    errors = {
+        ("a", 0.3): (0.5 * bar_l2, 0.9 * bar_if), ("b", 0.3): (0.1 * bar_l2, 0.1 * bar_if),  # a: inside bar, not margin
+        ("a", 0.1): (0.1 * bar_l2, 0.5 * bar_if), ("b", 0.1): (0.85 * bar_l2, 0.1 * bar_if),  # b: phi L2 past margin
+        ("a", 0.03): (0.1 * bar_l2, 0.3 * bar_if), ("b", 0.03): (0.2 * bar_l2, 0.2 * bar_if),
+    }
+    compare, asked = _fake_compare(errors)
+    monkeypatch.setattr(surrogate, "compare_to_solver", compare)
+    res = surrogate.calibrate_tolerance(None, [("a", None), ("b", None)], calls=8, candidates=cands, margin=0.8)
+    assert res["tol_disp"] == 0.03
+    assert [r["tol_disp"] for r in res["candidates"]] == [0.3, 0.1, 0.03]
+    assert [r["qualifies"] for r in res["candidates"]] == [False, False, True]
+    assert res["candidates"][0]["interface_max_cells"] == 0.9 * bar_if
+    assert res["candidates"][1]["phi_l2_max"] == 0.85 * bar_l2
+    assert res["candidates"][2]["network_share"] == 0.5
+    assert len(asked) == 6
+    # once a candidate qualifies, the smaller ones are not run
+    errors[("b", 0.1)] = (0.1 * bar_l2, 0.1 * bar_if)
+    compare, asked = _fake_compare(errors)
+    monkeypatch.setattr(surrogate, "compare_to_solver", compare)
+    res = surrogate.calibrate_tolerance(None, [("a", None), ("b", None)], calls=8, candidates=cands, margin=0.8)
+    assert res["tol_disp"] == 0.1 and len(res["candidates"]) == 2 and len(asked) == 4
+
+
+def test_calibration_reports_none_when_no_candidate_qualifies(monkeypatch):
+    bar_l2, bar_if = surrogate.BAR_PHI_L2, surrogate.BAR_INTERFACE
+    errors = {("a", td): (0.1 * bar_l2, 1.2 * bar_if) for td in (0.2, 0.02)}
+    compare, _ = _fake_compare(errors)
+    monkeypatch.setattr(surrogate, "compare_to_solver", compare)
+    res = surrogate.calibrate_tolerance(None, [("a", None)], calls=8, candidates=(0.02, 0.2))
+    assert res["tol_disp"] is None
+    assert [r["tol_disp"] for r in res["candidates"]] == [0.2, 0.02]
+    assert not any(r["qualifies"] for r in res["candidates"])
